@@ -1,0 +1,197 @@
+/*
+ * dg.h -- C ABI of the GB300 matrix-free discontinuous Galerkin solver for the
+ * first-order acoustic wave equation (Schoeder, Kormann, Wall, Kronbichler,
+ * "Efficient Explicit Time Stepping of High Order Discontinuous Galerkin
+ * Schemes for Waves").
+ *
+ * Problem (Sec. 2, Eq. (1)): du/dt + S u = 0 with u = (p, v),
+ *   dv/dt + rho^-1 grad p = 0,   dp/dt + rho c^2 div v = 0.
+ * Discretisation (Sec. 2.1, Eqs. (2)-(3)): DG on hexahedra, tensor degree k,
+ * state stored in the Lagrange basis on the (k+1)^3 Gauss-Lobatto nodes
+ * ("GL", Sec. 3.1), integrals by (k+1)^3 / (k+1)^2 Gauss points, mass terms
+ * weighted by rho (velocity) and 1/(rho c^2) (pressure); upwind (alpha = 1)
+ * or central (alpha = 0) impedance-weighted flux (Sec. 2.4).
+ *
+ * Conventions
+ * -----------
+ * - Every call returns an int status (DG_OK = 0, negative = error). No call
+ *   aborts, throws or exits; on error the context (when one is given) keeps
+ *   a message readable through dg_last_error().
+ * - State layout: U[E][4][(k+1)^3], fields (p, v_x, v_y, v_z), nodes
+ *   lexicographic with the first reference axis fastest. Element-local node
+ *   values in the GL basis. Device states are caller-owned device pointers in
+ *   the context's precision (double for DG_FP64, float for DG_FP32).
+ * - Streams are passed as uintptr_t holding a cudaStream_t (0 = legacy
+ *   default stream). All device work of a call is enqueued on that stream;
+ *   calls return once the work is enqueued unless stated otherwise.
+ * - Host arrays passed in are caller-owned and only read during the call.
+ * - Contexts are not thread safe: one thread at a time per context.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DG_OK            0
+#define DG_EINVAL       -1  /* bad argument (NULL, size, range) */
+#define DG_ENOMEM       -2  /* device or host allocation failed */
+#define DG_ECUDA        -3  /* a CUDA runtime call failed */
+#define DG_EUNSUPPORTED -4  /* e.g. degree outside [1, DG_KMAX] */
+#define DG_EAGAIN       -5  /* dg_poll: request not finished yet */
+#define DG_ETIMEOUT     -6  /* a bounded device wait gave up */
+#define DG_EMESH        -7  /* inconsistent connectivity or det J <= 0 */
+
+/* precisions */
+#define DG_FP64 0  /* operator, state and geometry in double */
+#define DG_FP32 1  /* operator and state in float; geometry set up in double */
+
+#define DG_KMAX 7
+
+typedef struct dg_ctx dg_ctx;
+
+/*
+ * Mesh description (all host arrays, caller-owned, read during the call).
+ *  n_elem       number of hexahedra E >= 1
+ *  geom_degree  q >= 1: each element is the image of [-1,1]^3 under the
+ *               degree-q Lagrange interpolant of its geometry nodes
+ *  nodes        [E][(q+1)^3][3] physical positions of the geometry nodes at
+ *               the tensor Gauss-Lobatto points of degree q (first axis
+ *               fastest)
+ *  nbr          [E][6] neighbour element across local face f, or -1 for a
+ *               reflecting wall. Faces: 0 -xi, 1 +xi, 2 -eta, 3 +eta,
+ *               4 -zeta, 5 +zeta. Periodicity is expressed by nbr alone.
+ *  nbr_face     [E][6] the neighbour's local face index (ignored at walls)
+ *  orient       [E][6] orientation code 0..7. The tangential axes of face f
+ *               are the two reference axes other than f/2, in increasing
+ *               order; a face point has indices (i, j) along them. Code o
+ *               maps (i, j) to the neighbour's (i', j'): (u, v) = (j, i) if
+ *               o & 1 else (i, j); i' = n-1-u if o & 2 else u;
+ *               j' = n-1-v if o & 4 else v.
+ */
+typedef struct {
+  int32_t n_elem;
+  int32_t geom_degree;
+  const double* nodes;
+  const int32_t* nbr;
+  const int8_t* nbr_face;
+  const int8_t* orient;
+} dg_mesh_desc;
+
+/*
+ * Validate the mesh (index ranges, nbr/nbr_face symmetry, orientation codes
+ * that are mutual inverses), upload it, compute geometry in FP64 on the GPU
+ * (inverse Jacobians, determinants, face normals; Sec. 3 "pre-computed
+ * inverse Jacobians", Sec. 3.3) with rho = c = 1, and return a context.
+ *  k           polynomial degree, 1 <= k <= DG_KMAX
+ *  prec        DG_FP64 or DG_FP32
+ *  flux_alpha  1 = upwind (HDG flux with tau = 1/(rho c), Sec. 2.4),
+ *              0 = central; any value in [0, 1]
+ *  stream      stream for the set-up work; the call synchronises it
+ * Errors: DG_EINVAL, DG_EUNSUPPORTED, DG_EMESH (bad connectivity or a
+ * non-positive Jacobian determinant anywhere), DG_ENOMEM, DG_ECUDA.
+ * On error *out is NULL and nothing is leaked.
+ */
+int dg_mesh_setup(const dg_mesh_desc* mesh, int k, int prec, double flux_alpha,
+                  uintptr_t stream, dg_ctx** out);
+
+/*
+ * Set the coefficients rho > 0 and c > 0 (Sec. 2, Eq. (1)) as host arrays
+ * [E][(k+1)^3] of values at each element's GL solution nodes; each is the
+ * degree-k polynomial through those values, and may jump between elements.
+ * Recomputes mass diagonals, impedances and predictor coefficients in FP64.
+ * Synchronises the stream. Errors: DG_EINVAL (NULL, non-positive value),
+ * DG_ECUDA.
+ */
+int dg_set_coefficients(dg_ctx* ctx, const double* rho, const double* c,
+                        uintptr_t stream);
+
+/*
+ * R = -M^-1 K U (Sec. 2.1 Eq. (3)): the semi-discrete right-hand side,
+ * cell terms by sum factorisation at Gauss points, face fluxes from the GL
+ * face nodes of both neighbours (Sec. 3.1), inverse mass by the basis change
+ * GL -> G, diagonal, G -> GL (Sec. 3.1). U and R are device arrays
+ * [E][4][(k+1)^3] that must not overlap.
+ */
+int dg_apply_operator(dg_ctx* ctx, const void* U, void* R, uintptr_t stream);
+
+/*
+ * nsteps of the five-stage fourth-order 2N-storage low-storage Runge-Kutta
+ * scheme (Sec. 2.2), dU <- A_s dU + dt R(U); U <- U + B_s dU, with the vector
+ * updates fused into the operator kernel. U (device) holds the initial state
+ * and receives the final one. dt > 0, nsteps >= 0.
+ */
+int dg_step_lsrk(dg_ctx* ctx, void* U, double dt, int32_t nsteps, uintptr_t stream);
+
+/*
+ * nsteps of ADER (Sec. 2.3, Eq. (6)): Ubar = Taylor-Cauchy-Kowalevski
+ * predictor with the element-local basis change GL -> G (Sec. 3.2,
+ * Algorithm 2) and degree reduction every reduce_every-th derivative
+ * (Sec. 3.3, Algorithm 3; 2 = the paper's choice, 0 = none), then
+ * U <- U - M^-1 K Ubar. Sum over j = 0..k+1. reduce_every in {0, 1, 2, 3}.
+ */
+int dg_step_ader(dg_ctx* ctx, void* U, double dt, int32_t nsteps,
+                 int32_t reduce_every, uintptr_t stream);
+
+/*
+ * The predictor alone: Ubar (device, GL basis) = sum_j dt^{j+1}/(j+1)! T_j of
+ * Eq. (6) for the state U. U and Ubar must not overlap.
+ */
+int dg_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int32_t reduce_every,
+           uintptr_t stream);
+
+/*
+ * Discrete energy 1/2 U^T M U = 1/2 (rho |v|^2 + p^2/(rho c^2)) integrated by
+ * the Gauss rule, accumulated in double with a fixed summation order
+ * (bitwise reproducible). *out is a host double; the call synchronises the
+ * stream.
+ */
+int dg_energy(dg_ctx* ctx, const void* U, double* out, uintptr_t stream);
+
+/*
+ * Sums of squares over all entries, accumulated in double in a fixed order:
+ * *out_aa = sum A^2 and, when B is not NULL, *out_dd = sum (A - B)^2.
+ * A, B are device states of this context. Synchronises the stream.
+ */
+int dg_norms(dg_ctx* ctx, const void* A, const void* B, double* out_aa,
+             double* out_dd, uintptr_t stream);
+
+/*
+ * End-to-end solve through host memory: copy U_host (host, [E][4][(k+1)^3]
+ * in the context precision) into a context-owned device state, run nsteps of
+ * method (0 = LSRK, 1 = ADER), copy the result back to U_out_host, and
+ * synchronise. Pinned host buffers make the copies asynchronous.
+ */
+int dg_solve_host(dg_ctx* ctx, int method, const void* U_host, void* U_out_host,
+                  double dt, int32_t nsteps, int32_t reduce_every, uintptr_t stream);
+
+/* Sizes: number of elements, degree, precision, bytes of one state. */
+int dg_info(const dg_ctx* ctx, int32_t* n_elem, int32_t* k, int32_t* prec,
+            size_t* state_bytes);
+
+/* Device bytes owned by the context (geometry, coefficients, scratch). */
+size_t dg_device_bytes(const dg_ctx* ctx);
+
+/* Kernel launches issued by this context since it was created. */
+uint64_t dg_launch_count(const dg_ctx* ctx);
+
+/* Free everything owned by the context. NULL-safe. */
+void dg_destroy(dg_ctx* ctx);
+
+/* Static string for a status code. */
+const char* dg_strerror(int status);
+
+/* Last error message of the context ("" if none); NULL ctx gives the
+ * message of the last failed dg_mesh_setup in this thread. */
+const char* dg_last_error(const dg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DG_H */

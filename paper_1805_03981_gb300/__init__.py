@@ -1,0 +1,10 @@
+"""GB300 (sm_103a) matrix-free DG solver for the acoustic wave equation.
+
+Thin Python binding of the C ABI in include/dg.h (``libdg.so`` built in-tree
+by ``build.py``).  Every step of the solver runs in the library's CUDA
+kernels; this package only marshals arrays, pointers and streams.  Importing
+it does not load the library; the first use does, and fails loudly if the
+library is missing.
+"""
+from ._lib import (DGError, Solver, load_library, library_path,  # noqa: F401
+                   DG_FP64, DG_FP32, EXPORTED_SYMBOLS)

@@ -1,0 +1,204 @@
+"""ctypes binding of libdg.so (include/dg.h): argument marshalling only."""
+import ctypes as C
+import os
+
+import numpy as np
+
+DG_FP64, DG_FP32 = 0, 1
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+# every symbol include/dg.h declares
+EXPORTED_SYMBOLS = [
+    "dg_mesh_setup", "dg_set_coefficients", "dg_apply_operator", "dg_step_lsrk",
+    "dg_step_ader", "dg_tck", "dg_energy", "dg_norms", "dg_solve_host", "dg_info",
+    "dg_device_bytes", "dg_launch_count", "dg_destroy", "dg_strerror", "dg_last_error",
+]
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"dg status {status}: {msg}")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("n_elem", C.c_int32), ("geom_degree", C.c_int32),
+                ("nodes", C.POINTER(C.c_double)), ("nbr", C.POINTER(C.c_int32)),
+                ("nbr_face", C.POINTER(C.c_int8)), ("orient", C.POINTER(C.c_int8))]
+
+
+_lib = None
+
+
+def library_path():
+    return os.path.join(_HERE, "libdg.so")
+
+
+def load_library():
+    """Load libdg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: build it with paper_1805_03981_gb300/build.py")
+    lib = C.CDLL(path)
+    vp, u = C.c_void_p, C.c_size_t
+    st = C.c_size_t  # uintptr_t stream
+    sig = {
+        "dg_mesh_setup": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.c_int, C.c_double, st, C.POINTER(vp)]),
+        "dg_set_coefficients": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), st]),
+        "dg_apply_operator": (C.c_int, [vp, vp, vp, st]),
+        "dg_step_lsrk": (C.c_int, [vp, vp, C.c_double, C.c_int32, st]),
+        "dg_step_ader": (C.c_int, [vp, vp, C.c_double, C.c_int32, C.c_int32, st]),
+        "dg_tck": (C.c_int, [vp, vp, vp, C.c_double, C.c_int32, st]),
+        "dg_energy": (C.c_int, [vp, vp, C.POINTER(C.c_double), st]),
+        "dg_norms": (C.c_int, [vp, vp, vp, C.POINTER(C.c_double), C.POINTER(C.c_double), st]),
+        "dg_solve_host": (C.c_int, [vp, C.c_int, vp, vp, C.c_double, C.c_int32, C.c_int32, st]),
+        "dg_info": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                              C.POINTER(u)]),
+        "dg_device_bytes": (u, [vp]),
+        "dg_launch_count": (C.c_uint64, [vp]),
+        "dg_destroy": (None, [vp]),
+        "dg_strerror": (C.c_char_p, [C.c_int]),
+        "dg_last_error": (C.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(x):
+    return C.c_void_p(x.data_ptr())
+
+
+class Solver:
+    """One mesh, degree and precision on the current CUDA device.
+
+    mesh: dict with ``n_elem``, ``geom_degree``, ``nodes`` [E,(q+1)^3,3],
+    ``nbr``, ``nbr_face``, ``orient`` [E,6] (see include/dg.h).
+    States are torch CUDA tensors [E, 4, (k+1)^3] of the solver's dtype.
+    """
+
+    def __init__(self, mesh, k, prec=DG_FP64, alpha=1.0, rho=None, c=None, stream=None):
+        import torch
+        self.lib = load_library()
+        self.k, self.n, self.prec = int(k), int(k) + 1, int(prec)
+        self.E = int(mesh["n_elem"])
+        self.dtype = torch.float64 if self.prec == DG_FP64 else torch.float32
+        self._nodes = np.ascontiguousarray(mesh["nodes"], np.float64)
+        self._nbr = np.ascontiguousarray(mesh["nbr"], np.int32)
+        self._nbf = np.ascontiguousarray(mesh["nbr_face"], np.int8)
+        self._ori = np.ascontiguousarray(mesh["orient"], np.int8)
+        desc = MeshDesc(self.E, int(mesh["geom_degree"]),
+                        self._nodes.ctypes.data_as(C.POINTER(C.c_double)),
+                        self._nbr.ctypes.data_as(C.POINTER(C.c_int32)),
+                        self._nbf.ctypes.data_as(C.POINTER(C.c_int8)),
+                        self._ori.ctypes.data_as(C.POINTER(C.c_int8)))
+        ctx = C.c_void_p()
+        rc = self.lib.dg_mesh_setup(C.byref(desc), self.k, self.prec, float(alpha),
+                                    _stream(stream), C.byref(ctx))
+        if rc != 0:
+            raise DGError(rc, self.lib.dg_last_error(None).decode())
+        self.ctx = ctx
+        if rho is not None or c is not None:
+            self.set_coefficients(rho, c, stream)
+
+    def _check(self, rc):
+        if rc != 0:
+            raise DGError(rc, self.lib.dg_last_error(self.ctx).decode())
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.dg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- state helpers -------------------------------------------------
+    def empty_state(self):
+        import torch
+        return torch.empty((self.E, 4, self.n ** 3), dtype=self.dtype, device="cuda")
+
+    def to_device(self, U):
+        import torch
+        return torch.as_tensor(np.ascontiguousarray(U)).to(device="cuda", dtype=self.dtype).contiguous()
+
+    def _state(self, U):
+        import torch
+        if not (isinstance(U, torch.Tensor) and U.is_cuda and U.dtype == self.dtype and U.is_contiguous()
+                and U.numel() == self.E * 4 * self.n ** 3):
+            raise DGError(-1, "state must be a contiguous CUDA tensor [E,4,(k+1)^3] of the solver dtype")
+        return _ptr(U)
+
+    # --- C ABI calls ------------------------------------------------------
+    def set_coefficients(self, rho, c, stream=None):
+        rho = np.ascontiguousarray(rho, np.float64).reshape(-1)
+        c = np.ascontiguousarray(c, np.float64).reshape(-1)
+        self._check(self.lib.dg_set_coefficients(
+            self.ctx, rho.ctypes.data_as(C.POINTER(C.c_double)),
+            c.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
+
+    def apply(self, U, R=None, stream=None):
+        R = self.empty_state() if R is None else R
+        self._check(self.lib.dg_apply_operator(self.ctx, self._state(U), self._state(R), _stream(stream)))
+        return R
+
+    def step_lsrk(self, U, dt, nsteps, stream=None):
+        self._check(self.lib.dg_step_lsrk(self.ctx, self._state(U), float(dt), int(nsteps), _stream(stream)))
+        return U
+
+    def step_ader(self, U, dt, nsteps, reduce_every=2, stream=None):
+        self._check(self.lib.dg_step_ader(self.ctx, self._state(U), float(dt), int(nsteps),
+                                          int(reduce_every), _stream(stream)))
+        return U
+
+    def tck(self, U, dt, reduce_every=2, out=None, stream=None):
+        out = self.empty_state() if out is None else out
+        self._check(self.lib.dg_tck(self.ctx, self._state(U), self._state(out), float(dt),
+                                    int(reduce_every), _stream(stream)))
+        return out
+
+    def energy(self, U, stream=None):
+        v = C.c_double()
+        self._check(self.lib.dg_energy(self.ctx, self._state(U), C.byref(v), _stream(stream)))
+        return v.value
+
+    def norms(self, A, B=None, stream=None):
+        aa, dd = C.c_double(), C.c_double()
+        self._check(self.lib.dg_norms(self.ctx, self._state(A), None if B is None else self._state(B),
+                                      C.byref(aa), C.byref(dd), _stream(stream)))
+        return aa.value, dd.value
+
+    def solve_host(self, method, U_host, U_out_host, dt, nsteps, reduce_every=2, stream=None):
+        """method 0 = LSRK, 1 = ADER; host buffers (torch CPU tensors, ideally pinned)."""
+        self._check(self.lib.dg_solve_host(self.ctx, int(method), _ptr(U_host), _ptr(U_out_host),
+                                           float(dt), int(nsteps), int(reduce_every), _stream(stream)))
+        return U_out_host
+
+    def info(self):
+        E, k, p, b = C.c_int32(), C.c_int32(), C.c_int32(), C.c_size_t()
+        self._check(self.lib.dg_info(self.ctx, C.byref(E), C.byref(k), C.byref(p), C.byref(b)))
+        return {"n_elem": E.value, "k": k.value, "prec": p.value, "state_bytes": b.value}
+
+    def device_bytes(self):
+        return int(self.lib.dg_device_bytes(self.ctx))
+
+    def launch_count(self):
+        return int(self.lib.dg_launch_count(self.ctx))

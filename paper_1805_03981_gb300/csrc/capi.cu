@@ -1,0 +1,667 @@
+// C ABI of the solver (include/dg.h): contexts, validation, dispatch and the
+// time-stepping drivers.  All arithmetic of the hot path runs in the kernels
+// of dg_kernels.cuh and setup.cu; this file only moves pointers and sizes.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "dg_internal.h"
+#include "dg_kernels.cuh"
+
+using namespace dg;
+
+namespace {
+
+// Five-stage fourth-order 2N-storage Runge-Kutta (Carpenter & Kennedy, 1994).
+const double kLsrkA[5] = {0.0, -567301805773.0 / 1357537059087.0,
+                          -2404267990393.0 / 2016746695238.0,
+                          -3550918686646.0 / 2091501179385.0,
+                          -1275806237668.0 / 842570457699.0};
+const double kLsrkB[5] = {1432997174477.0 / 9575080441755.0,
+                          5161836677717.0 / 13612068292357.0,
+                          1720146321549.0 / 2090206949498.0,
+                          3134564353537.0 / 4481467310338.0,
+                          2277821191437.0 / 14882151754819.0};
+
+std::mutex g_mu;
+KernelTable g_kt;
+bool g_kt_ready = false;
+HostTables g_tab;
+float g_tab_f[DG_TAB_LEN];
+unsigned long long g_dev_ready = 0;  // bit per device with uploaded tables
+thread_local std::string g_setup_err;
+
+int init_device(int dev, std::string* err) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_kt_ready) {
+    std::memset(&g_kt, 0, sizeof(g_kt));
+    build_tables(&g_tab);
+    for (int i = 0; i < DG_TAB_LEN; ++i) g_tab_f[i] = (float)g_tab.tab[i];
+    register_f64_lo(&g_kt);
+    register_f64_hi(&g_kt);
+    register_f32_lo(&g_kt);
+    register_f32_hi(&g_kt);
+    g_kt_ready = true;
+  }
+  if (dev < 0 || dev >= 64) {
+    *err = "device index out of range";
+    return DG_EINVAL;
+  }
+  if (!(g_dev_ready >> dev & 1ull)) {
+    int (*up[4])(const double*, const float*) = {upload_f64_lo, upload_f64_hi, upload_f32_lo,
+                                                  upload_f32_hi};
+    for (int i = 0; i < 4; ++i) {
+      const int e = up[i](g_tab.tab, g_tab_f);
+      if (e) {
+        cudaGetLastError();
+        *err = std::string("kernel set-up (constant tables / shared memory limits) failed: ") +
+               cudaGetErrorString((cudaError_t)e);
+        return DG_ECUDA;
+      }
+    }
+    g_dev_ready |= 1ull << dev;
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+struct dg_ctx {
+  int dev = 0;
+  int E = 0, k = 0, n = 0, q = 0, prec = 0;
+  double alpha = 1.0;
+  size_t rsize = 8;
+  int32_t* nbr = nullptr;
+  int8_t* nbr_face = nullptr;
+  int8_t* orient = nullptr;
+  double* nodes = nullptr;
+  double* rho = nullptr;
+  double* c = nullptr;
+  double* pts = nullptr;
+  double* xq = nullptr;
+  int* bad = nullptr;
+  void* geoA = nullptr;
+  void* geoM = nullptr;
+  void* geoF = nullptr;
+  void* geoT = nullptr;
+  int tstride = 0;
+  void* U2 = nullptr;    // LSRK ping-pong state
+  void* dU = nullptr;    // LSRK register
+  void* Ubar = nullptr;  // ADER predictor
+  void* Uh = nullptr;    // state for dg_solve_host
+  double* partial = nullptr;
+  int partial_cap = 0;
+  size_t dev_bytes = 0;
+  uint64_t launches = 0;
+  int epb_op = 1, epb_tck = 1, epb_en = 1;
+  std::vector<void*> allocs;
+  std::string err;
+
+  size_t state_elems() const { return (size_t)E * 4 * n * n * n; }
+  size_t state_bytes() const { return state_elems() * rsize; }
+
+  int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    err = buf;
+    return code;
+  }
+  int cuda_fail(cudaError_t e, const char* what) {
+    return fail(DG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+  }
+  template <typename T>
+  int alloc(T** p, size_t bytes, const char* what) {
+    void* v = nullptr;
+    cudaError_t e = cudaMalloc(&v, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DG_ENOMEM, "cudaMalloc(%zu) for %s failed: %s", bytes, what, cudaGetErrorString(e));
+    }
+    allocs.push_back(v);
+    dev_bytes += bytes;
+    *p = static_cast<T*>(v);
+    return DG_OK;
+  }
+  ~dg_ctx() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(dev);
+    for (void* p : allocs) cudaFree(p);
+    cudaSetDevice(cur);
+  }
+};
+
+namespace {
+
+#define DG_CK(call, what)                              \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, what); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline cudaStream_t S(uintptr_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int orient_map(int o, int n, int i, int j, int* ip, int* jp) {
+  const int u = (o & 1) ? j : i, v = (o & 1) ? i : j;
+  *ip = (o & 2) ? n - 1 - u : u;
+  *jp = (o & 4) ? n - 1 - v : v;
+  return 0;
+}
+
+int validate_mesh(const dg_mesh_desc* m, std::string* err) {
+  char buf[256];
+  const int E = m->n_elem;
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 6; ++f) {
+      const int en = m->nbr[e * 6 + f];
+      if (en < -1 || en >= E) {
+        snprintf(buf, sizeof buf, "nbr[%d][%d] = %d out of range", e, f, en);
+        *err = buf;
+        return DG_EMESH;
+      }
+      if (en < 0) continue;
+      const int fn = m->nbr_face[e * 6 + f], o = m->orient[e * 6 + f];
+      if (fn < 0 || fn >= 6 || o < 0 || o >= 8) {
+        snprintf(buf, sizeof buf, "nbr_face/orient of (%d,%d) out of range", e, f);
+        *err = buf;
+        return DG_EMESH;
+      }
+      if (m->nbr[en * 6 + fn] != e || m->nbr_face[en * 6 + fn] != f) {
+        snprintf(buf, sizeof buf, "face (%d,%d) -> (%d,%d) is not reciprocated", e, f, en, fn);
+        *err = buf;
+        return DG_EMESH;
+      }
+      const int ob = m->orient[en * 6 + fn];
+      if (ob < 0 || ob >= 8) {
+        *err = "orient out of range";
+        return DG_EMESH;
+      }
+      for (int j = 0; j < 3; ++j)
+        for (int i = 0; i < 3; ++i) {
+          int i1, j1, i2, j2;
+          orient_map(o, 3, i, j, &i1, &j1);
+          orient_map(ob, 3, i1, j1, &i2, &j2);
+          if (i2 != i || j2 != j) {
+            snprintf(buf, sizeof buf, "orientation codes of face (%d,%d) and (%d,%d) are not inverse",
+                     e, f, en, fn);
+            *err = buf;
+            return DG_EMESH;
+          }
+        }
+    }
+  return DG_OK;
+}
+
+int pick_epb(int n, int bytes_per_elem, int target_threads) {
+  int epb = target_threads / (n * n);
+  if (epb < 1) epb = 1;
+  const int smem_lim = 200 * 1024;
+  while (epb > 1 && epb * bytes_per_elem > smem_lim) --epb;
+  return epb;
+}
+
+int run_setup(dg_ctx* ctx, cudaStream_t st) {
+  SetupParams P;
+  P.E = ctx->E;
+  P.n = ctx->n;
+  P.q = ctx->q;
+  P.alpha = ctx->alpha;
+  P.nodes = ctx->nodes;
+  P.rho = ctx->rho;
+  P.c = ctx->c;
+  P.nbr = ctx->nbr;
+  P.nbr_face = ctx->nbr_face;
+  P.orient = ctx->orient;
+  P.pts = ctx->pts;
+  P.xq = ctx->xq;
+  P.geoA = ctx->geoA;
+  P.geoM = ctx->geoM;
+  P.geoF = ctx->geoF;
+  P.geoT = ctx->geoT;
+  P.tstride = ctx->tstride;
+  P.prec = ctx->prec;
+  P.bad = ctx->bad;
+  DG_CK(cudaMemsetAsync(ctx->bad, 0, sizeof(int), st), "memset");
+  DG_CK(launch_setup(P, st), "setup kernel launch");
+  ctx->launches++;
+  int bad = 0;
+  DG_CK(cudaMemcpyAsync(&bad, ctx->bad, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
+  DG_CK(cudaStreamSynchronize(st), "setup kernel");
+  if (bad) return ctx->fail(DG_EMESH, "non-positive Jacobian determinant in the mesh");
+  return DG_OK;
+}
+
+OpParams op_params(const dg_ctx* ctx) {
+  OpParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.nbr = ctx->nbr;
+  p.nbr_face = ctx->nbr_face;
+  p.orient = ctx->orient;
+  p.geoA = ctx->geoA;
+  p.geoM = ctx->geoM;
+  p.geoF = ctx->geoF;
+  p.E = ctx->E;
+  return p;
+}
+
+int launch_op(dg_ctx* ctx, const OpParams& p, int epi, cudaStream_t st) {
+  OpFn fn = g_kt.op[ctx->prec][ctx->n];
+  DG_CK(fn(p, epi, ctx->epb_op, st), "operator kernel launch");
+  ctx->launches++;
+  return DG_OK;
+}
+
+int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaStream_t st) {
+  TckParams p;
+  std::memset(&p, 0, sizeof(p));
+  p.U = U;
+  p.Ubar = Ubar;
+  p.geoT = ctx->geoT;
+  p.geoT_stride = ctx->tstride;
+  p.E = ctx->E;
+  double fact = 1.0;
+  for (int j = 0; j <= ctx->n; ++j) {  // dt^{j+1} / (j+1)!
+    fact *= (j + 1);
+    p.coef[j] = std::pow(dt, j + 1) / fact;
+  }
+  DG_CK(g_kt.tck[ctx->prec][ctx->n](p, red, ctx->epb_tck, st), "predictor kernel launch");
+  ctx->launches++;
+  return DG_OK;
+}
+
+int ensure(dg_ctx* ctx, void** p, const char* what) {
+  if (*p) return DG_OK;
+  return ctx->alloc(p, ctx->state_bytes(), what);
+}
+
+int check_state_ptr(dg_ctx* ctx, const void* p, const char* what) {
+  if (!p) return ctx->fail(DG_EINVAL, "%s is NULL", what);
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx->fail(DG_EINVAL, "%s is not a device pointer", what);
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    return ctx->fail(DG_EINVAL, "%s is not device memory", what);
+  return DG_OK;
+}
+
+int lsrk_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st) {
+  int rc;
+  if ((rc = ensure(ctx, &ctx->U2, "LSRK state"))) return rc;
+  if ((rc = ensure(ctx, &ctx->dU, "LSRK register"))) return rc;
+  OpParams p = op_params(ctx);
+  void* cur = U;
+  void* other = ctx->U2;
+  for (int s = 0; s < nsteps; ++s)
+    for (int st5 = 0; st5 < 5; ++st5) {
+      p.U = cur;
+      p.Uadd = cur;
+      p.out = other;
+      p.dU = ctx->dU;
+      p.cA = kLsrkA[st5];
+      p.cB = kLsrkB[st5];
+      p.dt = dt;
+      p.first = st5 == 0;
+      if ((rc = launch_op(ctx, p, EPI_LSRK, st))) return rc;
+      void* t = cur;
+      cur = other;
+      other = t;
+    }
+  if (cur != U) DG_CK(cudaMemcpyAsync(U, cur, ctx->state_bytes(), cudaMemcpyDeviceToDevice, st), "copy");
+  return DG_OK;
+}
+
+int ader_steps(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_t st) {
+  int rc;
+  if ((rc = ensure(ctx, &ctx->Ubar, "ADER predictor"))) return rc;
+  OpParams p = op_params(ctx);
+  for (int s = 0; s < nsteps; ++s) {
+    if ((rc = launch_tck(ctx, U, ctx->Ubar, dt, red, st))) return rc;
+    p.U = ctx->Ubar;
+    p.Uadd = U;
+    p.out = U;
+    if ((rc = launch_op(ctx, p, EPI_ADD, st))) return rc;
+  }
+  return DG_OK;
+}
+
+// Sums of squares with a fixed launch shape and summation order.
+template <typename Real>
+__global__ void sumsq_kernel(const Real* A, const Real* B, size_t n, double* part) {
+  double saa = 0.0, sdd = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double a = A[i];
+    saa += a * a;
+    if (B) {
+      const double d = a - (double)B[i];
+      sdd += d * d;
+    }
+  }
+  __shared__ double r1[256], r2[256];
+  r1[threadIdx.x] = saa;
+  r2[threadIdx.x] = sdd;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      r1[threadIdx.x] += r1[threadIdx.x + w];
+      r2[threadIdx.x] += r2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = r1[0];
+    part[2 * blockIdx.x + 1] = r2[0];
+  }
+}
+
+int ensure_partial(dg_ctx* ctx, int n) {
+  if (ctx->partial_cap >= n) return DG_OK;
+  int rc = ctx->alloc(&ctx->partial, sizeof(double) * n, "partial sums");
+  if (rc) return rc;
+  ctx->partial_cap = n;
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dg_strerror(int s) {
+  switch (s) {
+    case DG_OK: return "ok";
+    case DG_EINVAL: return "invalid argument";
+    case DG_ENOMEM: return "out of memory";
+    case DG_ECUDA: return "CUDA error";
+    case DG_EUNSUPPORTED: return "unsupported";
+    case DG_EAGAIN: return "not finished";
+    case DG_ETIMEOUT: return "timed out";
+    case DG_EMESH: return "invalid mesh";
+    default: return "unknown status";
+  }
+}
+
+const char* dg_last_error(const dg_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_setup_err.c_str();
+}
+
+int dg_mesh_setup(const dg_mesh_desc* m, int k, int prec, double alpha, uintptr_t stream,
+                  dg_ctx** out) {
+  if (!out) return DG_EINVAL;
+  *out = nullptr;
+  g_setup_err.clear();
+  if (!m || !m->nodes || !m->nbr || !m->nbr_face || !m->orient || m->n_elem < 1) {
+    g_setup_err = "NULL mesh array or n_elem < 1";
+    return DG_EINVAL;
+  }
+  if (k < 1 || k > DG_KMAX) {
+    g_setup_err = "degree k outside [1, DG_KMAX]";
+    return DG_EUNSUPPORTED;
+  }
+  if (m->geom_degree < 1 || m->geom_degree > DG_NMAX) {
+    g_setup_err = "geometry degree outside [1, 8]";
+    return DG_EUNSUPPORTED;
+  }
+  if (prec != DG_FP64 && prec != DG_FP32) {
+    g_setup_err = "precision must be DG_FP64 or DG_FP32";
+    return DG_EINVAL;
+  }
+  if (!(alpha >= 0.0 && alpha <= 1.0)) {
+    g_setup_err = "flux_alpha outside [0, 1]";
+    return DG_EINVAL;
+  }
+  int rc = validate_mesh(m, &g_setup_err);
+  if (rc) return rc;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    g_setup_err = "no CUDA device";
+    return DG_ECUDA;
+  }
+  if ((rc = init_device(dev, &g_setup_err))) return rc;
+
+  dg_ctx* ctx = new (std::nothrow) dg_ctx();
+  if (!ctx) return DG_ENOMEM;
+  ctx->dev = dev;
+  ctx->E = m->n_elem;
+  ctx->k = k;
+  ctx->n = k + 1;
+  ctx->q = m->geom_degree;
+  ctx->prec = prec;
+  ctx->alpha = alpha;
+  ctx->rsize = prec == DG_FP64 ? 8 : 4;
+  const int E = ctx->E, n = ctx->n, n3 = n * n * n, qc = ctx->q + 1;
+  cudaStream_t st = S(stream);
+  auto bail = [&](int code) {
+    g_setup_err = ctx->err;
+    delete ctx;
+    return code;
+  };
+  ctx->tstride = tck_geo_stride(n);
+  const size_t rs = ctx->rsize;
+  if ((rc = ctx->alloc(&ctx->nbr, sizeof(int32_t) * 6 * E, "nbr")) ||
+      (rc = ctx->alloc(&ctx->nbr_face, 6 * (size_t)E, "nbr_face")) ||
+      (rc = ctx->alloc(&ctx->orient, 6 * (size_t)E, "orient")) ||
+      (rc = ctx->alloc(&ctx->nodes, sizeof(double) * 3 * qc * qc * qc * (size_t)E, "nodes")) ||
+      (rc = ctx->alloc(&ctx->rho, sizeof(double) * n3 * (size_t)E, "rho")) ||
+      (rc = ctx->alloc(&ctx->c, sizeof(double) * n3 * (size_t)E, "c")) ||
+      (rc = ctx->alloc(&ctx->pts, sizeof(double) * 3 * DG_PTS_LEN, "points")) ||
+      (rc = ctx->alloc(&ctx->xq, sizeof(double) * (DG_NMAX + 2), "geometry points")) ||
+      (rc = ctx->alloc(&ctx->bad, sizeof(int), "flag")) ||
+      (rc = ctx->alloc(&ctx->geoA, rs * 9 * n3 * (size_t)E, "cell metric")) ||
+      (rc = ctx->alloc(&ctx->geoM, rs * 2 * n3 * (size_t)E, "mass diagonal")) ||
+      (rc = ctx->alloc(&ctx->geoF, rs * 36 * n * n * (size_t)E, "face data")) ||
+      (rc = ctx->alloc(&ctx->geoT, rs * (size_t)ctx->tstride * E, "predictor geometry")))
+    return bail(rc);
+  std::vector<double> hpts(3 * DG_PTS_LEN);
+  std::memcpy(hpts.data(), g_tab.xg, sizeof(double) * DG_PTS_LEN);
+  std::memcpy(hpts.data() + DG_PTS_LEN, g_tab.wg, sizeof(double) * DG_PTS_LEN);
+  std::memcpy(hpts.data() + 2 * DG_PTS_LEN, g_tab.xgl, sizeof(double) * DG_PTS_LEN);
+  std::vector<double> hxq(DG_NMAX + 2, 0.0);
+  gauss_lobatto(qc, hxq.data());
+  std::vector<double> ones((size_t)n3 * E, 1.0);
+  cudaError_t ce;
+#define DG_UP(dst, src, bytes)                                                            \
+  if ((ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) { \
+    ctx->cuda_fail(ce, "upload");                                                         \
+    return bail(DG_ECUDA);                                                                \
+  }
+  DG_UP(ctx->nbr, m->nbr, sizeof(int32_t) * 6 * E);
+  DG_UP(ctx->nbr_face, m->nbr_face, 6 * (size_t)E);
+  DG_UP(ctx->orient, m->orient, 6 * (size_t)E);
+  DG_UP(ctx->nodes, m->nodes, sizeof(double) * 3 * qc * qc * qc * (size_t)E);
+  DG_UP(ctx->rho, ones.data(), sizeof(double) * n3 * (size_t)E);
+  DG_UP(ctx->c, ones.data(), sizeof(double) * n3 * (size_t)E);
+  DG_UP(ctx->pts, hpts.data(), sizeof(double) * 3 * DG_PTS_LEN);
+  DG_UP(ctx->xq, hxq.data(), sizeof(double) * (DG_NMAX + 2));
+#undef DG_UP
+  const int pi = ctx->prec;
+  ctx->epb_op = pick_epb(n, g_kt.smem[pi][n](0, 2), 128);
+  ctx->epb_tck = pick_epb(n, g_kt.smem[pi][n](1, 2), 128);
+  ctx->epb_en = pick_epb(n, g_kt.smem[pi][n](2, 2), 128);
+  if ((rc = run_setup(ctx, st))) return bail(rc);
+  *out = ctx;
+  return DG_OK;
+}
+
+int dg_set_coefficients(dg_ctx* ctx, const double* rho, const double* c, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  if (!rho || !c) return ctx->fail(DG_EINVAL, "NULL coefficient array");
+  const size_t cnt = (size_t)ctx->E * ctx->n * ctx->n * ctx->n;
+  for (size_t i = 0; i < cnt; ++i)
+    if (!(rho[i] > 0.0) || !(c[i] > 0.0) || !std::isfinite(rho[i]) || !std::isfinite(c[i]))
+      return ctx->fail(DG_EINVAL, "coefficients must be positive and finite (index %zu)", i);
+  DeviceGuard g(ctx->dev);
+  cudaStream_t st = S(stream);
+  DG_CK(cudaMemcpyAsync(ctx->rho, rho, sizeof(double) * cnt, cudaMemcpyHostToDevice, st), "upload rho");
+  DG_CK(cudaMemcpyAsync(ctx->c, c, sizeof(double) * cnt, cudaMemcpyHostToDevice, st), "upload c");
+  return run_setup(ctx, st);
+}
+
+int dg_apply_operator(dg_ctx* ctx, const void* U, void* R, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  int rc;
+  if ((rc = check_state_ptr(ctx, U, "U")) || (rc = check_state_ptr(ctx, R, "R"))) return rc;
+  const char* u0 = static_cast<const char*>(U);
+  const char* r0 = static_cast<const char*>(R);
+  const size_t b = ctx->state_bytes();
+  if (u0 < r0 + b && r0 < u0 + b) return ctx->fail(DG_EINVAL, "U and R overlap");
+  DeviceGuard g(ctx->dev);
+  OpParams p = op_params(ctx);
+  p.U = U;
+  p.out = R;
+  return launch_op(ctx, p, EPI_WRITE, S(stream));
+}
+
+int dg_step_lsrk(dg_ctx* ctx, void* U, double dt, int32_t nsteps, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  int rc;
+  if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0)
+    return ctx->fail(DG_EINVAL, "need dt > 0 and nsteps >= 0");
+  DeviceGuard g(ctx->dev);
+  return lsrk_steps(ctx, U, dt, nsteps, S(stream));
+}
+
+int dg_step_ader(dg_ctx* ctx, void* U, double dt, int32_t nsteps, int32_t red, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  int rc;
+  if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0)
+    return ctx->fail(DG_EINVAL, "need dt > 0 and nsteps >= 0");
+  if (red != 0 && red != 2)
+    return ctx->fail(DG_EUNSUPPORTED, "reduce_every must be 0 or 2 in this build");
+  DeviceGuard g(ctx->dev);
+  return ader_steps(ctx, U, dt, nsteps, red, S(stream));
+}
+
+int dg_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int32_t red, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  int rc;
+  if ((rc = check_state_ptr(ctx, U, "U")) || (rc = check_state_ptr(ctx, Ubar, "Ubar"))) return rc;
+  if (red != 0 && red != 2)
+    return ctx->fail(DG_EUNSUPPORTED, "reduce_every must be 0 or 2 in this build");
+  if (!std::isfinite(dt)) return ctx->fail(DG_EINVAL, "dt not finite");
+  DeviceGuard g(ctx->dev);
+  return launch_tck(ctx, U, Ubar, dt, red, S(stream));
+}
+
+int dg_energy(dg_ctx* ctx, const void* U, double* out, uintptr_t stream) {
+  if (!ctx || !out) return DG_EINVAL;
+  int rc;
+  if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
+  DeviceGuard g(ctx->dev);
+  const int blocks = (ctx->E + ctx->epb_en - 1) / ctx->epb_en;
+  if ((rc = ensure_partial(ctx, blocks))) return rc;
+  EnergyParams p;
+  p.U = U;
+  p.geoM = ctx->geoM;
+  p.partial = ctx->partial;
+  p.E = ctx->E;
+  cudaStream_t st = S(stream);
+  DG_CK(g_kt.energy[ctx->prec][ctx->n](p, ctx->epb_en, st), "energy kernel launch");
+  ctx->launches++;
+  std::vector<double> h(blocks);
+  DG_CK(cudaMemcpyAsync(h.data(), ctx->partial, sizeof(double) * blocks, cudaMemcpyDeviceToHost, st),
+        "copy partials");
+  DG_CK(cudaStreamSynchronize(st), "energy");
+  double s = 0.0;
+  for (int i = 0; i < blocks; ++i) s += h[i];
+  *out = s;
+  return DG_OK;
+}
+
+int dg_norms(dg_ctx* ctx, const void* A, const void* B, double* aa, double* dd, uintptr_t stream) {
+  if (!ctx || !aa) return DG_EINVAL;
+  int rc;
+  if ((rc = check_state_ptr(ctx, A, "A"))) return rc;
+  if (B && (rc = check_state_ptr(ctx, B, "B"))) return rc;
+  DeviceGuard g(ctx->dev);
+  const int blocks = 1024;
+  if ((rc = ensure_partial(ctx, 2 * blocks))) return rc;
+  cudaStream_t st = S(stream);
+  const size_t cnt = ctx->state_elems();
+  if (ctx->prec == DG_FP64)
+    sumsq_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(A),
+                                                 static_cast<const double*>(B), cnt, ctx->partial);
+  else
+    sumsq_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(A),
+                                                static_cast<const float*>(B), cnt, ctx->partial);
+  DG_CK(cudaGetLastError(), "norm kernel launch");
+  ctx->launches++;
+  std::vector<double> h(2 * blocks);
+  DG_CK(cudaMemcpyAsync(h.data(), ctx->partial, sizeof(double) * 2 * blocks, cudaMemcpyDeviceToHost, st),
+        "copy partials");
+  DG_CK(cudaStreamSynchronize(st), "norms");
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = 0; i < blocks; ++i) {
+    s1 += h[2 * i];
+    s2 += h[2 * i + 1];
+  }
+  *aa = s1;
+  if (dd) *dd = s2;
+  return DG_OK;
+}
+
+int dg_solve_host(dg_ctx* ctx, int method, const void* Uh, void* Uout, double dt, int32_t nsteps,
+                  int32_t red, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  if (!Uh || !Uout) return ctx->fail(DG_EINVAL, "NULL host buffer");
+  if (method != 0 && method != 1) return ctx->fail(DG_EINVAL, "method must be 0 (LSRK) or 1 (ADER)");
+  if (!(dt > 0.0) || nsteps < 0) return ctx->fail(DG_EINVAL, "need dt > 0 and nsteps >= 0");
+  if (method == 1 && red != 0 && red != 2)
+    return ctx->fail(DG_EUNSUPPORTED, "reduce_every must be 0 or 2 in this build");
+  DeviceGuard g(ctx->dev);
+  int rc;
+  if ((rc = ensure(ctx, &ctx->Uh, "host-solve state"))) return rc;
+  cudaStream_t st = S(stream);
+  const size_t b = ctx->state_bytes();
+  DG_CK(cudaMemcpyAsync(ctx->Uh, Uh, b, cudaMemcpyHostToDevice, st), "copy in");
+  rc = method == 0 ? lsrk_steps(ctx, ctx->Uh, dt, nsteps, st)
+                   : ader_steps(ctx, ctx->Uh, dt, nsteps, red, st);
+  if (rc) return rc;
+  DG_CK(cudaMemcpyAsync(Uout, ctx->Uh, b, cudaMemcpyDeviceToHost, st), "copy out");
+  DG_CK(cudaStreamSynchronize(st), "solve");
+  return DG_OK;
+}
+
+int dg_info(const dg_ctx* ctx, int32_t* E, int32_t* k, int32_t* prec, size_t* bytes) {
+  if (!ctx) return DG_EINVAL;
+  if (E) *E = ctx->E;
+  if (k) *k = ctx->k;
+  if (prec) *prec = ctx->prec;
+  if (bytes) *bytes = ctx->state_bytes();
+  return DG_OK;
+}
+
+size_t dg_device_bytes(const dg_ctx* ctx) { return ctx ? ctx->dev_bytes : 0; }
+
+uint64_t dg_launch_count(const dg_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+void dg_destroy(dg_ctx* ctx) { delete ctx; }
+
+}  // extern "C"

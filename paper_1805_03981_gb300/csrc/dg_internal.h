@@ -1,0 +1,61 @@
+// Internal declarations shared by the C ABI (capi.cu), the set-up kernel and
+// the kernel instantiation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tables.h"
+
+namespace dg {
+
+struct OpParams;
+struct TckParams;
+struct EnergyParams;
+
+struct SetupParams {
+  int E, n, q;
+  double alpha;
+  const double* nodes;  // [E][(q+1)^3][3]
+  const double* rho;    // [E][n^3]
+  const double* c;      // [E][n^3]
+  const int32_t* nbr;
+  const int8_t* nbr_face;
+  const int8_t* orient;
+  const double* pts;  // [3][DG_PTS_LEN]: Gauss points, weights, GL points
+  const double* xq;   // GL points of the geometry degree (q + 1 of them)
+  void* geoA;
+  void* geoM;
+  void* geoF;
+  void* geoT;
+  int tstride;
+  int prec;  // 0 double, 1 float
+  int* bad;  // set to 1 if det J <= 0 anywhere
+};
+
+cudaError_t launch_setup(const SetupParams& P, cudaStream_t st);
+
+typedef cudaError_t (*OpFn)(const OpParams& p, int epi, int epb, cudaStream_t st);
+typedef cudaError_t (*TckFn)(const TckParams& p, int red, int epb, cudaStream_t st);
+typedef cudaError_t (*EnergyFn)(const EnergyParams& p, int epb, cudaStream_t st);
+typedef int (*SmemFn)(int which, int red);  // bytes per element
+
+struct KernelTable {
+  OpFn op[2][DG_NMAX + 1];
+  TckFn tck[2][DG_NMAX + 1];
+  EnergyFn energy[2][DG_NMAX + 1];
+  SmemFn smem[2][DG_NMAX + 1];
+};
+
+// Each kernel translation unit registers its instantiations and uploads the
+// constant tables into its own copy (returns 0 or a cudaError_t value).
+void register_f64_lo(KernelTable* t);
+void register_f64_hi(KernelTable* t);
+void register_f32_lo(KernelTable* t);
+void register_f32_hi(KernelTable* t);
+int upload_f64_lo(const double* d, const float* f);
+int upload_f64_hi(const double* d, const float* f);
+int upload_f32_lo(const double* d, const float* f);
+int upload_f32_hi(const double* d, const float* f);
+
+}  // namespace dg

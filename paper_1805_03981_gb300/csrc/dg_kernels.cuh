@@ -1,0 +1,688 @@
+// Device kernels of the matrix-free DG acoustic solver (sm_103a).
+//
+// Work decomposition: a thread block owns EPB consecutive elements and gives
+// each element (k+1)^2 threads.  Sum-factorised 1D contractions (Sec. 3,
+// "tensor product kernel") are done by letting every thread own one line of
+// the element tile along the contraction direction: it loads the line from
+// shared memory into registers, multiplies by the 1D matrix whose entries
+// sit in constant memory (uniform across the warp), and writes the line back.
+// Line ownership rotates between directions through shared memory.
+//
+// Tile index convention: node (x, y, z) of an n^3 tile is x + n y + n^2 z.
+// A thread with in-element index t = a + n b owns
+//   direction 0 (x): the line (y, z) = (a, b)
+//   direction 1 (y): the line (x, z) = (a, b)
+//   direction 2 (z): the line (x, y) = (a, b)
+// and in each case (a, b) are also the face-point indices (i, j) of the two
+// faces normal to that direction.  Per-point geometry used in a direction-d
+// phase is stored "line-major": point (line t, position s) at t + n^2 s, so
+// that a warp's loads are contiguous.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tables.h"
+
+// Each translation unit has its own copy of the constant tables (no
+// relocatable device code); the upload_* function of each kernel
+// instantiation unit fills it.
+static __constant__ double c_tab_d[DG_TAB_LEN];
+static __constant__ float c_tab_f[DG_TAB_LEN];
+
+
+namespace dg {
+
+enum { EPI_WRITE = 0, EPI_LSRK = 1, EPI_ADD = 2 };
+
+template <typename Real>
+__device__ __forceinline__ Real tab(int i);
+template <>
+__device__ __forceinline__ double tab<double>(int i) { return c_tab_d[i]; }
+template <>
+__device__ __forceinline__ float tab<float>(int i) { return c_tab_f[i]; }
+
+// out[i] = sum_j M[i][j] in[j];  M is RO x RI at table offset OFF.
+template <typename Real, int OFF, int RO, int RI>
+__device__ __forceinline__ void mv(const Real* in, Real* out) {
+#pragma unroll
+  for (int i = 0; i < RO; ++i) {
+    Real acc = tab<Real>(OFF + i * RI) * in[0];
+#pragma unroll
+    for (int j = 1; j < RI; ++j) acc = fma(tab<Real>(OFF + i * RI + j), in[j], acc);
+    out[i] = acc;
+  }
+}
+
+// out[j] = sum_i M[i][j] in[i];  M is RI x RO at table offset OFF (transpose).
+template <typename Real, int OFF, int RI, int RO>
+__device__ __forceinline__ void mtv(const Real* in, Real* out) {
+#pragma unroll
+  for (int j = 0; j < RO; ++j) {
+    Real acc = tab<Real>(OFF + j) * in[0];
+#pragma unroll
+    for (int i = 1; i < RI; ++i) acc = fma(tab<Real>(OFF + i * RO + j), in[i], acc);
+    out[j] = acc;
+  }
+}
+
+// Base index and stride of the line (a, b) along DIR in an X x Y x Z tile.
+template <int DIR, int X, int Y>
+__device__ __forceinline__ int line_base(int a, int b) {
+  return DIR == 0 ? X * a + X * Y * b : (DIR == 1 ? a + X * Y * b : a + X * b);
+}
+template <int DIR, int X, int Y>
+__host__ __device__ constexpr int line_stride() {
+  return DIR == 0 ? 1 : (DIR == 1 ? X : X * Y);
+}
+
+// Contract an X x Y x Z tile (4 fields, field stride FS_IN) along DIR with
+// the RO x RI matrix at OFF (RI = extent along DIR), writing the result tile
+// (extent RO along DIR, field stride FS_OUT) to dst.  Threads 0..nthr-1 of
+// the element share the lines.  dst may equal src only if RO == RI.
+template <typename Real, int DIR, int X, int Y, int Z, int RO, int OFF, int FS_IN, int FS_OUT,
+          bool ADD = false>
+__device__ __forceinline__ void contract_tile(const Real* src, Real* dst, int t, int nthr,
+                                              Real scale = Real(1)) {
+  constexpr int RI = DIR == 0 ? X : (DIR == 1 ? Y : Z);
+  constexpr int A = DIR == 0 ? Y : X;  // extent of the first line coordinate
+  constexpr int B = DIR == 2 ? Y : Z;  // extent of the second
+  constexpr int OX = DIR == 0 ? RO : X, OY = DIR == 1 ? RO : Y;
+  for (int l = t; l < A * B; l += nthr) {
+    const int a = l % A, b = l / A;
+    const int bi = line_base<DIR, X, Y>(a, b);
+    const int bo = line_base<DIR, OX, OY>(a, b);
+    constexpr int si = line_stride<DIR, X, Y>();
+    constexpr int so = line_stride<DIR, OX, OY>();
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      Real in[RI], out[RO];
+#pragma unroll
+      for (int s = 0; s < RI; ++s) in[s] = src[f * FS_IN + bi + si * s];
+      mv<Real, OFF, RO, RI>(in, out);
+#pragma unroll
+      for (int s = 0; s < RO; ++s) {
+        if (ADD)
+          dst[f * FS_OUT + bo + so * s] += scale * out[s];
+        else
+          dst[f * FS_OUT + bo + so * s] = out[s];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Operator R = -M^-1 K U (Sec. 2.1, Eq. (3)) with fused epilogues.
+// ---------------------------------------------------------------------------
+struct OpParams {
+  const void* U;      // input state, GL basis [E][4][n^3]
+  void* out;          // WRITE: R; ADD / LSRK: updated state
+  const void* Uadd;   // ADD / LSRK: state the update is added to
+  void* dU;           // LSRK register
+  double cA, cB, dt;  // LSRK: dU = cA dU + dt R (cA ignored if first), out = Uadd + cB dU
+  int first;          // LSRK: first stage (dU not read)
+  const int32_t* nbr;
+  const int8_t* nbr_face;
+  const int8_t* orient;
+  const void* geoA;  // [E][3 d][3 i][n^3] line-major per d: w adj(J)_{d i}
+  const void* geoM;  // [E][2][n^3]: rho c^2 / (w detJ), 1 / (rho w detJ)
+  const void* geoF;  // [E][6 f][6][n^2]: nw_x, nw_y, nw_z, Z-/(Z-+Z+), b, c
+  int E;
+};
+
+template <int N>
+__host__ __device__ constexpr int op_smem_per_elem() {
+  return 8 * N * N * N + 24 * N * N;
+}
+
+// Cell and face contributions of the direction-DIR phase along the thread's
+// line: cell test-gradient integration (the collocation derivative
+// transposed applied to the contravariant fluxes) and the lifting of the
+// two faces normal to DIR.  u: Gauss-point values of (p, v) on the line;
+// r: contributions to the Gauss-basis residual along the line.
+template <int N, typename Real, int DIR>
+__device__ __forceinline__ void cell_face_dir(const Real (&u)[4][N], Real (&r)[4][N],
+                                              const Real* __restrict__ gA,
+                                              const Real* __restrict__ gF, const Real* snb,
+                                              int t, int fmask) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  const Real* A0 = gA + (DIR * 3 + 0) * N3 + t;
+  const Real* A1 = gA + (DIR * 3 + 1) * N3 + t;
+  const Real* A2 = gA + (DIR * 3 + 2) * N3 + t;
+  Real F[N];
+  // pressure test: flux sum_i A_{DIR i} v_i
+#pragma unroll
+  for (int s = 0; s < N; ++s)
+    F[s] = fma(__ldg(A0 + N2 * s), u[1][s],
+               fma(__ldg(A1 + N2 * s), u[2][s], __ldg(A2 + N2 * s) * u[3][s]));
+  mtv<Real, OFF_D(N), N, N>(F, r[0]);
+  // velocity tests: flux A_{DIR i} p
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const Real* Ai = i == 0 ? A0 : (i == 1 ? A1 : A2);
+#pragma unroll
+    for (int s = 0; s < N; ++s) F[s] = __ldg(Ai + N2 * s) * u[0][s];
+    mtv<Real, OFF_D(N), N, N>(F, r[1 + i]);
+  }
+  // faces 2 DIR (xi_DIR = -1) and 2 DIR + 1 (xi_DIR = +1)
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    const int f = 2 * DIR + sd;
+    constexpr int LF = OFF_LF(N);
+    Real um[4];
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl) {
+      Real acc = tab<Real>(LF + sd * N) * u[fl][0];
+#pragma unroll
+      for (int s = 1; s < N; ++s) acc = fma(tab<Real>(LF + sd * N + s), u[fl][s], acc);
+      um[fl] = acc;
+    }
+    const Real* fc = gF + f * 6 * N2 + t;
+    const Real nw0 = __ldg(fc), nw1 = __ldg(fc + N2), nw2 = __ldg(fc + 2 * N2);
+    const Real a2 = __ldg(fc + 3 * N2), bb = __ldg(fc + 4 * N2), cc = __ldg(fc + 5 * N2);
+    const Real vnm = fma(nw0, um[1], fma(nw1, um[2], nw2 * um[3]));
+    Real pp, vnp;
+    if ((fmask >> f) & 1) {
+      const Real* nb = snb + f * 4 * N2 + t;
+      pp = nb[0];
+      vnp = fma(nw0, nb[N2], fma(nw1, nb[2 * N2], nw2 * nb[3 * N2]));
+    } else {  // reflecting wall: mirror state
+      pp = um[0];
+      vnp = -vnm;
+    }
+    const Real dp = um[0] - pp, dvn = vnm - vnp;
+    const Real pstar = fma(-a2, dp, fma(bb, dvn, um[0]));  // p*
+    const Real flp = fma(a2, dvn, fma(cc, dp, vnp));        // |J_f| w (v.n)*
+    const Real g0 = nw0 * pstar, g1 = nw1 * pstar, g2 = nw2 * pstar;
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+      const Real l = tab<Real>(LF + sd * N + s);
+      r[0][s] = fma(-l, flp, r[0][s]);
+      r[1][s] = fma(-l, g0, r[1][s]);
+      r[2][s] = fma(-l, g1, r[2][s]);
+      r[3][s] = fma(-l, g2, r[3][s]);
+    }
+  }
+}
+
+template <int N, typename Real, int EPI>
+__global__ void op_kernel(const OpParams p) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int SE = op_smem_per_elem<N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  const int epb = blockDim.x / N2;
+  const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
+  const int a = t % N, b = t / N;
+  const int e0 = blockIdx.x * epb;
+  const int ne = min(epb, p.E - e0);
+  const int e = e0 + le;
+  const bool act = le < ne;
+  Real* su = sm + le * SE;
+  Real* sr = su + 4 * N3;
+  Real* snb = sr + 4 * N3;
+  const Real* __restrict__ U = static_cast<const Real*>(p.U);
+
+  // 1. element tiles, contiguous in memory: flat coalesced copy
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+    const int l = i / (4 * N3);
+    sm[l * SE + (i - l * 4 * N3)] = U[(size_t)e0 * 4 * N3 + i];
+  }
+  // neighbours' GL face nodes, gathered into this element's face coordinates
+  int fmask = 0;
+  if (act) {
+#pragma unroll 1
+    for (int f = 0; f < 6; ++f) {
+      const int en = p.nbr[e * 6 + f];
+      if (en < 0) continue;
+      fmask |= 1 << f;
+      const int fn = p.nbr_face[e * 6 + f], o = p.orient[e * 6 + f];
+      const int uu = (o & 1) ? b : a, vv = (o & 1) ? a : b;
+      const int ip = (o & 2) ? N - 1 - uu : uu, jp = (o & 4) ? N - 1 - vv : vv;
+      const int dn = fn >> 1;
+      int crd[3];
+      crd[dn] = (fn & 1) ? N - 1 : 0;
+      crd[dn == 0 ? 1 : 0] = ip;
+      crd[dn == 2 ? 1 : 2] = jp;
+      const Real* src = U + (size_t)en * 4 * N3 + crd[0] + N * crd[1] + N2 * crd[2];
+#pragma unroll
+      for (int fl = 0; fl < 4; ++fl) snb[(f * 4 + fl) * N2 + t] = src[fl * N3];
+    }
+  }
+  __syncthreads();
+
+  // 2. GL -> G (Sec. 3.1) along z of the tile and along the first tangential
+  //    axis of the neighbour face data
+  if (act) {
+    contract_tile<Real, 2, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+    for (int it = t; it < 6 * N; it += N2) {
+      const int f = it / N, j = it - f * N;
+      if (!((fmask >> f) & 1)) continue;
+#pragma unroll
+      for (int fl = 0; fl < 4; ++fl) {
+        Real in[N], out[N];
+        Real* q = snb + (f * 4 + fl) * N2 + N * j;
+#pragma unroll
+        for (int s = 0; s < N; ++s) in[s] = q[s];
+        mv<Real, OFF_V(N), N, N>(in, out);
+#pragma unroll
+        for (int s = 0; s < N; ++s) q[s] = out[s];
+      }
+    }
+  }
+  __syncthreads();
+  if (act) {
+    contract_tile<Real, 0, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+    for (int it = t; it < 6 * N; it += N2) {
+      const int f = it / N, i = it - f * N;
+      if (!((fmask >> f) & 1)) continue;
+#pragma unroll
+      for (int fl = 0; fl < 4; ++fl) {
+        Real in[N], out[N];
+        Real* q = snb + (f * 4 + fl) * N2 + i;
+#pragma unroll
+        for (int s = 0; s < N; ++s) in[s] = q[N * s];
+        mv<Real, OFF_V(N), N, N>(in, out);
+#pragma unroll
+        for (int s = 0; s < N; ++s) q[N * s] = out[s];
+      }
+    }
+  }
+  __syncthreads();
+
+  const Real* gA = static_cast<const Real*>(p.geoA) + (size_t)e * 9 * N3;
+  const Real* gF = static_cast<const Real*>(p.geoF) + (size_t)e * 36 * N2;
+  const Real* gM = static_cast<const Real*>(p.geoM) + (size_t)e * 2 * N3;
+
+  // 3. y: finish GL -> G along y in registers, then the y cell/face terms
+  if (act) {
+    Real u[4][N], r[4][N];
+    const int base = line_base<1, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl) {
+      Real in[N];
+#pragma unroll
+      for (int s = 0; s < N; ++s) in[s] = su[fl * N3 + base + N * s];
+      mv<Real, OFF_V(N), N, N>(in, u[fl]);
+#pragma unroll
+      for (int s = 0; s < N; ++s) su[fl * N3 + base + N * s] = u[fl][s];
+    }
+    cell_face_dir<N, Real, 1>(u, r, gA, gF, snb, t, fmask);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + N * s] = r[fl][s];
+  }
+  __syncthreads();
+  // 4. x
+  if (act) {
+    Real u[4][N], r[4][N];
+    const int base = line_base<0, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + s];
+    cell_face_dir<N, Real, 0>(u, r, gA, gF, snb, t, fmask);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + s] += r[fl][s];
+  }
+  __syncthreads();
+  // 5. z, then inverse mass (diagonal in G, Sec. 3.1) and G -> GL along z
+  if (act) {
+    Real u[4][N], r[4][N];
+    const int base = line_base<2, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + N2 * s];
+    cell_face_dir<N, Real, 2>(u, r, gA, gF, snb, t, fmask);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+      const Real mp = __ldg(gM + base + N2 * s), mvv = __ldg(gM + N3 + base + N2 * s);
+      r[0][s] = (r[0][s] + sr[base + N2 * s]) * mp;
+#pragma unroll
+      for (int fl = 1; fl < 4; ++fl) r[fl][s] = (r[fl][s] + sr[fl * N3 + base + N2 * s]) * mvv;
+    }
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl) {
+      Real out[N];
+      mv<Real, OFF_VI(N), N, N>(r[fl], out);
+#pragma unroll
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + N2 * s] = out[s];
+    }
+  }
+  __syncthreads();
+  if (act) contract_tile<Real, 0, N, N, N, N, OFF_VI(N), N3, N3>(sr, sr, t, N2);
+  __syncthreads();
+  if (act) contract_tile<Real, 1, N, N, N, N, OFF_VI(N), N3, N3>(sr, sr, t, N2);
+  __syncthreads();
+
+  // 6. epilogue, flat and coalesced over the block's elements
+  Real* __restrict__ out = static_cast<Real*>(p.out);
+  const Real* __restrict__ Uadd = static_cast<const Real*>(p.Uadd);
+  Real* __restrict__ dU = static_cast<Real*>(p.dU);
+  const Real cA = (Real)p.cA, cB = (Real)p.cB, dt = (Real)p.dt;
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+    const int l = i / (4 * N3);
+    const Real R = sm[l * SE + 4 * N3 + (i - l * 4 * N3)];
+    const size_t g = (size_t)e0 * 4 * N3 + i;
+    if (EPI == EPI_WRITE) {
+      out[g] = R;
+    } else if (EPI == EPI_ADD) {
+      out[g] = Uadd[g] + R;
+    } else {
+      const Real d = p.first ? dt * R : fma(cA, dU[g], dt * R);
+      dU[g] = d;
+      out[g] = fma(cB, d, Uadd[g]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Taylor-Cauchy-Kowalevski predictor (Sec. 2.3 Eq. (6), Sec. 3.2 Alg. 2,
+// Sec. 3.3 Alg. 3).
+// ---------------------------------------------------------------------------
+struct TckParams {
+  const void* U;   // GL state
+  void* Ubar;      // GL predictor output
+  const void* geoT;
+  long long geoT_stride;  // Reals per element
+  double coef[DG_NMAX + 2];  // dt^{j+1} / (j+1)!
+  int E;
+};
+
+// m-point levels visited with reduction every second derivative: N, N-2, ...
+template <int N, int RED>
+__host__ __device__ constexpr int tck_level_count() {
+  return RED == 0 ? 1 : (N + 1) / 2;
+}
+template <int N, int RED>
+__host__ __device__ constexpr int tck_level_m(int l) {
+  return RED == 0 ? N : N - 2 * l;
+}
+// accumulator offset of level l (Reals, 4 fields each)
+template <int N, int RED>
+__host__ __device__ constexpr int tck_acc_off(int l) {
+  return l == 0 ? 0 : tck_acc_off<N, RED>(l - 1) + 4 * tck_level_m<N, RED>(l - 1) *
+                                                        tck_level_m<N, RED>(l - 1) *
+                                                        tck_level_m<N, RED>(l - 1);
+}
+template <int N, int RED>
+__host__ __device__ constexpr int tck_smem_per_elem() {
+  return 8 * N * N * N + tck_acc_off<N, RED>(tck_level_count<N, RED>());
+}
+// per-element geometry of the predictor: levels m = N, N-2, ... >= 2,
+// each [3 d][3 i][m^3] line-major J^-1_{d i}, then [2][m^3] (-rho c^2, -1/rho)
+__host__ __device__ constexpr int tck_geo_level_off(int n, int l) {
+  return l == 0 ? 0 : tck_geo_level_off(n, l - 1) + 11 * (n - 2 * (l - 1)) * (n - 2 * (l - 1)) *
+                                                         (n - 2 * (l - 1));
+}
+__host__ __device__ constexpr int tck_geo_levels(int n) { return n / 2; }  // m >= 2
+__host__ __device__ constexpr int tck_geo_stride(int n) {
+  return tck_geo_level_off(n, tck_geo_levels(n));
+}
+
+// One derivative T_j = -S T_{j-1} at an M^3 Gauss set (Alg. 2 "evaluate the
+// gradient, set values"): src holds T_{j-1} (4 x M^3, field stride FS),
+// dst receives T_j.  g points at this level's geometry block.
+template <int M, typename Real, int FS>
+__device__ __forceinline__ void tck_derivative(const Real* src, Real* dst, const Real* __restrict__ g,
+                                               int t, int nthr) {
+  constexpr int M2 = M * M, M3 = M2 * M;
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    for (int l = t; l < M2; l += nthr) {
+      const int a = l % M, b = l / M;
+      const int base = dir == 0 ? M * a + M2 * b : (dir == 1 ? a + M2 * b : a + M * b);
+      const int st = dir == 0 ? 1 : (dir == 1 ? M : M2);
+      Real q[4][M], d[4][M];
+#pragma unroll
+      for (int fl = 0; fl < 4; ++fl) {
+#pragma unroll
+        for (int s = 0; s < M; ++s) q[fl][s] = src[fl * FS + base + st * s];
+        mv<Real, OFF_D(M), M, M>(q[fl], d[fl]);
+      }
+      const Real* J0 = g + (dir * 3 + 0) * M3 + l;
+      const Real* J1 = g + (dir * 3 + 1) * M3 + l;
+      const Real* J2 = g + (dir * 3 + 2) * M3 + l;
+#pragma unroll
+      for (int s = 0; s < M; ++s) {
+        const Real j0 = __ldg(J0 + M2 * s), j1 = __ldg(J1 + M2 * s), j2 = __ldg(J2 + M2 * s);
+        Real tp = fma(j0, d[1][s], fma(j1, d[2][s], j2 * d[3][s]));
+        Real tv0 = j0 * d[0][s], tv1 = j1 * d[0][s], tv2 = j2 * d[0][s];
+        const int idx = base + st * s;
+        if (dir > 0) {
+          tp += dst[idx];
+          tv0 += dst[FS + idx];
+          tv1 += dst[2 * FS + idx];
+          tv2 += dst[3 * FS + idx];
+        }
+        if (dir == 2) {  // coefficients: -rho c^2 (p), -1/rho (v)
+          const Real cp = __ldg(g + 9 * M3 + idx), cv = __ldg(g + 10 * M3 + idx);
+          tp *= cp;
+          tv0 *= cv;
+          tv1 *= cv;
+          tv2 *= cv;
+        }
+        dst[idx] = tp;
+        dst[FS + idx] = tv0;
+        dst[2 * FS + idx] = tv1;
+        dst[3 * FS + idx] = tv2;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Reference L2 projection M^3 -> (M-2)^3 (Alg. 3): three contractions,
+// src (M^3, field stride FS) -> tmp -> src ... result in dst.
+template <int M, typename Real, int FS>
+__device__ __forceinline__ void tck_project(Real* src, Real* tmp, int t, int nthr) {
+  constexpr int R = M - 2;
+  contract_tile<Real, 0, M, M, M, R, OFF_P(M), FS, FS>(src, tmp, t, nthr);
+  __syncthreads();
+  contract_tile<Real, 1, R, M, M, R, OFF_P(M), FS, FS>(tmp, src, t, nthr);
+  __syncthreads();
+  contract_tile<Real, 2, R, R, M, R, OFF_P(M), FS, FS>(src, tmp, t, nthr);
+  __syncthreads();
+}
+
+// acc_big += IU(M+2 <- M) applied to acc_small in all three directions
+template <int M, typename Real, int FS>
+__device__ __forceinline__ void tck_fold(const Real* small, Real* big, Real* t1, Real* t2, int t,
+                                         int nthr) {
+  constexpr int B = M + 2;
+  contract_tile<Real, 0, M, M, M, B, OFF_IU(B), M * M * M, FS>(small, t1, t, nthr);
+  __syncthreads();
+  contract_tile<Real, 1, B, M, M, B, OFF_IU(B), FS, FS>(t1, t2, t, nthr);
+  __syncthreads();
+  contract_tile<Real, 2, B, B, M, B, OFF_IU(B), FS, B * B * B, true>(t2, big, t, nthr);
+  __syncthreads();
+}
+
+template <int N, typename Real, int RED>
+__device__ __forceinline__ void tck_accumulate(Real* acc, const Real* T, int m3, Real c, int t,
+                                               int nthr, int fs) {
+  for (int i = t; i < 4 * m3; i += nthr) {
+    const int fl = i / m3, q = i - fl * m3;
+    acc[i] = fma(c, T[fl * fs + q], acc[i]);
+  }
+}
+
+template <int N, typename Real, int RED>
+__global__ void tck_kernel(const TckParams p) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int SE = tck_smem_per_elem<N, RED>();
+  constexpr int NL = tck_level_count<N, RED>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  const int epb = blockDim.x / N2;
+  const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
+  const int e0 = blockIdx.x * epb;
+  const int ne = min(epb, p.E - e0);
+  const int e = e0 + le;
+  const bool act = le < ne;
+  Real* s0 = sm + le * SE;  // T buffers (field stride N3)
+  Real* s1 = s0 + 4 * N3;
+  Real* acc = s1 + 4 * N3;  // per-level accumulators (field stride m^3)
+  const Real* __restrict__ U = static_cast<const Real*>(p.U);
+  const Real* geo = static_cast<const Real*>(p.geoT) + (size_t)(act ? e : 0) * p.geoT_stride;
+
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+    const int l = i / (4 * N3);
+    sm[l * SE + (i - l * 4 * N3)] = U[(size_t)e0 * 4 * N3 + i];
+  }
+  for (int i = t; i < tck_acc_off<N, RED>(NL); i += N2) acc[i] = Real(0);
+  __syncthreads();
+  // GL -> G (Sec. 3.2: the basis change is done per element on the fly)
+  contract_tile<Real, 2, N, N, N, N, OFF_V(N), N3, N3>(s0, s0, t, N2);
+  __syncthreads();
+  contract_tile<Real, 0, N, N, N, N, OFF_V(N), N3, N3>(s0, s0, t, N2);
+  __syncthreads();
+  contract_tile<Real, 1, N, N, N, N, OFF_V(N), N3, N3>(s0, s0, t, N2);
+  __syncthreads();
+  tck_accumulate<N, Real, RED>(acc, s0, N3, (Real)p.coef[0], t, N2, N3);
+
+  // Taylor terms j = 1 .. k+1 (k + 1 = N)
+  Real* cur = s0;
+  Real* nxt = s1;
+  int m = N, lvl = 0;
+#pragma unroll 1
+  for (int j = 1; j <= N; ++j) {
+    const Real* g = geo + tck_geo_level_off(N, lvl);
+    // derivative at the current m (T_{j-1} in cur, field stride N3)
+    switch (m) {
+#define DG_TCK_DERIV(MM)                                                 \
+  case MM:                                                               \
+    if constexpr (MM <= N) tck_derivative<MM, Real, N3>(cur, nxt, g, t, N2); \
+    break;
+      DG_TCK_DERIV(2) DG_TCK_DERIV(3) DG_TCK_DERIV(4) DG_TCK_DERIV(5) DG_TCK_DERIV(6)
+      DG_TCK_DERIV(7) DG_TCK_DERIV(8)
+#undef DG_TCK_DERIV
+      default:  // m == 1: the derivative of a constant vanishes
+        for (int i = t; i < 4 * N3; i += N2) nxt[i] = Real(0);
+        __syncthreads();
+        break;
+    }
+    if (RED == 2 && (j % 2) == 0) {
+      if (m - 2 < 1) break;  // projected to degree < 0: T_j = 0, stop
+      switch (m) {
+#define DG_TCK_PROJ(MM)                                                  \
+  case MM:                                                               \
+    if constexpr (MM <= N && MM >= 3) tck_project<MM, Real, N3>(nxt, cur, t, N2); \
+    break;
+        DG_TCK_PROJ(3) DG_TCK_PROJ(4) DG_TCK_PROJ(5) DG_TCK_PROJ(6) DG_TCK_PROJ(7)
+        DG_TCK_PROJ(8)
+#undef DG_TCK_PROJ
+        default:
+          break;
+      }
+      // the projection leaves its result in cur
+      Real* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+      m -= 2;
+      ++lvl;
+    }
+    // T_j is in nxt at m points
+    {
+      int off = 0, mm = N;
+      for (int l = 0; l < lvl; ++l) {
+        off += 4 * mm * mm * mm;
+        mm -= 2;
+      }
+      tck_accumulate<N, Real, RED>(acc + off, nxt, m * m * m, (Real)p.coef[j], t, N2, N3);
+    }
+    __syncthreads();
+    Real* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  // fold the levels from the smallest up: acc(m+2) += I(m -> m+2) acc(m)
+  if (RED == 2) {
+#pragma unroll
+    for (int l = NL - 1; l >= 1; --l) {
+      const int ms = tck_level_m<N, RED>(l);
+      Real* small = acc + tck_acc_off<N, RED>(l);
+      Real* big = acc + tck_acc_off<N, RED>(l - 1);
+      switch (ms) {
+#define DG_TCK_FOLD(MM)                                                   \
+  case MM:                                                                \
+    if constexpr (MM + 2 <= N) tck_fold<MM, Real, N3>(small, big, s0, s1, t, N2); \
+    break;
+        DG_TCK_FOLD(1) DG_TCK_FOLD(2) DG_TCK_FOLD(3) DG_TCK_FOLD(4) DG_TCK_FOLD(5)
+        DG_TCK_FOLD(6)
+#undef DG_TCK_FOLD
+        default:
+          break;
+      }
+    }
+  }
+  // G -> GL and store
+  contract_tile<Real, 2, N, N, N, N, OFF_VI(N), N3, N3>(acc, s0, t, N2);
+  __syncthreads();
+  contract_tile<Real, 0, N, N, N, N, OFF_VI(N), N3, N3>(s0, s1, t, N2);
+  __syncthreads();
+  contract_tile<Real, 1, N, N, N, N, OFF_VI(N), N3, N3>(s1, s0, t, N2);
+  __syncthreads();
+  Real* __restrict__ out = static_cast<Real*>(p.Ubar);
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+    const int l = i / (4 * N3);
+    out[(size_t)e0 * 4 * N3 + i] = sm[l * SE + (i - l * 4 * N3)];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Energy 1/2 U^T M U (Gauss rule, diagonal mass in G) and sums of squares.
+// Each block writes one partial; a second pass sums the partials in order.
+// ---------------------------------------------------------------------------
+struct EnergyParams {
+  const void* U;
+  const void* geoM;
+  double* partial;
+  int E;
+};
+
+template <int N, typename Real>
+__global__ void energy_kernel(const EnergyParams p) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  const int epb = blockDim.x / N2;
+  const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
+  const int e0 = blockIdx.x * epb;
+  const int ne = min(epb, p.E - e0);
+  const int e = e0 + le;
+  const bool act = le < ne;
+  Real* su = sm + le * 4 * N3;
+  const Real* U = static_cast<const Real*>(p.U);
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x)
+    sm[i] = U[(size_t)e0 * 4 * N3 + i];
+  __syncthreads();
+  if (act) contract_tile<Real, 2, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+  __syncthreads();
+  if (act) contract_tile<Real, 0, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+  __syncthreads();
+  if (act) contract_tile<Real, 1, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+  __syncthreads();
+  double s = 0.0;
+  if (act) {
+    const Real* gM = static_cast<const Real*>(p.geoM) + (size_t)e * 2 * N3;
+    for (int q = t; q < N3; q += N2) {
+      const double pp = su[q], vx = su[N3 + q], vy = su[2 * N3 + q], vz = su[3 * N3 + q];
+      s += pp * pp / (double)gM[q] + (vx * vx + vy * vy + vz * vz) / (double)gM[N3 + q];
+    }
+  }
+  __shared__ double red[1024];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) tot += red[i];
+    p.partial[blockIdx.x] = 0.5 * tot;
+  }
+}
+
+}  // namespace dg

@@ -1,0 +1,91 @@
+// Explicit instantiation helpers for one precision and a range of degrees.
+// Included by kern_f64_lo.cu, kern_f64_hi.cu, kern_f32_lo.cu, kern_f32_hi.cu.
+#pragma once
+
+#include "dg_internal.h"
+#include "dg_kernels.cuh"
+
+namespace dg {
+
+template <int N, typename Real>
+cudaError_t launch_op(const OpParams& p, int epi, int epb, cudaStream_t st) {
+  const int threads = epb * N * N;
+  const size_t smem = (size_t)epb * op_smem_per_elem<N>() * sizeof(Real);
+  const int blocks = (p.E + epb - 1) / epb;
+  if (epi == EPI_WRITE)
+    op_kernel<N, Real, EPI_WRITE><<<blocks, threads, smem, st>>>(p);
+  else if (epi == EPI_LSRK)
+    op_kernel<N, Real, EPI_LSRK><<<blocks, threads, smem, st>>>(p);
+  else
+    op_kernel<N, Real, EPI_ADD><<<blocks, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int N, typename Real>
+cudaError_t launch_tck(const TckParams& p, int red, int epb, cudaStream_t st) {
+  const int threads = epb * N * N;
+  const int blocks = (p.E + epb - 1) / epb;
+  if (red == 2) {
+    const size_t smem = (size_t)epb * tck_smem_per_elem<N, 2>() * sizeof(Real);
+    tck_kernel<N, Real, 2><<<blocks, threads, smem, st>>>(p);
+  } else {
+    const size_t smem = (size_t)epb * tck_smem_per_elem<N, 0>() * sizeof(Real);
+    tck_kernel<N, Real, 0><<<blocks, threads, smem, st>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+template <int N, typename Real>
+cudaError_t launch_energy(const EnergyParams& p, int epb, cudaStream_t st) {
+  const int threads = epb * N * N;
+  const int blocks = (p.E + epb - 1) / epb;
+  const size_t smem = (size_t)epb * 4 * N * N * N * sizeof(Real);
+  energy_kernel<N, Real><<<blocks, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+// which: 0 operator, 1 predictor, 2 energy
+template <int N, typename Real>
+int smem_bytes(int which, int red) {
+  if (which == 0) return op_smem_per_elem<N>() * (int)sizeof(Real);
+  if (which == 1)
+    return (red == 2 ? tck_smem_per_elem<N, 2>() : tck_smem_per_elem<N, 0>()) * (int)sizeof(Real);
+  return 4 * N * N * N * (int)sizeof(Real);
+}
+
+// Allow each kernel the opt-in shared memory limit minus its static use.
+template <typename K>
+cudaError_t allow_smem(K kernel) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes);
+}
+
+template <int N, typename Real>
+cudaError_t set_max_smem() {
+  cudaError_t e;
+  if ((e = allow_smem(op_kernel<N, Real, EPI_WRITE>)) != cudaSuccess) return e;
+  if ((e = allow_smem(op_kernel<N, Real, EPI_LSRK>)) != cudaSuccess) return e;
+  if ((e = allow_smem(op_kernel<N, Real, EPI_ADD>)) != cudaSuccess) return e;
+  if ((e = allow_smem(tck_kernel<N, Real, 0>)) != cudaSuccess) return e;
+  if ((e = allow_smem(tck_kernel<N, Real, 2>)) != cudaSuccess) return e;
+  return allow_smem(energy_kernel<N, Real>);
+}
+
+template <int N, typename Real>
+void register_one(KernelTable* t) {
+  const int pi = sizeof(Real) == 8 ? 0 : 1;
+  t->op[pi][N] = &launch_op<N, Real>;
+  t->tck[pi][N] = &launch_tck<N, Real>;
+  t->energy[pi][N] = &launch_energy<N, Real>;
+  t->smem[pi][N] = &smem_bytes<N, Real>;
+}
+
+}  // namespace dg

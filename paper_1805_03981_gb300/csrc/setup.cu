@@ -1,0 +1,205 @@
+// Geometry and coefficient set-up in FP64 (one block per element).
+//
+// The paper pre-computes inverse Jacobians at each quadrature point and
+// re-uses them (Sec. 3.3, Sec. 4.4); this kernel evaluates, from the degree-q
+// geometry nodes and the degree-k nodal coefficients, everything the
+// operator and the predictor read per point, and writes it in the precision
+// of the context and in the layouts of dg_kernels.cuh:
+//   geoA [3 d][3 i][n^3] line-major per d   w adj(J)_{d i} = w detJ (J^-1)_{d i}
+//   geoM [2][n^3]                            rho c^2/(w detJ), 1/(rho w detJ)
+//   geoF [6 f][6][n^2]                       nw = w_f adj(J)_{d .} (+-1),
+//                                            Z-/(Z-+Z+), alpha Z- Z+/((Z-+Z+)|nw|),
+//                                            alpha |nw|/(Z-+Z+)
+//   geoT per level m = n, n-2, ... >= 2: [3 d][3 i][m^3] J^-1_{d i} line-major,
+//                                        [m^3] -rho c^2, [m^3] -1/rho
+// with J_{i j} = d x_i / d xi_j, Nanson's formula for the face normal and
+// Z = rho c (Sec. 2.4).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dg_internal.h"
+#include "tables.h"
+
+namespace dg {
+namespace {
+
+constexpr int CMAX = DG_NMAX + 2;
+
+__device__ void lag1d(const double* nodes, int c, double x, double* L, double* dL) {
+  for (int a = 0; a < c; ++a) {
+    double v = 1.0, d = 0.0;
+    for (int b = 0; b < c; ++b) {
+      if (b == a) continue;
+      const double inv = 1.0 / (nodes[a] - nodes[b]);
+      d = d * (x - nodes[b]) * inv + v * inv;
+      v *= (x - nodes[b]) * inv;
+    }
+    L[a] = v;
+    if (dL) dL[a] = d;
+  }
+}
+
+__device__ void jacobian(const SetupParams& P, int e, const double xi[3], double J[3][3]) {
+  const int c = P.q + 1;
+  double L[3][CMAX], dL[3][CMAX];
+  for (int d = 0; d < 3; ++d) lag1d(P.xq, c, xi[d], L[d], dL[d]);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) J[i][j] = 0.0;
+  const double* X = P.nodes + (size_t)e * c * c * c * 3;
+  for (int kk = 0; kk < c; ++kk)
+    for (int jj = 0; jj < c; ++jj)
+      for (int ii = 0; ii < c; ++ii) {
+        const int idx = ii + c * jj + c * c * kk;
+        const double w0 = dL[0][ii] * L[1][jj] * L[2][kk];
+        const double w1 = L[0][ii] * dL[1][jj] * L[2][kk];
+        const double w2 = L[0][ii] * L[1][jj] * dL[2][kk];
+        for (int i = 0; i < 3; ++i) {
+          const double x = X[idx * 3 + i];
+          J[i][0] += x * w0;
+          J[i][1] += x * w1;
+          J[i][2] += x * w2;
+        }
+      }
+}
+
+// adj(J) = det(J) J^-1; returns det(J)
+__device__ double adjugate(const double J[3][3], double A[3][3]) {
+  A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  return J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
+}
+
+__device__ double nodal_at(const double* f, const double* xgl, int n, const double xi[3]) {
+  double L[3][CMAX];
+  for (int d = 0; d < 3; ++d) lag1d(xgl, n, xi[d], L[d], nullptr);
+  double s = 0.0;
+  for (int z = 0; z < n; ++z)
+    for (int y = 0; y < n; ++y) {
+      double row = 0.0;
+      for (int x = 0; x < n; ++x) row += f[x + n * y + n * n * z] * L[0][x];
+      s += row * L[1][y] * L[2][z];
+    }
+  return s;
+}
+
+__device__ __forceinline__ void put(void* base, size_t i, double v, int prec) {
+  if (prec == 0)
+    static_cast<double*>(base)[i] = v;
+  else
+    static_cast<float*>(base)[i] = (float)v;
+}
+
+// position of point (x, y, z) of an m^3 tile in the line-major order of dir
+__device__ __forceinline__ int line_major(int dir, int m, int x, int y, int z) {
+  return dir == 0 ? (y + m * z) + m * m * x : (dir == 1 ? (x + m * z) + m * m * y : (x + m * y) + m * m * z);
+}
+
+__global__ void setup_kernel(const SetupParams P) {
+  const int e = blockIdx.x;
+  const int n = P.n, n2 = n * n, n3 = n2 * n;
+  const double* xg = P.pts + dg_pts_off(n);
+  const double* wg = P.pts + DG_PTS_LEN + dg_pts_off(n);
+  const double* xgl = P.pts + 2 * DG_PTS_LEN + dg_pts_off(n);
+  const double* rho = P.rho + (size_t)e * n3;
+  const double* cc = P.c + (size_t)e * n3;
+  const int ncell = n3, nface = 6 * n2;
+  int ntck = 0;
+  for (int m = n; m >= 2; m -= 2) ntck += m * m * m;
+  const int nitems = ncell + nface + ntck;
+  for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+    double J[3][3], A[3][3], xi[3];
+    if (it < ncell) {
+      const int x = it % n, y = (it / n) % n, z = it / n2;
+      xi[0] = xg[x];
+      xi[1] = xg[y];
+      xi[2] = xg[z];
+      const double w = wg[x] * wg[y] * wg[z];
+      jacobian(P, e, xi, J);
+      const double det = adjugate(J, A);
+      if (!(det > 0.0)) atomicExch(P.bad, 1);
+      const double r = nodal_at(rho, xgl, n, xi), c = nodal_at(cc, xgl, n, xi);
+      for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < 3; ++i)
+          put(P.geoA, (size_t)e * 9 * n3 + (d * 3 + i) * n3 + line_major(d, n, x, y, z), w * A[d][i],
+              P.prec);
+      put(P.geoM, (size_t)e * 2 * n3 + it, r * c * c / (w * det), P.prec);
+      put(P.geoM, (size_t)e * 2 * n3 + n3 + it, 1.0 / (r * w * det), P.prec);
+    } else if (it < ncell + nface) {
+      const int k = it - ncell;
+      const int f = k / n2, ij = k - f * n2, i = ij % n, j = ij / n;
+      const int d = f >> 1;
+      const double side = (f & 1) ? 1.0 : -1.0;
+      const int t0 = d == 0 ? 1 : 0, t1 = d == 2 ? 1 : 2;
+      xi[d] = side;
+      xi[t0] = xg[i];
+      xi[t1] = xg[j];
+      jacobian(P, e, xi, J);
+      const double det = adjugate(J, A);
+      if (!(det > 0.0)) atomicExch(P.bad, 1);
+      const double wf = wg[i] * wg[j];
+      const double nw[3] = {wf * side * A[d][0], wf * side * A[d][1], wf * side * A[d][2]};
+      const double s = sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
+      const double zm = nodal_at(rho, xgl, n, xi) * nodal_at(cc, xgl, n, xi);
+      double zp = zm;
+      const int en = P.nbr[e * 6 + f];
+      if (en >= 0) {
+        const int fn = P.nbr_face[e * 6 + f], o = P.orient[e * 6 + f];
+        const int uu = (o & 1) ? j : i, vv = (o & 1) ? i : j;
+        const int ip = (o & 2) ? n - 1 - uu : uu, jp = (o & 4) ? n - 1 - vv : vv;
+        const int dn = fn >> 1;
+        double xn[3];
+        xn[dn] = (fn & 1) ? 1.0 : -1.0;
+        xn[dn == 0 ? 1 : 0] = xg[ip];
+        xn[dn == 2 ? 1 : 2] = xg[jp];
+        zp = nodal_at(P.rho + (size_t)en * n3, xgl, n, xn) * nodal_at(P.c + (size_t)en * n3, xgl, n, xn);
+      }
+      const double zs = zm + zp;
+      const size_t fb = (size_t)e * 36 * n2 + (size_t)f * 6 * n2 + ij;
+      put(P.geoF, fb, nw[0], P.prec);
+      put(P.geoF, fb + n2, nw[1], P.prec);
+      put(P.geoF, fb + 2 * n2, nw[2], P.prec);
+      put(P.geoF, fb + 3 * n2, zm / zs, P.prec);
+      put(P.geoF, fb + 4 * n2, P.alpha * zm * zp / (zs * s), P.prec);
+      put(P.geoF, fb + 5 * n2, P.alpha * s / zs, P.prec);
+    } else {
+      int k = it - ncell - nface, m = n, off = 0;
+      while (k >= m * m * m) {
+        k -= m * m * m;
+        off += 11 * m * m * m;
+        m -= 2;
+      }
+      const int m2 = m * m, m3 = m2 * m;
+      const int x = k % m, y = (k / m) % m, z = k / m2;
+      const double* xm = P.pts + dg_pts_off(m);
+      xi[0] = xm[x];
+      xi[1] = xm[y];
+      xi[2] = xm[z];
+      jacobian(P, e, xi, J);
+      const double det = adjugate(J, A);
+      if (!(det > 0.0)) atomicExch(P.bad, 1);
+      const double r = nodal_at(rho, xgl, n, xi), c = nodal_at(cc, xgl, n, xi);
+      const size_t tb = (size_t)e * P.tstride + off;
+      for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < 3; ++i)
+          put(P.geoT, tb + (d * 3 + i) * m3 + line_major(d, m, x, y, z), A[d][i] / det, P.prec);
+      put(P.geoT, tb + 9 * m3 + k, -r * c * c, P.prec);
+      put(P.geoT, tb + 10 * m3 + k, -1.0 / r, P.prec);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_setup(const SetupParams& P, cudaStream_t st) {
+  setup_kernel<<<P.E, 128, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace dg

@@ -1,0 +1,60 @@
+// 1D tables of the tensor-product DG discretisation (host side, FP64).
+//
+// A "count" c is a number of points per direction; c = k+1 for the element
+// and c = k+1, k-1, ... for the reduced point sets of the Taylor-Cauchy-
+// Kowalevski predictor (Sec. 3.3).  For every c in [1, DG_NMAX] the flat
+// table holds, row-major:
+//   V  [c][c]      GL(c) -> G(c): V[q][a] = l^GL_a(x^G_q)       (Sec. 3.1)
+//   VI [c][c]      G(c) -> GL(c): VI[a][q] = l^G_q(x^GL_a)      (exact inverse)
+//   D  [c][c]      collocation derivative on the Gauss points:
+//                  D[q][a] = (l^G_a)'(x^G_q)                    (Sec. 3.2, Alg. 2)
+//   LF [2][c]      l^G_a(-1), l^G_a(+1): Gauss-basis face traces
+//   P  [c-2][c]    reference-element L2 projection Gauss(c) -> Gauss(c-2):
+//                  P[a][b] = w^c_b l^{c-2}_a(x^c_b) / w^{c-2}_a  (Sec. 3.3)
+//   IU [c][c-2]    prolongation Gauss(c-2) -> Gauss(c):
+//                  IU[q][b] = l^{c-2}_b(x^c_q)
+// The projection and prolongation blocks are empty for c <= 2.
+#pragma once
+
+#define DG_NMAX 8
+
+#ifdef __CUDACC__
+#define DG_HD __host__ __device__
+#else
+#define DG_HD
+#endif
+
+DG_HD constexpr int dg_tab_block(int c) {
+  return 3 * c * c + 2 * c + (c > 2 ? 2 * c * (c - 2) : 0);
+}
+DG_HD constexpr int dg_tab_base(int c) {
+  return c <= 1 ? 0 : dg_tab_base(c - 1) + dg_tab_block(c - 1);
+}
+DG_HD constexpr int OFF_V(int c) { return dg_tab_base(c); }
+DG_HD constexpr int OFF_VI(int c) { return dg_tab_base(c) + c * c; }
+DG_HD constexpr int OFF_D(int c) { return dg_tab_base(c) + 2 * c * c; }
+DG_HD constexpr int OFF_LF(int c) { return dg_tab_base(c) + 3 * c * c; }
+DG_HD constexpr int OFF_P(int c) { return dg_tab_base(c) + 3 * c * c + 2 * c; }
+DG_HD constexpr int OFF_IU(int c) { return OFF_P(c) + (c > 2 ? c * (c - 2) : 0); }
+constexpr int DG_TAB_LEN = dg_tab_base(DG_NMAX + 1);
+
+// Raw points for the geometry set-up: for each count c in [1, DG_NMAX],
+// Gauss points, Gauss weights and (c >= 2) Gauss-Lobatto points at offset
+// dg_pts_off(c) = c (c - 1) / 2 within each of three arrays.
+DG_HD constexpr int dg_pts_off(int c) { return c * (c - 1) / 2; }
+constexpr int DG_PTS_LEN = dg_pts_off(DG_NMAX + 2);
+
+namespace dg {
+
+struct HostTables {
+  double tab[DG_TAB_LEN];
+  double xg[DG_PTS_LEN], wg[DG_PTS_LEN], xgl[DG_PTS_LEN];
+};
+
+// Fill all tables (idempotent). Returns 0 on success.
+int build_tables(HostTables* t);
+
+// Gauss-Lobatto points of count c (c >= 2), ascending, into x[c].
+void gauss_lobatto(int c, double* x);
+
+}  // namespace dg
