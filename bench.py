@@ -1,0 +1,342 @@
+"""Benchmark: DoF-steps/s of the DG acoustic solver on a GB300.
+
+Workload (one GPU): unit cube split into 32^3 curved hexahedra, degree k = 5
+(28,311,552 DoF counting p, v_x, v_y, v_z), variable rho and c, reflecting
+walls, Gaussian pressure pulse, FP64.  One bench step advances one state by
+one LSRK(5,4) time step and another by one ADER time step (order k+1 = 6,
+degree reduction every second derivative) at the same dt (Cr = 0.1), so a
+step processes 2 x 28.3M DoF-steps and runs every kernel of the hot path.
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and a
+device synchronisation, timed with CUDA events on the launching stream; the
+max over ranks is reported.  The state (226 MB) and geometry (1.8 GB) are
+larger than L2, so no flush is needed between steps.  Per-kernel device time
+comes from the library's own event profiling on the same stream.
+
+e2e: the same steps through dg_solve_host, copying the state from pinned host
+memory to the device and back every step.
+
+--impl reference: the FP64 CPU oracle on a bounded sample of the same recipe
+(4^3 elements), one LSRK and one ADER step per bench step, single thread.
+
+Multi-GPU (torchrun, N > 1): every rank runs its own replica of the
+workload; value = DoF-steps of all ranks / max time over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DoF-steps/s at fixed L2 error (ADER/LSRK, FP32/FP64); served p99 latency"
+UNIT = "DoF-steps/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Derived FP pipe peaks of a GB300 (152 SMs, 2070 MHz maximum SM clock):
+# FP64: 2 FMA/clk/SM (the nominal 1.25 TFLOP/s) -> 152 * 2 * 2 * 2.07e9;
+# FP32: 128 FMA/clk/SM -> 152 * 128 * 2 * 2.07e9.
+FP64_PEAK = 152 * 2 * 2 * 2.07e9
+FP32_PEAK = 152 * 128 * 2 * 2.07e9
+HBM_FALLBACK = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--size", type=int, default=32, help="elements per axis")
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def workload(N, k):
+    import synth
+    return synth.configs.curved_pulse(N=N, k=k, nsteps=200)
+
+
+def workload_desc(N, k, prec):
+    dof = 4 * (k + 1) ** 3 * N ** 3
+    return (f"curved_pulse: unit cube, {N}^3 curved hexahedra (x_i += 0.05 prod sin 2 pi x_j), "
+            f"k={k} ({dof} DoF), c=1+0.5 sin2pix cos2piy, rho=1+0.3 cos2piz, walls, Gaussian "
+            f"pulse sigma=0.05 (seed 2), Cr=0.1; bench step = 1 LSRK(5,4) step + 1 ADER(order {k + 1}, "
+            f"reduction every 2nd derivative) step, {prec.upper()}")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev, self.proc, self.path = dev, None, None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import synth, oracle
+cfg = synth.configs.curved_pulse(N={n}, k={k})
+o = oracle.Oracle(cfg["mesh"], {k}, cfg["rho"], cfg["c"], 1.0)
+U1 = cfg["U0"].copy(); U2 = cfg["U0"].copy()
+for _ in range({warm}):
+    U1 = o.lsrk(U1, cfg["dt"], 1); U2 = o.ader(U2, cfg["dt"], 1, 2)
+times = []
+for _ in range({steps}):
+    t0 = time.perf_counter()
+    U1 = o.lsrk(U1, cfg["dt"], 1); U2 = o.ader(U2, cfg["dt"], 1, 2)
+    times.append(time.perf_counter() - t0)
+print(json.dumps({{"times": times, "dof": int(U1.size)}}))
+"""
+
+
+def run_oracle(n, k, warm, steps):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = CPU_SNIPPET.format(root=ROOT, n=n, k=k, warm=warm, steps=steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    total = sum(out["times"])
+    return 2 * out["dof"] * len(out["times"]) / total, total, out
+
+
+def cpu_sample_desc(n, k, steps):
+    return (f"FP64 oracle (dense element matrices, numpy, 1 thread) on the {n}^3-element instance of "
+            f"the same recipe (k={k}, {4 * (k + 1) ** 3 * n ** 3} DoF): {steps} steps of 1 LSRK + 1 ADER step, "
+            f"oracle set-up excluded")
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = 4
+    value, total, out = run_oracle(n, args.k, args.warmup, args.steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_desc(args.size, args.k, "fp64"),
+                                        "sample": cpu_sample_desc(n, args.k, args.steps)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": cpu_sample_desc(n, args.k, args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+    import paper_1805_03981_gb300 as dgw
+    from paper_1805_03981_gb300 import opcount
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    prec = dgw.DG_FP64 if args.prec == "fp64" else dgw.DG_FP32
+    N, k = args.size, args.k
+    cfg = workload(N, k)
+    s = dgw.Solver(cfg["mesh"], k, prec, cfg["alpha"], cfg["rho"], cfg["c"])
+    dof = 4 * (k + 1) ** 3 * N ** 3
+    dt = cfg["dt"]
+    U_l = s.to_device(cfg["U0"])
+    U_a = s.to_device(cfg["U0"])
+    stream = torch.cuda.current_stream()
+
+    def bench_step():
+        s.step_lsrk(U_l, dt, 1)
+        s.step_ader(U_a, dt, 1, 2)
+
+    for _ in range(args.warmup):
+        bench_step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    s.profile(True)
+    s.profile_read(reset=True)
+    launches0 = s.launch_count()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        bench_step()
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count() - launches0
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms)
+    value = world * 2 * dof * args.steps / (ms_max * 1e-3)
+
+    # per-method rates from the profile (device time per kind)
+    t_lsrk = prof["lsrk_stage"][0]
+    t_ader = prof["ader_update"][0] + prof["tck"][0]
+    per_method = {"lsrk": dof * args.steps / (t_lsrk * 1e-3) if t_lsrk else None,
+                  "ader": dof * args.steps / (t_ader * 1e-3) if t_ader else None}
+
+    # dominant kernel and its roofline
+    rsize = 8 if prec == dgw.DG_FP64 else 4
+    dom = max(prof, key=lambda kk: prof[kk][0])
+    tot_ms, nlaunch = prof[dom]
+    avg_s = tot_ms * 1e-3 / max(nlaunch, 1)
+    E = N ** 3
+    nonwall = 1.0 - 1.0 / N
+    flops = opcount.flops_per_element(dom, k + 1, 2, nonwall) * E
+    byts = opcount.bytes_per_element(dom, k + 1, rsize, 2) * E
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs")
+    if prec == dgw.DG_FP64:
+        roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": FP64_PEAK / 1e12,
+                "unit": "TFLOP/s", "peak_source": "derived FP64 pipe: 152 SM x 2 FMA/clk x 2 x 2.07 GHz"}
+    else:
+        ai = flops / byts
+        peak_hbm = (hbm or HBM_FALLBACK) * 1e9
+        if ai * peak_hbm > FP32_PEAK:
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": FP32_PEAK / 1e12,
+                    "unit": "TFLOP/s", "peak_source": "derived FP32 pipe: 152 SM x 128 FMA/clk x 2 x 2.07 GHz"}
+        else:
+            roof = {"bound": "hbm", "achieved": byts / avg_s / 1e9, "peak": hbm or HBM_FALLBACK,
+                    "unit": "GB/s", "peak_source": "measured" if hbm else "fallback"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["traffic"] = None
+    roof["per_launch_ms"] = avg_s * 1e3
+    roof["algorithmic_flops_per_launch"] = flops
+    roof["algorithmic_bytes_per_launch"] = byts
+
+    # e2e through the C ABI with host buffers (pinned), copies inside the timing
+    Uh = torch.from_numpy(np.ascontiguousarray(cfg["U0"])).to(s.dtype).pin_memory()
+    out_l = torch.empty_like(Uh).pin_memory()
+    out_a = torch.empty_like(Uh).pin_memory()
+    in_l, in_a = Uh.clone().pin_memory(), Uh.clone().pin_memory()
+    for _ in range(1):
+        s.solve_host(0, in_l, out_l, dt, 1)
+        s.solve_host(1, in_a, out_a, dt, 1, 2)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.solve_host(0, in_l, out_l, dt, 1)
+        s.solve_host(1, in_a, out_a, dt, 1, 2)
+        in_l, out_l = out_l, in_l
+        in_a, out_a = out_a, in_a
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    state_bytes = s.info()["state_bytes"]
+    e2e = {"value": world * 2 * dof * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * state_bytes, "d2h_bytes_per_step": 2 * state_bytes}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            v, total, _ = run_oracle(4, k, 1, args.cpu_steps)
+            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": cpu_sample_desc(4, k, args.cpu_steps), "seconds": total}
+        except Exception as exc:  # the GPU number stands without it
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(exc)[:200]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == dgw.DG_FP64 else "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_desc(N, k, args.prec), "elements": E, "k": k, "dof": dof,
+                       "l2": "inputs larger than L2 (state %d MB, %d MB device-resident incl. geometry), no flush"
+                       % (state_bytes >> 20, s.device_bytes() >> 20),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "per_method_dofs_per_s": per_method,
+            "kernel_ms": {kk: {"total_ms": v[0], "launches": v[1]} for kk, v in prof.items() if v[1]},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

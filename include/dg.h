@@ -133,7 +133,8 @@ int dg_step_lsrk(dg_ctx* ctx, void* U, double dt, int32_t nsteps, uintptr_t stre
  * predictor with the element-local basis change GL -> G (Sec. 3.2,
  * Algorithm 2) and degree reduction every reduce_every-th derivative
  * (Sec. 3.3, Algorithm 3; 2 = the paper's choice, 0 = none), then
- * U <- U - M^-1 K Ubar. Sum over j = 0..k+1. reduce_every in {0, 1, 2, 3}.
+ * U <- U - M^-1 K Ubar. Sum over j = 0..k+1. reduce_every must be 0 or 2;
+ * other values return DG_EUNSUPPORTED.
  */
 int dg_step_ader(dg_ctx* ctx, void* U, double dt, int32_t nsteps,
                  int32_t reduce_every, uintptr_t stream);
@@ -169,6 +170,22 @@ int dg_norms(dg_ctx* ctx, const void* A, const void* B, double* out_aa,
  */
 int dg_solve_host(dg_ctx* ctx, int method, const void* U_host, void* U_out_host,
                   double dt, int32_t nsteps, int32_t reduce_every, uintptr_t stream);
+
+/*
+ * Per-kernel timing. While enabled, every kernel launch of the context is
+ * bracketed by two CUDA events recorded on the launching stream.
+ * dg_profile_read synchronises on those events and returns, per kind, the
+ * summed device time in ms and the number of launches since the last reset
+ * (arrays of DG_NKINDS entries); reset != 0 starts a new interval.
+ */
+#define DG_KIND_OPERATOR 0 /* R = -M^-1 K U alone */
+#define DG_KIND_LSRK 1     /* operator fused with one LSRK stage update */
+#define DG_KIND_ADER 2     /* operator fused with the ADER update */
+#define DG_KIND_TCK 3      /* Taylor-Cauchy-Kowalevski predictor */
+#define DG_KIND_OTHER 4    /* set-up, energy, norms */
+#define DG_NKINDS 5
+int dg_profile_enable(dg_ctx* ctx, int enable);
+int dg_profile_read(dg_ctx* ctx, double* ms, int64_t* launches, int reset);
 
 /* Sizes: number of elements, degree, precision, bytes of one state. */
 int dg_info(const dg_ctx* ctx, int32_t* n_elem, int32_t* k, int32_t* prec,

@@ -12,7 +12,9 @@ EXPORTED_SYMBOLS = [
     "dg_mesh_setup", "dg_set_coefficients", "dg_apply_operator", "dg_step_lsrk",
     "dg_step_ader", "dg_tck", "dg_energy", "dg_norms", "dg_solve_host", "dg_info",
     "dg_device_bytes", "dg_launch_count", "dg_destroy", "dg_strerror", "dg_last_error",
+    "dg_profile_enable", "dg_profile_read",
 ]
+KINDS = ["operator", "lsrk_stage", "ader_update", "tck", "other"]
 
 
 class DGError(RuntimeError):
@@ -61,6 +63,8 @@ def load_library():
         "dg_launch_count": (C.c_uint64, [vp]),
         "dg_destroy": (None, [vp]),
         "dg_strerror": (C.c_char_p, [C.c_int]),
+        "dg_profile_enable": (C.c_int, [vp, C.c_int]),
+        "dg_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
         "dg_last_error": (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -196,6 +200,16 @@ class Solver:
         E, k, p, b = C.c_int32(), C.c_int32(), C.c_int32(), C.c_size_t()
         self._check(self.lib.dg_info(self.ctx, C.byref(E), C.byref(k), C.byref(p), C.byref(b)))
         return {"n_elem": E.value, "k": k.value, "prec": p.value, "state_bytes": b.value}
+
+    def profile(self, enable=True):
+        self._check(self.lib.dg_profile_enable(self.ctx, int(bool(enable))))
+
+    def profile_read(self, reset=True):
+        """{kind: (total_ms, launches)} since the last reset."""
+        ms = (C.c_double * len(KINDS))()
+        cnt = (C.c_int64 * len(KINDS))()
+        self._check(self.lib.dg_profile_read(self.ctx, ms, cnt, int(bool(reset))))
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KINDS)}
 
     def device_bytes(self):
         return int(self.lib.dg_device_bytes(self.ctx))

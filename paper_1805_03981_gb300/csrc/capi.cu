@@ -92,7 +92,8 @@ struct dg_ctx {
   void* geoF = nullptr;
   void* geoT = nullptr;
   int tstride = 0;
-  void* U2 = nullptr;    // LSRK ping-pong state
+  void* U2 = nullptr;    // LSRK intermediate stage states
+  void* U3 = nullptr;
   void* dU = nullptr;    // LSRK register
   void* Ubar = nullptr;  // ADER predictor
   void* Uh = nullptr;    // state for dg_solve_host
@@ -101,6 +102,14 @@ struct dg_ctx {
   size_t dev_bytes = 0;
   uint64_t launches = 0;
   int epb_op = 1, epb_tck = 1, epb_en = 1;
+  // profiling: event pairs recorded around launches while enabled
+  bool prof = false;
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> event_pool;
   std::vector<void*> allocs;
   std::string err;
 
@@ -132,10 +141,49 @@ struct dg_ctx {
     *p = static_cast<T*>(v);
     return DG_OK;
   }
+  cudaEvent_t take_event() {
+    if (!event_pool.empty()) {
+      cudaEvent_t ev = event_pool.back();
+      event_pool.pop_back();
+      return ev;
+    }
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return ev;
+  }
+  // bracket one launch with events when profiling is on
+  struct Span {
+    dg_ctx* c;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    Span(dg_ctx* c_, int k, cudaStream_t s) : c(c_), kind(k), st(s) {
+      if (c->prof && (a = c->take_event())) cudaEventRecord(a, st);
+    }
+    void done() {
+      if (!a) return;
+      cudaEvent_t b = c->take_event();
+      if (b) {
+        cudaEventRecord(b, st);
+        c->recs.push_back({kind, a, b});
+      } else {
+        c->event_pool.push_back(a);
+      }
+      a = nullptr;
+    }
+  };
   ~dg_ctx() {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(dev);
+    for (auto& r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto ev : event_pool) cudaEventDestroy(ev);
     for (void* p : allocs) cudaFree(p);
     cudaSetDevice(cur);
   }
@@ -269,7 +317,10 @@ OpParams op_params(const dg_ctx* ctx) {
 
 int launch_op(dg_ctx* ctx, const OpParams& p, int epi, cudaStream_t st) {
   OpFn fn = g_kt.op[ctx->prec][ctx->n];
+  const int kind = epi == EPI_WRITE ? DG_KIND_OPERATOR : (epi == EPI_LSRK ? DG_KIND_LSRK : DG_KIND_ADER);
+  dg_ctx::Span span(ctx, kind, st);
   DG_CK(fn(p, epi, ctx->epb_op, st), "operator kernel launch");
+  span.done();
   ctx->launches++;
   return DG_OK;
 }
@@ -287,7 +338,9 @@ int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaS
     fact *= (j + 1);
     p.coef[j] = std::pow(dt, j + 1) / fact;
   }
+  dg_ctx::Span span(ctx, DG_KIND_TCK, st);
   DG_CK(g_kt.tck[ctx->prec][ctx->n](p, red, ctx->epb_tck, st), "predictor kernel launch");
+  span.done();
   ctx->launches++;
   return DG_OK;
 }
@@ -309,29 +362,28 @@ int check_state_ptr(dg_ctx* ctx, const void* p, const char* what) {
   return DG_OK;
 }
 
+// Stage s reads the state of stage s-1 and writes a different buffer
+// (neighbours read face values of the input while it is being written):
+// U -> A -> B -> A -> B -> U, so each step ends in U without a copy.
 int lsrk_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st) {
   int rc;
   if ((rc = ensure(ctx, &ctx->U2, "LSRK state"))) return rc;
+  if ((rc = ensure(ctx, &ctx->U3, "LSRK state"))) return rc;
   if ((rc = ensure(ctx, &ctx->dU, "LSRK register"))) return rc;
   OpParams p = op_params(ctx);
-  void* cur = U;
-  void* other = ctx->U2;
+  void* const chain[6] = {U, ctx->U2, ctx->U3, ctx->U2, ctx->U3, U};
   for (int s = 0; s < nsteps; ++s)
     for (int st5 = 0; st5 < 5; ++st5) {
-      p.U = cur;
-      p.Uadd = cur;
-      p.out = other;
+      p.U = chain[st5];
+      p.Uadd = chain[st5];
+      p.out = chain[st5 + 1];
       p.dU = ctx->dU;
       p.cA = kLsrkA[st5];
       p.cB = kLsrkB[st5];
       p.dt = dt;
       p.first = st5 == 0;
       if ((rc = launch_op(ctx, p, EPI_LSRK, st))) return rc;
-      void* t = cur;
-      cur = other;
-      other = t;
     }
-  if (cur != U) DG_CK(cudaMemcpyAsync(U, cur, ctx->state_bytes(), cudaMemcpyDeviceToDevice, st), "copy");
   return DG_OK;
 }
 
@@ -659,6 +711,36 @@ int dg_info(const dg_ctx* ctx, int32_t* E, int32_t* k, int32_t* prec, size_t* by
 }
 
 size_t dg_device_bytes(const dg_ctx* ctx) { return ctx ? ctx->dev_bytes : 0; }
+
+int dg_profile_enable(dg_ctx* ctx, int enable) {
+  if (!ctx) return DG_EINVAL;
+  ctx->prof = enable != 0;
+  return DG_OK;
+}
+
+int dg_profile_read(dg_ctx* ctx, double* ms, int64_t* launches, int reset) {
+  if (!ctx || !ms || !launches) return DG_EINVAL;
+  DeviceGuard g(ctx->dev);
+  for (int i = 0; i < DG_NKINDS; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  for (auto& r : ctx->recs) {
+    DG_CK(cudaEventSynchronize(r.b), "profile event");
+    float t = 0.f;
+    DG_CK(cudaEventElapsedTime(&t, r.a, r.b), "profile elapsed");
+    ms[r.kind] += t;
+    launches[r.kind] += 1;
+  }
+  if (reset) {
+    for (auto& r : ctx->recs) {
+      ctx->event_pool.push_back(r.a);
+      ctx->event_pool.push_back(r.b);
+    }
+    ctx->recs.clear();
+  }
+  return DG_OK;
+}
 
 uint64_t dg_launch_count(const dg_ctx* ctx) { return ctx ? ctx->launches : 0; }
 

@@ -1,0 +1,119 @@
+"""Algorithmic operation and byte counts of the kernels, per element.
+
+Flops count what the formulation requires: a 1D contraction producing one
+value from m inputs costs 2m flops (m multiply-adds), point-wise operations
+are counted one by one.  Bytes count compulsory device-memory traffic: each
+state vector and geometry array read or written once per launch; face values
+of neighbours are assumed to come from cache (the element's own read brings
+them in), as the paper's measurements show for its CPU loops (Sec. 4.4).
+
+Also here: the paper's own per-element operation-count model (Sec. 4.1,
+C_tensorial and Table "kernel-calls"), used for comparison only.
+"""
+
+
+def contraction(outputs, m):
+    return 2 * m * outputs
+
+
+def operator_flops(n, curved=True, nonwall_frac=1.0):
+    """R = -M^-1 K U on one element: basis changes, cell terms, faces, M^-1."""
+    N3, N2 = n ** 3, n ** 2
+    f = 0
+    f += 12 * contraction(N3, n)            # GL -> G, 4 fields x 3 directions
+    f += 3 * N3 * (5 + 3)                   # contravariant fluxes per direction
+    f += 12 * contraction(N3, n)            # test-gradient (transposed derivative)
+    f += 2 * 4 * N3                         # accumulation over the 3 directions
+    face_pt = 4 * 2 * n + 5 + 5 + 2 + 4 + 4 + 3 + 4 * 2 * n
+    f += 6 * N2 * face_pt                   # traces, flux, lifting
+    f += nonwall_frac * 6 * 4 * 2 * contraction(N2, n)   # neighbour GL face nodes -> Gauss
+    f += 4 * N3                             # diagonal inverse mass
+    f += 12 * contraction(N3, n)            # G -> GL
+    return f
+
+
+EPILOGUE_FLOPS = {"operator": 0, "lsrk_stage": 5, "ader_update": 1}
+
+
+def tck_levels(n, red):
+    """(m, number of derivative evaluations at m, projections from m) for
+    the Taylor terms j = 1..n (k + 1 = n), reduction every `red` steps."""
+    seq = []
+    m = n
+    for j in range(1, n + 1):
+        if m <= 0:
+            break
+        seq.append(m)
+        if red == 2 and j % 2 == 0:
+            m -= 2
+    return seq
+
+
+def tck_flops(n, red=2):
+    N3 = n ** 3
+    f = 12 * contraction(N3, n) + 12 * contraction(N3, n)   # GL -> G, G -> GL
+    f += 2 * 4 * N3                                          # first Taylor term
+    m = n
+    levels = [n]
+    for j in range(1, n + 1):
+        if m <= 0:
+            break
+        if m > 1:
+            m3 = m ** 3
+            f += 12 * contraction(m3, m) + 36 * m3           # derivatives + chain rule
+        if red == 2 and j % 2 == 0:
+            if m - 2 < 1:
+                break
+            r = m - 2
+            f += 4 * (contraction(r * m * m, m) + contraction(r * r * m, m) + contraction(r ** 3, m))
+            m = r
+            levels.append(m)
+        f += 2 * 4 * m ** 3                                  # accumulate the term
+    for a, b in zip(levels[1:], levels[:-1]):                # fold small -> big
+        f += 4 * (contraction(b * a * a, a) + contraction(b * b * a, a) + contraction(b ** 3, a))
+        f += 4 * b ** 3
+    return f
+
+
+def geometry_reals(n, curved=True):
+    """Per-element geometry values read by the operator: 9 metric + 2 mass
+    diagonal per cell point, 6 per face point."""
+    return 11 * n ** 3 + 36 * n ** 2
+
+
+def tck_geometry_reals(n, red=2):
+    lv = [n] if red == 0 else [m for m in range(n, 1, -2)]
+    return 11 * sum(m ** 3 for m in lv)
+
+
+def bytes_per_element(kind, n, rsize, red=2, first_stage=False):
+    vec = 4 * n ** 3 * rsize
+    conn = 6 * (4 + 1 + 1)
+    if kind == "operator":
+        return 2 * vec + geometry_reals(n) * rsize + conn
+    if kind == "lsrk_stage":
+        return (3 if first_stage else 4) * vec + geometry_reals(n) * rsize + conn
+    if kind == "ader_update":
+        return 3 * vec + geometry_reals(n) * rsize + conn
+    if kind == "tck":
+        return 2 * vec + tck_geometry_reals(n, red) * rsize
+    raise ValueError(kind)
+
+
+def flops_per_element(kind, n, red=2, nonwall_frac=1.0):
+    if kind == "tck":
+        return tck_flops(n, red)
+    return operator_flops(n, nonwall_frac=nonwall_frac) + EPILOGUE_FLOPS[kind] * 4 * n ** 3
+
+
+# --- the paper's model (Sec. 4.1), for comparison --------------------------
+def c_tensorial(k, delta):
+    """Operations of one tensor-product kernel with even-odd decomposition:
+    (2 (k+1)/2 * 2 + (k+1) + 2 floor((k-1)(k+1)/2)) (k+1)^(delta-1)."""
+    return (2 * ((k + 1) / 2) * 2 + (k + 1) + 2 * (((k - 1) * (k + 1)) // 2)) * (k + 1) ** (delta - 1)
+
+
+def paper_kernel_calls(k, d=3):
+    """(cell, face) tensor-kernel calls of M^-1, K and TCK (Table kernel-calls)."""
+    return {"mass": (2 * d, 0), "stiffness": (d * d + 4 * d, 4 * (d * d - d)),
+            "tck": (2 * d + d * (k - 1), 0)}

@@ -89,7 +89,7 @@ def cube_mesh(N, q=1, periodic=True, deform=None, frames=None):
     E = N ** 3
     h = 1.0 / N
     if frames is None:
-        frames = np.tile(np.eye(3), (E, 1, 1))
+        return _cube_mesh_aligned(N, q, periodic, deform)
     info = {"N": N, "h": h, "frames": frames, "deform": deform}
     xg = _tensor_points(gll_points_1d(q))
     nodes = np.empty((E, (q + 1) ** 3, 3))
@@ -146,11 +146,49 @@ def cube_mesh(N, q=1, periodic=True, deform=None, frames=None):
     }
 
 
+def _element_ijk(N):
+    e = np.arange(N ** 3)
+    return np.stack([e % N, (e // N) % N, e // (N * N)], axis=1)
+
+
+def _cube_mesh_aligned(N, q, periodic, deform):
+    """cube_mesh with every element's reference axes along the global axes
+    (vectorised; orientation codes are all 0)."""
+    E, h = N ** 3, 1.0 / N
+    ijk = _element_ijk(N)
+    xg = _tensor_points(gll_points_1d(q))
+    x0 = (ijk[:, None, :] + 0.5) * h + 0.5 * h * xg[None, :, :]
+    nodes = deform(x0) if deform is not None else x0
+    per = (periodic,) * 3 if isinstance(periodic, bool) else tuple(periodic)
+    nbr = np.full((E, 6), -1, np.int32)
+    nbr_face = np.full((E, 6), -1, np.int8)
+    for f in range(6):
+        d, step = f // 2, (1 if f % 2 else -1)
+        nb = ijk.copy()
+        nb[:, d] += step
+        inside = (nb[:, d] >= 0) & (nb[:, d] < N)
+        if per[d]:
+            nb[:, d] %= N
+            inside[:] = True
+        en = nb[:, 0] + N * nb[:, 1] + N * N * nb[:, 2]
+        nbr[inside, f] = en[inside]
+        nbr_face[inside, f] = f ^ 1
+    return {
+        "n_elem": E, "geom_degree": q, "nodes": np.ascontiguousarray(nodes), "nbr": nbr,
+        "nbr_face": nbr_face, "orient": np.zeros((E, 6), np.int8), "N": N, "h": h,
+        "frames": None, "deform": deform, "periodic": per,
+    }
+
+
 def solution_node_positions(mesh, k):
     """Physical positions [E, (k+1)^3, 3] of the degree-k Gauss-Lobatto
     solution nodes, through the exact (analytic) deformation map."""
     xg = _tensor_points(gll_points_1d(k))
     E = mesh["n_elem"]
+    if mesh["frames"] is None:
+        N, h = mesh["N"], mesh["h"]
+        x0 = (_element_ijk(N)[:, None, :] + 0.5) * h + 0.5 * h * xg[None, :, :]
+        return mesh["deform"](x0) if mesh["deform"] is not None else x0
     out = np.empty((E, xg.shape[0], 3))
     for e in range(E):
         x0 = _undeformed(mesh, e, xg)
