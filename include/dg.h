@@ -155,6 +155,33 @@ int dg_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int32_t reduce_eve
 int dg_energy(dg_ctx* ctx, const void* U, double* out, uintptr_t stream);
 
 /*
+ * dg_energy without allocation.  The paper has no counterpart to this call;
+ * it exists for callers that must not allocate device memory once they are
+ * running: a serving process that has promised its whole HBM budget to
+ * admitted solves, code whose memory use is fixed and checked up front, or a
+ * latency-critical loop where cudaMalloc/cudaFree would synchronise the
+ * device and stall other streams.
+ *
+ * Computes the same value as dg_energy for the device state U and writes it
+ * to *out, a caller-owned device double, on the given stream (no host
+ * synchronisation; read *out after the stream's work completes).  The
+ * partial sums go to one fixed device array of 16384 doubles (128 KB) that
+ * every GPU loading the library holds until the process exits; meshes that
+ * need more partial sums than that (more than 16384 blocks of the energy
+ * kernel, e.g. more than 49152 elements at k = 5 in FP64) are rejected with
+ * DG_EINVAL and a message naming the limit.  The call makes no cudaMalloc or
+ * cudaFree and, when it succeeds, no host allocation.
+ *
+ * The first call on a device resolves the device address of that array with
+ * the device current (this may load the library's device code), so make that
+ * first call before capturing any stream.  All calls on a device share the
+ * array: calls whose GPU work overlaps (different streams, no ordering)
+ * race on it and give wrong results; calls on one stream are safe.  Each
+ * call writes every slot it reads, so nothing from an earlier call leaks in.
+ */
+int dg_energy_noalloc(dg_ctx* ctx, const void* U, double* out, uintptr_t stream);
+
+/*
  * Sums of squares over all entries, accumulated in double in a fixed order:
  * *out_aa = sum A^2 and, when B is not NULL, *out_dd = sum (A - B)^2.
  * A, B are device states of this context. Synchronises the stream.

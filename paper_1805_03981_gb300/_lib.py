@@ -12,7 +12,7 @@ EXPORTED_SYMBOLS = [
     "dg_mesh_setup", "dg_set_coefficients", "dg_apply_operator", "dg_step_lsrk",
     "dg_step_ader", "dg_tck", "dg_energy", "dg_norms", "dg_solve_host", "dg_info",
     "dg_device_bytes", "dg_launch_count", "dg_destroy", "dg_strerror", "dg_last_error",
-    "dg_profile_enable", "dg_profile_read",
+    "dg_profile_enable", "dg_profile_read", "dg_energy_noalloc",
 ]
 KINDS = ["operator", "lsrk_stage", "ader_update", "tck", "other"]
 
@@ -64,6 +64,7 @@ def load_library():
         "dg_destroy": (None, [vp]),
         "dg_strerror": (C.c_char_p, [C.c_int]),
         "dg_profile_enable": (C.c_int, [vp, C.c_int]),
+        "dg_energy_noalloc": (C.c_int, [vp, vp, vp, st]),
         "dg_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
         "dg_last_error": (C.c_char_p, [vp]),
     }
@@ -183,6 +184,12 @@ class Solver:
         v = C.c_double()
         self._check(self.lib.dg_energy(self.ctx, self._state(U), C.byref(v), _stream(stream)))
         return v.value
+
+    def energy_noalloc(self, U, out, stream=None):
+        """Energy into the device double ``out`` (a 1-element float64 CUDA
+        tensor) without any allocation by the library; see include/dg.h."""
+        self._check(self.lib.dg_energy_noalloc(self.ctx, self._state(U), _ptr(out), _stream(stream)))
+        return out
 
     def norms(self, A, B=None, stream=None):
         aa, dd = C.c_double(), C.c_double()

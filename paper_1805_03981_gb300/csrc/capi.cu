@@ -747,3 +747,79 @@ uint64_t dg_launch_count(const dg_ctx* ctx) { return ctx ? ctx->launches : 0; }
 void dg_destroy(dg_ctx* ctx) { delete ctx; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free energy.  Same result as dg_energy, but the per-block
+// partial sums live in a fixed device array that belongs to the library
+// instead of context scratch allocated on first use, the final sum is done
+// on the device, and the result goes to a caller-owned device double.  The
+// call allocates no device memory and, when it succeeds, no host memory.
+// ---------------------------------------------------------------------------
+namespace {
+
+// 16384 doubles = 128 KB, held by every GPU that loads the library until the
+// process exits.  One slot per block of the energy kernel.
+constexpr int kNoallocMaxPartials = 16384;
+static __device__ __align__(256) double g_noalloc_partials[kNoallocMaxPartials];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[64] = {nullptr};  // device address of the array, per device
+
+// Sum part[0..n) in a fixed order (strided per thread, then a fixed tree).
+__global__ void noalloc_sum_kernel(const double* part, int n, double* out) {
+  __shared__ double r[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  r[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) r[threadIdx.x] += r[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = r[0];
+}
+
+}  // namespace
+
+extern "C" int dg_energy_noalloc(dg_ctx* ctx, const void* U, double* out, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  int rc;
+  if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
+  if (!out) return ctx->fail(DG_EINVAL, "out is NULL");
+  const int blocks = (ctx->E + ctx->epb_en - 1) / ctx->epb_en;
+  if (blocks > kNoallocMaxPartials)
+    return ctx->fail(DG_EINVAL,
+                     "dg_energy_noalloc: this mesh needs %d partial sums but the fixed buffer "
+                     "holds %d (at most %d elements at this degree and precision); use dg_energy",
+                     blocks, kNoallocMaxPartials, kNoallocMaxPartials * ctx->epb_en);
+  DeviceGuard g(ctx->dev);
+  double* part = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[ctx->dev]) {
+      // first call on this device: the host-side name of the array is only a
+      // stand-in, so look up its device address with this device current
+      void* p = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return ctx->cuda_fail(e, "cudaGetSymbolAddress of the fixed partial-sum buffer");
+      }
+      g_noalloc_addr[ctx->dev] = static_cast<double*>(p);
+    }
+    part = g_noalloc_addr[ctx->dev];
+  }
+  // every slot the sum reads is written first by this call's energy kernel,
+  // so nothing left over from an earlier call is used
+  EnergyParams p;
+  p.U = U;
+  p.geoM = ctx->geoM;
+  p.partial = part;
+  p.E = ctx->E;
+  cudaStream_t st = S(stream);
+  DG_CK(g_kt.energy[ctx->prec][ctx->n](p, ctx->epb_en, st), "energy kernel launch");
+  noalloc_sum_kernel<<<1, 256, 0, st>>>(part, blocks, out);
+  DG_CK(cudaGetLastError(), "partial-sum kernel launch");
+  ctx->launches += 2;
+  return DG_OK;
+}
