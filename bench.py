@@ -56,18 +56,28 @@ def parse():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--size", type=int, default=32, help="elements per axis")
     ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--workload", default="curved_pulse", choices=["curved_pulse", "plane_wave"])
+    ap.add_argument("--accuracy", type=int, default=0,
+                    help="instead of timing: run this many steps of each method in FP32 and FP64 "
+                         "and report the relative l2 differences and errors against the exact plane wave")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=20)
     return ap.parse_args()
 
 
-def workload(N, k):
+def workload(N, k, name="curved_pulse"):
     import synth
+    if name == "plane_wave":
+        return synth.configs.plane_wave(N=N, k=k)
     return synth.configs.curved_pulse(N=N, k=k, nsteps=200)
 
 
-def workload_desc(N, k, prec):
+def workload_desc(N, k, prec, name="curved_pulse"):
     dof = 4 * (k + 1) ** 3 * N ** 3
+    if name == "plane_wave":
+        return (f"plane_wave: periodic unit cube, {N}^3 affine hexahedra, k={k} ({dof} DoF), rho=c=1, "
+                f"p=cos(4 pi (x+y+z) - w t), Cr=0.1; bench step = 1 LSRK(5,4) step + 1 ADER(order "
+                f"{k + 1}, reduction every 2nd derivative) step, {prec.upper()}")
     return (f"curved_pulse: unit cube, {N}^3 curved hexahedra (x_i += 0.05 prod sin 2 pi x_j), "
             f"k={k} ({dof} DoF), c=1+0.5 sin2pix cos2piy, rho=1+0.3 cos2piz, walls, Gaussian "
             f"pulse sigma=0.05 (seed 2), Cr=0.1; bench step = 1 LSRK(5,4) step + 1 ADER(order {k + 1}, "
@@ -183,6 +193,40 @@ def reference_arm(args):
     return 0
 
 
+# ------------------------------------------------------------------ precision study
+def accuracy_study(args, cfg, dgw, torch):
+    """FP32 vs FP64 on the GPU after ``args.accuracy`` steps of each method,
+    and both against the exact solution at the nodes (plane wave)."""
+    k, steps = cfg["k"], args.accuracy
+    out = {"workload": workload_desc(args.size, k, "fp32/fp64", args.workload), "steps": steps,
+           "dt": cfg["dt"]}
+    exact = None
+    if cfg.get("exact") is not None:
+        exact = np.transpose(cfg["exact"](cfg["xnodes"], steps * cfg["dt"]), (0, 2, 1))
+    for method in ("lsrk", "ader"):
+        res = {}
+        for prec in (dgw.DG_FP64, dgw.DG_FP32):
+            s = dgw.Solver(cfg["mesh"], k, prec, cfg["alpha"], cfg["rho"], cfg["c"])
+            U = s.to_device(cfg["U0"])
+            t0 = time.perf_counter()
+            if method == "lsrk":
+                s.step_lsrk(U, cfg["dt"], steps)
+            else:
+                s.step_ader(U, cfg["dt"], steps, 2)
+            torch.cuda.synchronize()
+            res[prec] = (U.double().cpu().numpy(), time.perf_counter() - t0)
+            s.close()
+        u64, u32 = res[dgw.DG_FP64][0], res[dgw.DG_FP32][0]
+        r = {"fp32_vs_fp64_rel_l2": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
+             "seconds_fp64": res[dgw.DG_FP64][1], "seconds_fp32": res[dgw.DG_FP32][1]}
+        if exact is not None:
+            r["fp64_vs_exact_nodal_rel_l2"] = float(np.linalg.norm(u64 - exact) / np.linalg.norm(exact))
+            r["fp32_vs_exact_nodal_rel_l2"] = float(np.linalg.norm(u32 - exact) / np.linalg.norm(exact))
+        out[method] = r
+    print(json.dumps({"accuracy": out}))
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -214,7 +258,9 @@ def main():
 
     prec = dgw.DG_FP64 if args.prec == "fp64" else dgw.DG_FP32
     N, k = args.size, args.k
-    cfg = workload(N, k)
+    cfg = workload(N, k, args.workload)
+    if args.accuracy:
+        return accuracy_study(args, cfg, dgw, torch)
     s = dgw.Solver(cfg["mesh"], k, prec, cfg["alpha"], cfg["rho"], cfg["c"])
     dof = 4 * (k + 1) ** 3 * N ** 3
     dt = cfg["dt"]
@@ -262,7 +308,7 @@ def main():
     tot_ms, nlaunch = prof[dom]
     avg_s = tot_ms * 1e-3 / max(nlaunch, 1)
     E = N ** 3
-    nonwall = 1.0 - 1.0 / N
+    nonwall = 1.0 if args.workload == "plane_wave" else 1.0 - 1.0 / N
     flops = opcount.flops_per_element(dom, k + 1, 2, nonwall) * E
     byts = opcount.bytes_per_element(dom, k + 1, rsize, 2) * E
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
@@ -308,7 +354,7 @@ def main():
            "h2d_bytes_per_step": 2 * state_bytes, "d2h_bytes_per_step": 2 * state_bytes}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "curved_pulse":
         try:
             v, total, _ = run_oracle(4, k, 1, args.cpu_steps)
             cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -322,7 +368,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == dgw.DG_FP64 else "f32",
             "data": "synthetic",
-            "config": {"workload": workload_desc(N, k, args.prec), "elements": E, "k": k, "dof": dof,
+            "config": {"workload": workload_desc(N, k, args.prec, args.workload), "elements": E, "k": k, "dof": dof,
                        "l2": "inputs larger than L2 (state %d MB, %d MB device-resident incl. geometry), no flush"
                        % (state_bytes >> 20, s.device_bytes() >> 20),
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -214,6 +214,45 @@ int dg_solve_host(dg_ctx* ctx, int method, const void* U_host, void* U_out_host,
 int dg_profile_enable(dg_ctx* ctx, int enable);
 int dg_profile_read(dg_ctx* ctx, double* ms, int64_t* launches, int reset);
 
+/*
+ * Tiling: elements per thread block of the operator kernels (epb_op) and of
+ * the predictor (epb_tck); each element gets (k+1)^2 threads. Values <= 0
+ * leave a setting unchanged; impossible values (over 1024 threads or the
+ * shared-memory budget) give DG_EINVAL. Results do not depend on tiling.
+ */
+int dg_set_tiling(dg_ctx* ctx, int32_t epb_op, int32_t epb_tck);
+int dg_get_tiling(const dg_ctx* ctx, int32_t* epb_op, int32_t* epb_tck);
+
+/*
+ * Measure one kernel kind (DG_KIND_LSRK, DG_KIND_ADER or DG_KIND_TCK) on this
+ * context's mesh for each candidate elements-per-block value: ms_out[c] =
+ * device ms per launch (average of reps), -1 for impossible candidates. The
+ * fastest candidate is left set. Uses context scratch; synchronises.
+ */
+int dg_tune(dg_ctx* ctx, int kind, const int32_t* cand, int32_t ncand, int32_t reps,
+            double* ms_out, uintptr_t stream);
+
+/*
+ * Batched form: n independent solves (different meshes, degrees, time steps;
+ * one precision, one device) advanced together. Each phase of a step (the
+ * LSRK stages; the ADER predictor and update) is one persistent launch over
+ * work items (runs of consecutive elements of one solve, largest first) taken
+ * dynamically by the blocks; chunks of 8 steps are captured once as a CUDA
+ * graph and replayed. Every element runs the same arithmetic as in the
+ * single-solve calls, so each solve's result is bitwise identical to running
+ * it alone. U[i] are the solves' device states (updated in place), dt[i]
+ * their time steps; contexts and states must outlive the batch.
+ */
+typedef struct dg_batch dg_batch;
+int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double* dt, int32_t n,
+                    uintptr_t stream, dg_batch** out);
+int dg_batch_step_ader(dg_batch* b, int32_t nsteps, int32_t reduce_every, uintptr_t stream);
+int dg_batch_step_lsrk(dg_batch* b, int32_t nsteps, uintptr_t stream);
+int dg_batch_info(const dg_batch* b, int32_t* n_inst, int32_t* n_items, int32_t* block,
+                  int32_t* grid, uint64_t* launches);
+const char* dg_batch_last_error(const dg_batch* b);
+void dg_batch_destroy(dg_batch* b);
+
 /* Sizes: number of elements, degree, precision, bytes of one state. */
 int dg_info(const dg_ctx* ctx, int32_t* n_elem, int32_t* k, int32_t* prec,
             size_t* state_bytes);

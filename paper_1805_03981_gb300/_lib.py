@@ -13,7 +13,10 @@ EXPORTED_SYMBOLS = [
     "dg_step_ader", "dg_tck", "dg_energy", "dg_norms", "dg_solve_host", "dg_info",
     "dg_device_bytes", "dg_launch_count", "dg_destroy", "dg_strerror", "dg_last_error",
     "dg_profile_enable", "dg_profile_read", "dg_energy_noalloc",
+    "dg_set_tiling", "dg_get_tiling", "dg_tune", "dg_batch_create", "dg_batch_step_ader",
+    "dg_batch_step_lsrk", "dg_batch_info", "dg_batch_last_error", "dg_batch_destroy",
 ]
+KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
 KINDS = ["operator", "lsrk_stage", "ader_update", "tck", "other"]
 
 
@@ -65,6 +68,18 @@ def load_library():
         "dg_strerror": (C.c_char_p, [C.c_int]),
         "dg_profile_enable": (C.c_int, [vp, C.c_int]),
         "dg_energy_noalloc": (C.c_int, [vp, vp, vp, st]),
+        "dg_set_tiling": (C.c_int, [vp, C.c_int32, C.c_int32]),
+        "dg_get_tiling": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+        "dg_tune": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int32), C.c_int32, C.c_int32,
+                              C.POINTER(C.c_double), st]),
+        "dg_batch_create": (C.c_int, [C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_double), C.c_int32, st,
+                                      C.POINTER(vp)]),
+        "dg_batch_step_ader": (C.c_int, [vp, C.c_int32, C.c_int32, st]),
+        "dg_batch_step_lsrk": (C.c_int, [vp, C.c_int32, st]),
+        "dg_batch_info": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]),
+        "dg_batch_last_error": (C.c_char_p, [vp]),
+        "dg_batch_destroy": (None, [vp]),
         "dg_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
         "dg_last_error": (C.c_char_p, [vp]),
     }
@@ -218,8 +233,70 @@ class Solver:
         self._check(self.lib.dg_profile_read(self.ctx, ms, cnt, int(bool(reset))))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KINDS)}
 
+    def set_tiling(self, epb_op=0, epb_tck=0):
+        self._check(self.lib.dg_set_tiling(self.ctx, int(epb_op), int(epb_tck)))
+
+    def tiling(self):
+        a, b = C.c_int32(), C.c_int32()
+        self._check(self.lib.dg_get_tiling(self.ctx, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def tune(self, kind, candidates, reps=3, stream=None):
+        """Per-candidate ms per launch of one kernel kind; leaves the best set."""
+        cand = (C.c_int32 * len(candidates))(*candidates)
+        ms = (C.c_double * len(candidates))()
+        self._check(self.lib.dg_tune(self.ctx, int(kind), cand, len(candidates), int(reps), ms,
+                                     _stream(stream)))
+        return list(ms)
+
     def device_bytes(self):
         return int(self.lib.dg_device_bytes(self.ctx))
 
     def launch_count(self):
         return int(self.lib.dg_launch_count(self.ctx))
+
+
+class Batch:
+    """Independent solves advanced together (include/dg.h, dg_batch_*).
+
+    solvers: list of Solver (one precision); states: matching CUDA tensors
+    (kept alive by the batch); dts: time steps."""
+
+    def __init__(self, solvers, states, dts, stream=None):
+        self.lib = load_library()
+        self.solvers, self.states = list(solvers), list(states)
+        n = len(self.solvers)
+        ctxs = (C.c_void_p * n)(*[s.ctx.value for s in self.solvers])
+        ptrs = (C.c_void_p * n)(*[s._state(u).value for s, u in zip(self.solvers, self.states)])
+        dt = (C.c_double * n)(*[float(x) for x in dts])
+        b = C.c_void_p()
+        rc = self.lib.dg_batch_create(ctxs, ptrs, dt, n, _stream(stream), C.byref(b))
+        if rc != 0:
+            raise DGError(rc, self.lib.dg_last_error(None).decode())
+        self.b = b
+
+    def _check(self, rc):
+        if rc != 0:
+            raise DGError(rc, self.lib.dg_batch_last_error(self.b).decode())
+
+    def step_ader(self, nsteps, reduce_every=2, stream=None):
+        self._check(self.lib.dg_batch_step_ader(self.b, int(nsteps), int(reduce_every), _stream(stream)))
+
+    def step_lsrk(self, nsteps, stream=None):
+        self._check(self.lib.dg_batch_step_lsrk(self.b, int(nsteps), _stream(stream)))
+
+    def info(self):
+        vals = [C.c_int32() for _ in range(4)] + [C.c_uint64()]
+        self._check(self.lib.dg_batch_info(self.b, *[C.byref(v) for v in vals]))
+        return dict(zip(["instances", "items", "block", "grid", "launches"], [v.value for v in vals]))
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.dg_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

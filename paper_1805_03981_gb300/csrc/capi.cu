@@ -3,6 +3,7 @@
 // of dg_kernels.cuh and setup.cu; this file only moves pointers and sizes.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -55,9 +56,9 @@ int init_device(int dev, std::string* err) {
     return DG_EINVAL;
   }
   if (!(g_dev_ready >> dev & 1ull)) {
-    int (*up[4])(const double*, const float*) = {upload_f64_lo, upload_f64_hi, upload_f32_lo,
-                                                  upload_f32_hi};
-    for (int i = 0; i < 4; ++i) {
+    int (*up[6])(const double*, const float*) = {upload_f64_lo, upload_f64_hi, upload_f32_lo,
+                                                  upload_f32_hi, upload_batch_f64, upload_batch_f32};
+    for (int i = 0; i < 6; ++i) {
       const int e = up[i](g_tab.tab, g_tab_f);
       if (e) {
         cudaGetLastError();
@@ -823,3 +824,358 @@ extern "C" int dg_energy_noalloc(dg_ctx* ctx, const void* U, double* out, uintpt
   ctx->launches += 2;
   return DG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Tiling (elements per block) and its measurement, for the autotuner.
+// ---------------------------------------------------------------------------
+namespace {
+
+int epb_ok(const dg_ctx* ctx, int which, int epb) {
+  const int n = ctx->n;
+  if (epb < 1 || epb * n * n > 1024) return 0;
+  const int bytes = g_kt.smem[ctx->prec][n](which, 2);
+  return (size_t)epb * bytes <= 200 * 1024;
+}
+
+}  // namespace
+
+extern "C" int dg_set_tiling(dg_ctx* ctx, int32_t epb_op, int32_t epb_tck) {
+  if (!ctx) return DG_EINVAL;
+  if (epb_op > 0) {
+    if (!epb_ok(ctx, 0, epb_op)) return ctx->fail(DG_EINVAL, "elements per block %d not possible", epb_op);
+    ctx->epb_op = epb_op;
+  }
+  if (epb_tck > 0) {
+    if (!epb_ok(ctx, 1, epb_tck)) return ctx->fail(DG_EINVAL, "elements per block %d not possible", epb_tck);
+    ctx->epb_tck = epb_tck;
+  }
+  return DG_OK;
+}
+
+extern "C" int dg_get_tiling(const dg_ctx* ctx, int32_t* epb_op, int32_t* epb_tck) {
+  if (!ctx) return DG_EINVAL;
+  if (epb_op) *epb_op = ctx->epb_op;
+  if (epb_tck) *epb_tck = ctx->epb_tck;
+  return DG_OK;
+}
+
+extern "C" int dg_tune(dg_ctx* ctx, int kind, const int32_t* cand, int32_t ncand, int32_t reps,
+                       double* ms_out, uintptr_t stream) {
+  if (!ctx || !cand || !ms_out || ncand < 1 || reps < 1) return DG_EINVAL;
+  if (kind != DG_KIND_LSRK && kind != DG_KIND_TCK && kind != DG_KIND_ADER)
+    return ctx->fail(DG_EINVAL, "kind must be DG_KIND_LSRK, DG_KIND_ADER or DG_KIND_TCK");
+  DeviceGuard g(ctx->dev);
+  int rc;
+  if ((rc = ensure(ctx, &ctx->U2, "tuning state")) || (rc = ensure(ctx, &ctx->U3, "tuning state")) ||
+      (rc = ensure(ctx, &ctx->dU, "tuning register")) || (rc = ensure(ctx, &ctx->Ubar, "tuning state")))
+    return rc;
+  cudaStream_t st = S(stream);
+  DG_CK(cudaMemsetAsync(ctx->U2, 0, ctx->state_bytes(), st), "memset");
+  DG_CK(cudaMemsetAsync(ctx->dU, 0, ctx->state_bytes(), st), "memset");
+  const int which = kind == DG_KIND_TCK ? 1 : 0;
+  const int saved = which ? ctx->epb_tck : ctx->epb_op;
+  cudaEvent_t a = nullptr, b = nullptr;
+  DG_CK(cudaEventCreate(&a), "event");
+  DG_CK(cudaEventCreate(&b), "event");
+  double best = 1e300;
+  int best_epb = saved;
+  for (int c = 0; c < ncand; ++c) {
+    ms_out[c] = -1.0;
+    if (!epb_ok(ctx, which, cand[c])) continue;
+    if (which) ctx->epb_tck = cand[c]; else ctx->epb_op = cand[c];
+    OpParams p = op_params(ctx);
+    p.U = ctx->U2;
+    p.Uadd = ctx->U2;
+    p.out = ctx->U3;
+    p.dU = ctx->dU;
+    p.cA = 0.5;
+    p.cB = 0.5;
+    p.dt = 1e-3;
+    for (int r = -1; r < reps; ++r) {  // one untimed launch first
+      if (r == 0) cudaEventRecord(a, st);
+      if (kind == DG_KIND_TCK)
+        rc = launch_tck(ctx, ctx->U2, ctx->Ubar, 1e-3, 2, st);
+      else
+        rc = launch_op(ctx, p, kind == DG_KIND_LSRK ? EPI_LSRK : EPI_ADD, st);
+      if (rc) break;
+    }
+    if (rc) break;
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    ms_out[c] = ms / reps;
+    if (ms_out[c] < best) {
+      best = ms_out[c];
+      best_epb = cand[c];
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (which) ctx->epb_tck = best_epb; else ctx->epb_op = best_epb;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: independent solves advanced together by persistent launches.
+// ---------------------------------------------------------------------------
+struct dg_batch {
+  int dev = 0, prec = 0, n = 0;
+  std::vector<dg_ctx*> ctx;
+  std::vector<void*> allocs;
+  BatchInst* inst = nullptr;
+  BatchItem* items_op = nullptr;
+  BatchItem* items_tck = nullptr;
+  int n_op = 0, n_tck = 0;
+  int* counters = nullptr;
+  int block_op = 0, block_tck = 0, grid_op = 0, grid_tck[3] = {0, 0, 0};
+  size_t smem_op = 0, smem_tck[3] = {0, 0, 0};
+  cudaStream_t cap = nullptr;       // private stream used for graph capture
+  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // ADER red 0, ADER red 2, LSRK
+  uint64_t launches = 0;
+  size_t dev_bytes = 0;
+  std::string err;
+  static constexpr int kChunk = 8;          // steps per captured graph
+  static constexpr int kCounters = 5 * kChunk;
+
+  int fail(int code, const char* msg) {
+    err = msg;
+    return code;
+  }
+  ~dg_batch() {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(dev);
+    for (auto& g : gexec)
+      if (g) cudaGraphExecDestroy(g);
+    if (cap) cudaStreamDestroy(cap);
+    for (void* p : allocs) cudaFree(p);
+    cudaSetDevice(cur);
+  }
+};
+
+namespace {
+
+int batch_alloc(dg_batch* b, void** p, size_t bytes) {
+  if (cudaMalloc(p, bytes ? bytes : 16) != cudaSuccess) {
+    cudaGetLastError();
+    return b->fail(DG_ENOMEM, "cudaMalloc for batch tables failed");
+  }
+  b->allocs.push_back(*p);
+  b->dev_bytes += bytes;
+  return DG_OK;
+}
+
+// Launch the phases of `steps` steps of one method starting at counter slot 0.
+int batch_launch_steps(dg_batch* b, int method, int red, int steps, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b->counters, 0, sizeof(int) * dg_batch::kCounters, st);
+  if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
+  int slot = 0;
+  const int ti = red == 2 ? 1 : 2;
+  for (int s = 0; s < steps; ++s) {
+    if (method == 1) {  // ADER: predictor, then update
+      e = (b->prec == DG_FP64 ? launch_batch_tck_f64 : launch_batch_tck_f32)(
+          b->items_tck, b->n_tck, b->inst, red, b->counters + slot++, b->grid_tck[ti], b->block_tck,
+          b->smem_tck[ti], st);
+      if (e == cudaSuccess)
+        e = (b->prec == DG_FP64 ? launch_batch_op_f64 : launch_batch_op_f32)(
+            b->items_op, b->n_op, b->inst, 5, b->counters + slot++, b->grid_op, b->block_op, b->smem_op, st);
+      b->launches += 2;
+    } else {
+      for (int ph = 0; ph < 5 && e == cudaSuccess; ++ph) {
+        e = (b->prec == DG_FP64 ? launch_batch_op_f64 : launch_batch_op_f32)(
+            b->items_op, b->n_op, b->inst, ph, b->counters + slot++, b->grid_op, b->block_op, b->smem_op,
+            st);
+        b->launches += 1;
+      }
+    }
+    if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
+  }
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double* dt, int32_t n,
+                               uintptr_t stream, dg_batch** out) {
+  if (!out) return DG_EINVAL;
+  *out = nullptr;
+  g_setup_err.clear();
+  if (!ctxs || !U || !dt || n < 1) {
+    g_setup_err = "dg_batch_create: NULL arrays or n < 1";
+    return DG_EINVAL;
+  }
+  const int prec = ctxs[0]->prec, dev = ctxs[0]->dev;
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i] || ctxs[i]->prec != prec || ctxs[i]->dev != dev) {
+      g_setup_err = "dg_batch_create: contexts must be non-NULL, of one precision and one device";
+      return DG_EINVAL;
+    }
+    if (!(dt[i] > 0.0)) {
+      g_setup_err = "dg_batch_create: dt must be positive";
+      return DG_EINVAL;
+    }
+    if (check_state_ptr(ctxs[i], U[i], "U")) {
+      g_setup_err = ctxs[i]->err;
+      return DG_EINVAL;
+    }
+  }
+  DeviceGuard g(dev);
+  dg_batch* b = new (std::nothrow) dg_batch();
+  if (!b) return DG_ENOMEM;
+  b->dev = dev;
+  b->prec = prec;
+  b->n = n;
+  auto bail = [&](int code) {
+    g_setup_err = b->err;
+    delete b;
+    return code;
+  };
+  std::vector<BatchInst> hinst(n);
+  std::vector<BatchItem> hop, htck;
+  const size_t rs = prec == DG_FP64 ? 8 : 4;
+  for (int i = 0; i < n; ++i) {
+    dg_ctx* c = ctxs[i];
+    int rc;
+    if ((rc = ensure(c, &c->U2, "LSRK state")) || (rc = ensure(c, &c->U3, "LSRK state")) ||
+        (rc = ensure(c, &c->dU, "LSRK register")) || (rc = ensure(c, &c->Ubar, "ADER predictor"))) {
+      b->err = c->err;
+      return bail(rc);
+    }
+    BatchInst& I = hinst[i];
+    std::memset(&I, 0, sizeof(I));
+    void* const chain[6] = {U[i], c->U2, c->U3, c->U2, c->U3, U[i]};
+    for (int s = 0; s < 5; ++s) {
+      I.op[s] = op_params(c);
+      I.op[s].U = chain[s];
+      I.op[s].Uadd = chain[s];
+      I.op[s].out = chain[s + 1];
+      I.op[s].dU = c->dU;
+      I.op[s].cA = kLsrkA[s];
+      I.op[s].cB = kLsrkB[s];
+      I.op[s].dt = dt[i];
+      I.op[s].first = s == 0;
+    }
+    I.op[5] = op_params(c);
+    I.op[5].U = c->Ubar;
+    I.op[5].Uadd = U[i];
+    I.op[5].out = U[i];
+    I.tck.U = U[i];
+    I.tck.Ubar = c->Ubar;
+    I.tck.geoT = c->geoT;
+    I.tck.geoT_stride = c->tstride;
+    I.tck.E = c->E;
+    double fact = 1.0;
+    for (int j = 0; j <= c->n; ++j) {
+      fact *= (j + 1);
+      I.tck.coef[j] = std::pow(dt[i], j + 1) / fact;
+    }
+    const int n2 = c->n * c->n;
+    for (int e0 = 0; e0 < c->E; e0 += c->epb_op)
+      hop.push_back({i, e0, std::min(c->epb_op, c->E - e0), c->n, c->epb_op});
+    for (int e0 = 0; e0 < c->E; e0 += c->epb_tck)
+      htck.push_back({i, e0, std::min(c->epb_tck, c->E - e0), c->n, c->epb_tck});
+    b->block_op = std::max(b->block_op, c->epb_op * n2);
+    b->block_tck = std::max(b->block_tck, c->epb_tck * n2);
+    b->smem_op = std::max(b->smem_op, (size_t)c->epb_op * g_kt.smem[prec][c->n](0, 2));
+    b->smem_tck[1] = std::max(b->smem_tck[1], (size_t)c->epb_tck * g_kt.smem[prec][c->n](1, 2));
+    b->smem_tck[2] = std::max(b->smem_tck[2], (size_t)c->epb_tck * g_kt.smem[prec][c->n](1, 0));
+    b->ctx.push_back(c);
+  }
+  (void)rs;
+  // largest work first: per-element cost grows like n^4
+  auto cost = [](const BatchItem& w) { return (double)w.ne * w.n * w.n * w.n * w.n; };
+  std::stable_sort(hop.begin(), hop.end(), [&](const BatchItem& x, const BatchItem& y) { return cost(x) > cost(y); });
+  std::stable_sort(htck.begin(), htck.end(), [&](const BatchItem& x, const BatchItem& y) { return cost(x) > cost(y); });
+  b->n_op = (int)hop.size();
+  b->n_tck = (int)htck.size();
+  int rc;
+  if ((rc = batch_alloc(b, (void**)&b->inst, sizeof(BatchInst) * n)) ||
+      (rc = batch_alloc(b, (void**)&b->items_op, sizeof(BatchItem) * hop.size())) ||
+      (rc = batch_alloc(b, (void**)&b->items_tck, sizeof(BatchItem) * htck.size())) ||
+      (rc = batch_alloc(b, (void**)&b->counters, sizeof(int) * dg_batch::kCounters)))
+    return bail(rc);
+  cudaStream_t st = S(stream);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(b->inst, hinst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(b->items_op, hop.data(), sizeof(BatchItem) * hop.size(), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(b->items_tck, htck.data(), sizeof(BatchItem) * htck.size(), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaStreamSynchronize(st))) {
+    b->fail(DG_ECUDA, cudaGetErrorString(e));
+    return bail(DG_ECUDA);
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto occ = prec == DG_FP64 ? batch_occupancy_f64 : batch_occupancy_f32;
+  b->grid_op = sms * std::max(1, occ(0, b->block_op, b->smem_op));
+  b->grid_tck[1] = sms * std::max(1, occ(1, b->block_tck, b->smem_tck[1]));
+  b->grid_tck[2] = sms * std::max(1, occ(2, b->block_tck, b->smem_tck[2]));
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    b->fail(DG_ECUDA, "stream creation failed");
+    return bail(DG_ECUDA);
+  }
+  *out = b;
+  return DG_OK;
+}
+
+static int batch_steps(dg_batch* b, int method, int red, int32_t nsteps, uintptr_t stream) {
+  DeviceGuard g(b->dev);
+  cudaStream_t st = S(stream);
+  const int gi = method == 0 ? 2 : (red == 2 ? 1 : 0);
+  const int chunks = nsteps / dg_batch::kChunk, rest = nsteps % dg_batch::kChunk;
+  if (chunks > 0 && !b->gexec[gi]) {
+    // capture kChunk steps once; the graph is replayed on the caller's stream
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
+    const uint64_t l0 = b->launches;
+    int rc = batch_launch_steps(b, method, red, dg_batch::kChunk, b->cap);
+    b->launches = l0;
+    e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&b->gexec[gi], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      b->gexec[gi] = nullptr;
+      return b->fail(DG_ECUDA, cudaGetErrorString(e));
+    }
+  }
+  for (int c = 0; c < chunks; ++c) {
+    cudaError_t e = cudaGraphLaunch(b->gexec[gi], st);
+    if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
+    b->launches += (uint64_t)dg_batch::kChunk * (method == 0 ? 5 : 2);
+  }
+  if (rest) return batch_launch_steps(b, method, red, rest, st);
+  return DG_OK;
+}
+
+extern "C" int dg_batch_step_ader(dg_batch* b, int32_t nsteps, int32_t red, uintptr_t stream) {
+  if (!b || nsteps < 0) return DG_EINVAL;
+  if (red != 0 && red != 2) return b->fail(DG_EUNSUPPORTED, "reduce_every must be 0 or 2 in this build");
+  return batch_steps(b, 1, red, nsteps, stream);
+}
+
+extern "C" int dg_batch_step_lsrk(dg_batch* b, int32_t nsteps, uintptr_t stream) {
+  if (!b || nsteps < 0) return DG_EINVAL;
+  return batch_steps(b, 0, 0, nsteps, stream);
+}
+
+extern "C" int dg_batch_info(const dg_batch* b, int32_t* n_inst, int32_t* n_items, int32_t* block,
+                             int32_t* grid, uint64_t* launches) {
+  if (!b) return DG_EINVAL;
+  if (n_inst) *n_inst = b->n;
+  if (n_items) *n_items = b->n_op;
+  if (block) *block = b->block_op;
+  if (grid) *grid = b->grid_op;
+  if (launches) *launches = b->launches;
+  return DG_OK;
+}
+
+extern "C" const char* dg_batch_last_error(const dg_batch* b) { return b ? b->err.c_str() : ""; }
+
+extern "C" void dg_batch_destroy(dg_batch* b) { delete b; }

@@ -58,4 +58,19 @@ int upload_f64_hi(const double* d, const float* f);
 int upload_f32_lo(const double* d, const float* f);
 int upload_f32_hi(const double* d, const float* f);
 
+struct BatchItem;
+struct BatchInst;
+cudaError_t launch_batch_op_f64(const BatchItem* items, int nitems, const BatchInst* inst, int phase,
+                                int* counter, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_op_f32(const BatchItem* items, int nitems, const BatchInst* inst, int phase,
+                                int* counter, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_tck_f64(const BatchItem* items, int nitems, const BatchInst* inst, int red,
+                                 int* counter, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_tck_f32(const BatchItem* items, int nitems, const BatchInst* inst, int red,
+                                 int* counter, int grid, int block, size_t smem, cudaStream_t st);
+int batch_occupancy_f64(int which, int block, size_t smem);
+int batch_occupancy_f32(int which, int block, size_t smem);
+int upload_batch_f64(const double* d, const float* f);
+int upload_batch_f32(const double* d, const float* f);
+
 }  // namespace dg

@@ -205,17 +205,15 @@ __device__ __forceinline__ void cell_face_dir(const Real (&u)[4][N], Real (&r)[4
   }
 }
 
+// One block's share of the operator: elements e0 .. e0+ne-1, (k+1)^2
+// threads each (threads beyond ne (k+1)^2 only help with the flat copies).
+// Every element's arithmetic is independent of e0, ne and the block shape.
 template <int N, typename Real, int EPI>
-__global__ void op_kernel(const OpParams p) {
+__device__ __forceinline__ void op_block(const OpParams& p, const int e0, const int ne, Real* sm) {
   constexpr int N2 = N * N, N3 = N2 * N;
   constexpr int SE = op_smem_per_elem<N>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sm = reinterpret_cast<Real*>(smem_raw);
-  const int epb = blockDim.x / N2;
   const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
   const int a = t % N, b = t / N;
-  const int e0 = blockIdx.x * epb;
-  const int ne = min(epb, p.E - e0);
   const int e = e0 + le;
   const bool act = le < ne;
   Real* su = sm + le * SE;
@@ -380,6 +378,14 @@ __global__ void op_kernel(const OpParams p) {
   }
 }
 
+template <int N, typename Real, int EPI>
+__global__ void op_kernel(const OpParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int epb = blockDim.x / (N * N);
+  const int e0 = blockIdx.x * epb;
+  op_block<N, Real, EPI>(p, e0, min(epb, p.E - e0), reinterpret_cast<Real*>(smem_raw));
+}
+
 // ---------------------------------------------------------------------------
 // Taylor-Cauchy-Kowalevski predictor (Sec. 2.3 Eq. (6), Sec. 3.2 Alg. 2,
 // Sec. 3.3 Alg. 3).
@@ -511,19 +517,22 @@ __device__ __forceinline__ void tck_accumulate(Real* acc, const Real* T, int m3,
   }
 }
 
+// One block's share of the predictor: elements e0 .. e0+ne-1 of a block
+// laid out for epb elements.  Threads of element slots >= epb (a block sized
+// for another degree) take no lines and touch no shared memory, but still
+// reach every barrier.
 template <int N, typename Real, int RED>
-__global__ void tck_kernel(const TckParams p) {
+__device__ __forceinline__ void tck_block(const TckParams& p, const int e0, const int ne, const int epb,
+                                          Real* sm) {
   constexpr int N2 = N * N, N3 = N2 * N;
   constexpr int SE = tck_smem_per_elem<N, RED>();
   constexpr int NL = tck_level_count<N, RED>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sm = reinterpret_cast<Real*>(smem_raw);
-  const int epb = blockDim.x / N2;
-  const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
-  const int e0 = blockIdx.x * epb;
-  const int ne = min(epb, p.E - e0);
+  const int le0 = threadIdx.x / N2;
+  const bool own = le0 < epb;
+  const int le = own ? le0 : 0;
+  const int t = own ? (int)threadIdx.x - le0 * N2 : (1 << 28);  // no line for non-owners
   const int e = e0 + le;
-  const bool act = le < ne;
+  const bool act = le0 < ne;
   Real* s0 = sm + le * SE;  // T buffers (field stride N3)
   Real* s1 = s0 + 4 * N3;
   Real* acc = s1 + 4 * N3;  // per-level accumulators (field stride m^3)
@@ -634,6 +643,14 @@ __global__ void tck_kernel(const TckParams p) {
   }
 }
 
+template <int N, typename Real, int RED>
+__global__ void tck_kernel(const TckParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int epb = blockDim.x / (N * N);
+  const int e0 = blockIdx.x * epb;
+  tck_block<N, Real, RED>(p, e0, min(epb, p.E - e0), epb, reinterpret_cast<Real*>(smem_raw));
+}
+
 // ---------------------------------------------------------------------------
 // Energy 1/2 U^T M U (Gauss rule, diagonal mass in G) and sums of squares.
 // Each block writes one partial; a second pass sums the partials in order.
@@ -682,6 +699,86 @@ __global__ void energy_kernel(const EnergyParams p) {
     double tot = 0.0;
     for (int i = 0; i < (int)blockDim.x; ++i) tot += red[i];
     p.partial[blockIdx.x] = 0.5 * tot;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched form: many independent solves (different meshes, degrees, time
+// steps) advanced by one persistent launch per phase.  A work item is a run
+// of consecutive elements of one instance; blocks take items from a counter
+// (dynamic scheduling, no waiting) and run the same per-element code as the
+// single-solve kernels, so each instance's result does not depend on what
+// else is in the batch.
+// ---------------------------------------------------------------------------
+struct BatchItem {
+  int inst, e0, ne, n, epb;
+};
+// per instance: operator parameters of the five LSRK stages and of the ADER
+// update, and the predictor parameters
+struct BatchInst {
+  OpParams op[6];
+  TckParams tck;
+};
+
+template <typename Real>
+__global__ void batch_op_kernel(const BatchItem* __restrict__ items, int nitems,
+                                const BatchInst* __restrict__ inst, int phase, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BatchItem w = items[it];
+    const OpParams& p = inst[w.inst].op[phase];
+    const bool lsrk = phase < 5;
+    switch (w.n) {
+#define DG_BATCH_OP(NN)                                          \
+  case NN:                                                       \
+    if (lsrk)                                                    \
+      op_block<NN, Real, EPI_LSRK>(p, w.e0, w.ne, sm);           \
+    else                                                         \
+      op_block<NN, Real, EPI_ADD>(p, w.e0, w.ne, sm);            \
+    break;
+      DG_BATCH_OP(2) DG_BATCH_OP(3) DG_BATCH_OP(4) DG_BATCH_OP(5) DG_BATCH_OP(6) DG_BATCH_OP(7)
+      DG_BATCH_OP(8)
+#undef DG_BATCH_OP
+      default:
+        break;
+    }
+    __syncthreads();  // shared memory is reused by the next item
+  }
+}
+
+template <typename Real, int RED>
+__global__ void batch_tck_kernel(const BatchItem* __restrict__ items, int nitems,
+                                 const BatchInst* __restrict__ inst, int* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BatchItem w = items[it];
+    const TckParams& p = inst[w.inst].tck;
+    switch (w.n) {
+#define DG_BATCH_TCK(NN)                                   \
+  case NN:                                                 \
+    tck_block<NN, Real, RED>(p, w.e0, w.ne, w.epb, sm);    \
+    break;
+      DG_BATCH_TCK(2) DG_BATCH_TCK(3) DG_BATCH_TCK(4) DG_BATCH_TCK(5) DG_BATCH_TCK(6)
+      DG_BATCH_TCK(7) DG_BATCH_TCK(8)
+#undef DG_BATCH_TCK
+      default:
+        break;
+    }
+    __syncthreads();
   }
 }
 

@@ -1,0 +1,83 @@
+"""Batched form: independent solves (mixed degrees and sizes) advanced by
+persistent launches give, for every solve, exactly (bitwise) the state the
+single-solve path gives, and that state matches the oracle."""
+import numpy as np
+import pytest
+
+import synth
+import paper_1805_03981_gb300 as dgw
+from gpu_helpers import rel_l2, pair
+
+pytestmark = pytest.mark.gpu
+
+
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _mix(seed, count, prec):
+    rng = np.random.default_rng(seed)
+    cfgs = []
+    ks = [2, 3, 4, 5, 6, 7]
+    for i in range(count):
+        k = ks[i % len(ks)]
+        N = int(rng.integers(2, 5 if k >= 6 else 6))
+        cfgs.append(synth.configs.random_instance(seed * 1000 + i, N=N, k=k, nsteps=10))
+    solvers = [dgw.Solver(c["mesh"], c["k"], prec, c["alpha"], c["rho"], c["c"]) for c in cfgs]
+    return cfgs, solvers
+
+
+@pytest.mark.parametrize("prec", [dgw.DG_FP64, dgw.DG_FP32])
+@pytest.mark.parametrize("method", ["ader", "lsrk"])
+def test_batch_bitwise_equals_alone(prec, method):
+    torch = _cuda()
+    cfgs, solvers = _mix(3, 9, prec)
+    steps = 11                                     # one captured chunk of 8 and 3 direct steps
+    alone = []
+    for c, s in zip(cfgs, solvers):
+        U = s.to_device(c["U0"])
+        if method == "ader":
+            s.step_ader(U, c["dt"], steps, 2)
+        else:
+            s.step_lsrk(U, c["dt"], steps)
+        alone.append(U)
+    states = [s.to_device(c["U0"]) for c, s in zip(cfgs, solvers)]
+    b = dgw.Batch(solvers, states, [c["dt"] for c in cfgs])
+    if method == "ader":
+        b.step_ader(steps, 2)
+    else:
+        b.step_lsrk(steps)
+    torch.cuda.synchronize()
+    for i, (u, v) in enumerate(zip(states, alone)):
+        assert torch.equal(u, v), (i, cfgs[i]["k"], (u - v).abs().max().item())
+    info = b.info()
+    assert info["instances"] == 9 and info["launches"] > 0
+    b.close()
+
+
+def test_batch_matches_oracle_and_tiling_invariance():
+    torch = _cuda()
+    cfgs, solvers = _mix(5, 3, dgw.DG_FP64)
+    c0, s0 = cfgs[0], solvers[0]
+    s0.set_tiling(1, 1)                            # a different tiling changes nothing
+    states = [s.to_device(c["U0"]) for c, s in zip(cfgs, solvers)]
+    b = dgw.Batch(solvers, states, [c["dt"] for c in cfgs])
+    b.step_ader(3, 2)
+    torch.cuda.synchronize()
+    _, o = pair(c0)
+    ref = o.ader(c0["U0"], c0["dt"], 3, 2)
+    assert rel_l2(states[0].cpu().numpy(), ref) < 1e-12
+    b.close()
+
+
+def test_tune_sets_a_valid_tiling():
+    torch = _cuda()
+    cfg = synth.configs.curved_pulse(N=4, k=4)
+    s = dgw.Solver(cfg["mesh"], 4, dgw.DG_FP32, 1.0, cfg["rho"], cfg["c"])
+    ms = s.tune(dgw.KIND_LSRK, [1, 2, 3, 5, 40], reps=2)
+    assert ms[-1] == -1.0                          # 40 x 25 threads > 1024: impossible
+    assert all(m > 0 for m in ms[:-1])
+    assert s.tiling()[0] == [1, 2, 3, 5][int(np.argmin(ms[:-1]))]
