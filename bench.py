@@ -56,7 +56,9 @@ def parse():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--size", type=int, default=32, help="elements per axis")
     ap.add_argument("--k", type=int, default=5)
-    ap.add_argument("--workload", default="curved_pulse", choices=["curved_pulse", "plane_wave"])
+    ap.add_argument("--workload", default="curved_pulse", choices=["curved_pulse", "plane_wave", "batched"])
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--autotune", default="", help="autotune table (JSON) to apply to every solver")
     ap.add_argument("--accuracy", type=int, default=0,
                     help="instead of timing: run this many steps of each method in FP32 and FP64 "
                          "and report the relative l2 differences and errors against the exact plane wave")
@@ -227,6 +229,102 @@ def accuracy_study(args, cfg, dgw, torch):
     return 0
 
 
+# ------------------------------------------------------------------ batched form
+def _gen_one(seed):
+    import synth
+    c = synth.configs.random_instance(seed, nsteps=500)
+    c.pop("xnodes", None)
+    c["mesh"].pop("deform", None)
+    return c
+
+
+def generate_instances(seeds, workers=None):
+    """Seeded instances built in a process pool started with 'spawn' (safe
+    after CUDA is initialised in this process)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    workers = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_one, seeds, chunksize=4))
+
+
+def batched_bench(args, dgw, torch):
+    """256 independent seeded solves (N ~ U{4..24} elements per axis, k ~
+    U{2..7}, random smooth rho and c in [0.55, 1.95], curving <= 0.05, walls,
+    Gaussian pulses), FP32 ADER (order k+1, reduction every 2nd derivative).
+    Times the batched persistent form against the same solves run one at a
+    time in FP32 and in FP64."""
+    import synth
+    from paper_1805_03981_gb300 import autotune
+    table = autotune.load(args.autotune) if args.autotune else None
+    n = args.instances
+    t_gen = time.perf_counter()
+    cfgs = generate_instances([4 * 10 ** 6 + i for i in range(n)])
+    dof = [4 * (c["k"] + 1) ** 3 * c["mesh"]["n_elem"] for c in cfgs]
+    total = sum(dof)
+    steps = args.steps
+    t_gen = time.perf_counter() - t_gen
+    out = {"workload": f"batched: {n} instances, N~U{{4..24}}^3 curved hexahedra, k~U{{2..7}}, seeded rho/c/pulses, "
+                       f"ADER order k+1", "total_dof": total, "steps": steps,
+           "k_histogram": {str(k): sum(1 for c in cfgs if c["k"] == k) for k in range(2, 8)}}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    t_setup = time.perf_counter()
+    solvers = [dgw.Solver(c["mesh"], c["k"], dgw.DG_FP32, 1.0, c["rho"], c["c"]) for c in cfgs]
+    if table:
+        for s in solvers:
+            autotune.apply(s, table)
+    states = [s.to_device(c["U0"]) for s, c in zip(solvers, cfgs)]
+    out["setup_s"] = time.perf_counter() - t_setup
+    out["host_generation_s"] = t_gen
+    b = dgw.Batch(solvers, states, [c["dt"] for c in cfgs])
+    b.step_ader(8, 2)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    b.step_ader(steps, 2)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    out["batched_fp32"] = {"dofs_per_s": total * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                           "info": b.info()}
+    # one solve at a time, FP32, same steps
+    for s, c, U in zip(solvers, cfgs, states):
+        s.step_ader(U, c["dt"], 2, 2)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for s, c, U in zip(solvers, cfgs, states):
+        s.step_ader(U, c["dt"], steps, 2)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = ev0.elapsed_time(ev1)
+    out["one_at_a_time_fp32"] = {"dofs_per_s": total * steps / (ms1 * 1e-3), "ms_per_step": ms1 / steps}
+    b.close()
+    for s in solvers:
+        s.close()
+    del states
+    # one solve at a time, FP64 (contexts created and freed one by one)
+    st64 = max(1, steps // 4)
+    ms64 = 0.0
+    for c in cfgs:
+        s = dgw.Solver(c["mesh"], c["k"], dgw.DG_FP64, 1.0, c["rho"], c["c"])
+        U = s.to_device(c["U0"])
+        s.step_ader(U, c["dt"], 1, 2)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.step_ader(U, c["dt"], st64, 2)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms64 += ev0.elapsed_time(ev1)
+        s.close()
+    out["one_at_a_time_fp64"] = {"dofs_per_s": total * st64 / (ms64 * 1e-3), "ms_per_step": ms64 / st64}
+    out["speedup_batched_fp32_vs_fp64_one_at_a_time"] = (out["batched_fp32"]["dofs_per_s"]
+                                                          / out["one_at_a_time_fp64"]["dofs_per_s"])
+    out["speedup_batched_vs_one_at_a_time_fp32"] = (out["batched_fp32"]["dofs_per_s"]
+                                                     / out["one_at_a_time_fp32"]["dofs_per_s"])
+    print(json.dumps({"batched": out}))
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     args = parse()
@@ -257,6 +355,8 @@ def main():
         return float(t.item())
 
     prec = dgw.DG_FP64 if args.prec == "fp64" else dgw.DG_FP32
+    if args.workload == "batched":
+        return batched_bench(args, dgw, torch)
     N, k = args.size, args.k
     cfg = workload(N, k, args.workload)
     if args.accuracy:

@@ -234,11 +234,13 @@ int dg_tune(dg_ctx* ctx, int kind, const int32_t* cand, int32_t ncand, int32_t r
 
 /*
  * Batched form: n independent solves (different meshes, degrees, time steps;
- * one precision, one device) advanced together. Each phase of a step (the
- * LSRK stages; the ADER predictor and update) is one persistent launch over
- * work items (runs of consecutive elements of one solve, largest first) taken
- * dynamically by the blocks; chunks of 8 steps are captured once as a CUDA
- * graph and replayed. Every element runs the same arithmetic as in the
+ * one precision, one device) advanced together. For each degree present,
+ * each phase of a step (the LSRK stages; the ADER predictor and update) is
+ * one persistent launch over work items (runs of consecutive elements of one
+ * solve; largest solves first, each in element order) taken dynamically by
+ * the blocks; the degrees run as
+ * concurrent branches forked from and joined to the caller's stream. Chunks
+ * of 8 steps are captured once as a CUDA graph and replayed. Every element runs the same arithmetic as in the
  * single-solve calls, so each solve's result is bitwise identical to running
  * it alone. U[i] are the solves' device states (updated in place), dt[i]
  * their time steps; contexts and states must outlive the batch.

@@ -264,11 +264,11 @@ int validate_mesh(const dg_mesh_desc* m, std::string* err) {
   return DG_OK;
 }
 
-int pick_epb(int n, int bytes_per_elem, int target_threads) {
+int pick_epb(int n, int bytes_per_elem, int target_threads, int max_threads) {
   int epb = target_threads / (n * n);
   if (epb < 1) epb = 1;
   const int smem_lim = 200 * 1024;
-  while (epb > 1 && epb * bytes_per_elem > smem_lim) --epb;
+  while (epb > 1 && (epb * bytes_per_elem > smem_lim || epb * n * n > max_threads)) --epb;
   return epb;
 }
 
@@ -553,9 +553,9 @@ int dg_mesh_setup(const dg_mesh_desc* m, int k, int prec, double alpha, uintptr_
   DG_UP(ctx->xq, hxq.data(), sizeof(double) * (DG_NMAX + 2));
 #undef DG_UP
   const int pi = ctx->prec;
-  ctx->epb_op = pick_epb(n, g_kt.smem[pi][n](0, 2), 128);
-  ctx->epb_tck = pick_epb(n, g_kt.smem[pi][n](1, 2), 128);
-  ctx->epb_en = pick_epb(n, g_kt.smem[pi][n](2, 2), 128);
+  ctx->epb_op = pick_epb(n, g_kt.smem[pi][n](0, 2), 128, g_kt.maxthr[pi][n](0));
+  ctx->epb_tck = pick_epb(n, g_kt.smem[pi][n](1, 2), 128, g_kt.maxthr[pi][n](1));
+  ctx->epb_en = pick_epb(n, g_kt.smem[pi][n](2, 2), 128, g_kt.maxthr[pi][n](2));
   if ((rc = run_setup(ctx, st))) return bail(rc);
   *out = ctx;
   return DG_OK;
@@ -832,7 +832,7 @@ namespace {
 
 int epb_ok(const dg_ctx* ctx, int which, int epb) {
   const int n = ctx->n;
-  if (epb < 1 || epb * n * n > 1024) return 0;
+  if (epb < 1 || epb * n * n > 1024 || epb * n * n > g_kt.maxthr[ctx->prec][n](which)) return 0;
   const int bytes = g_kt.smem[ctx->prec][n](which, 2);
   return (size_t)epb * bytes <= 200 * 1024;
 }
@@ -899,7 +899,12 @@ extern "C" int dg_tune(dg_ctx* ctx, int kind, const int32_t* cand, int32_t ncand
         rc = launch_op(ctx, p, kind == DG_KIND_LSRK ? EPI_LSRK : EPI_ADD, st);
       if (rc) break;
     }
-    if (rc) break;
+    if (rc) {  // launch configuration refused: not a candidate
+      cudaGetLastError();
+      rc = DG_OK;
+      cudaStreamSynchronize(st);
+      continue;
+    }
     cudaEventRecord(b, st);
     cudaEventSynchronize(b);
     float ms = 0.f;
@@ -919,23 +924,32 @@ extern "C" int dg_tune(dg_ctx* ctx, int kind, const int32_t* cand, int32_t ncand
 // ---------------------------------------------------------------------------
 // Batched form: independent solves advanced together by persistent launches.
 // ---------------------------------------------------------------------------
-struct dg_batch {
-  int dev = 0, prec = 0, n = 0;
-  std::vector<dg_ctx*> ctx;
-  std::vector<void*> allocs;
-  BatchInst* inst = nullptr;
+// Solves of one degree in a batch: their work items and launch shape.
+struct BatchGroup {
+  int n = 0;
   BatchItem* items_op = nullptr;
   BatchItem* items_tck = nullptr;
   int n_op = 0, n_tck = 0;
-  int* counters = nullptr;
   int block_op = 0, block_tck = 0, grid_op = 0, grid_tck[3] = {0, 0, 0};
   size_t smem_op = 0, smem_tck[3] = {0, 0, 0};
-  cudaStream_t cap = nullptr;       // private stream used for graph capture
+  cudaStream_t s = nullptr;  // branch stream
+  cudaEvent_t done = nullptr;
+};
+
+struct dg_batch {
+  int dev = 0, prec = 0, n = 0;
+  std::vector<dg_ctx*> ctx;
+  std::vector<BatchGroup> groups;
+  std::vector<void*> allocs;
+  BatchInst* inst = nullptr;
+  int* counters = nullptr;  // kCounters per group
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;  // private stream used for graph capture
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // ADER red 0, ADER red 2, LSRK
   uint64_t launches = 0;
   size_t dev_bytes = 0;
   std::string err;
-  static constexpr int kChunk = 8;          // steps per captured graph
+  static constexpr int kChunk = 8;  // steps per captured graph
   static constexpr int kCounters = 5 * kChunk;
 
   int fail(int code, const char* msg) {
@@ -948,6 +962,11 @@ struct dg_batch {
     cudaSetDevice(dev);
     for (auto& g : gexec)
       if (g) cudaGraphExecDestroy(g);
+    for (auto& g : groups) {
+      if (g.s) cudaStreamDestroy(g.s);
+      if (g.done) cudaEventDestroy(g.done);
+    }
+    if (fork) cudaEventDestroy(fork);
     if (cap) cudaStreamDestroy(cap);
     for (void* p : allocs) cudaFree(p);
     cudaSetDevice(cur);
@@ -966,31 +985,37 @@ int batch_alloc(dg_batch* b, void** p, size_t bytes) {
   return DG_OK;
 }
 
-// Launch the phases of `steps` steps of one method starting at counter slot 0.
+// `steps` steps of one method: the degree groups branch off `st`, each runs
+// its phases on its own stream, and `st` waits for all of them.
 int batch_launch_steps(dg_batch* b, int method, int red, int steps, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(b->counters, 0, sizeof(int) * dg_batch::kCounters, st);
+  const int ng = (int)b->groups.size();
+  cudaError_t e = cudaMemsetAsync(b->counters, 0, sizeof(int) * dg_batch::kCounters * ng, st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, st);
   if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
-  int slot = 0;
   const int ti = red == 2 ? 1 : 2;
-  for (int s = 0; s < steps; ++s) {
-    if (method == 1) {  // ADER: predictor, then update
-      e = (b->prec == DG_FP64 ? launch_batch_tck_f64 : launch_batch_tck_f32)(
-          b->items_tck, b->n_tck, b->inst, red, b->counters + slot++, b->grid_tck[ti], b->block_tck,
-          b->smem_tck[ti], st);
-      if (e == cudaSuccess)
-        e = (b->prec == DG_FP64 ? launch_batch_op_f64 : launch_batch_op_f32)(
-            b->items_op, b->n_op, b->inst, 5, b->counters + slot++, b->grid_op, b->block_op, b->smem_op, st);
-      b->launches += 2;
-    } else {
-      for (int ph = 0; ph < 5 && e == cudaSuccess; ++ph) {
-        e = (b->prec == DG_FP64 ? launch_batch_op_f64 : launch_batch_op_f32)(
-            b->items_op, b->n_op, b->inst, ph, b->counters + slot++, b->grid_op, b->block_op, b->smem_op,
-            st);
-        b->launches += 1;
+  auto op = b->prec == DG_FP64 ? launch_batch_op_f64 : launch_batch_op_f32;
+  auto tck = b->prec == DG_FP64 ? launch_batch_tck_f64 : launch_batch_tck_f32;
+  for (int gi = 0; gi < ng && e == cudaSuccess; ++gi) {
+    BatchGroup& g = b->groups[gi];
+    int* cnt = b->counters + gi * dg_batch::kCounters;
+    e = cudaStreamWaitEvent(g.s, b->fork, 0);
+    for (int s = 0; s < steps && e == cudaSuccess; ++s) {
+      if (method == 1) {  // ADER: predictor, then update
+        e = tck(g.n, g.items_tck, g.n_tck, b->inst, red, cnt++, g.grid_tck[ti], g.block_tck, g.smem_tck[ti], g.s);
+        if (e == cudaSuccess)
+          e = op(g.n, g.items_op, g.n_op, b->inst, 5, cnt++, g.grid_op, g.block_op, g.smem_op, g.s);
+        b->launches += 2;
+      } else {
+        for (int ph = 0; ph < 5 && e == cudaSuccess; ++ph) {
+          e = op(g.n, g.items_op, g.n_op, b->inst, ph, cnt++, g.grid_op, g.block_op, g.smem_op, g.s);
+          b->launches += 1;
+        }
       }
     }
-    if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
+    if (e == cudaSuccess) e = cudaEventRecord(g.done, g.s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g.done, 0);
   }
+  if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
   return DG_OK;
 }
 
@@ -1005,7 +1030,7 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     g_setup_err = "dg_batch_create: NULL arrays or n < 1";
     return DG_EINVAL;
   }
-  const int prec = ctxs[0]->prec, dev = ctxs[0]->dev;
+  const int prec = ctxs[0] ? ctxs[0]->prec : 0, dev = ctxs[0] ? ctxs[0]->dev : 0;
   for (int i = 0; i < n; ++i) {
     if (!ctxs[i] || ctxs[i]->prec != prec || ctxs[i]->dev != dev) {
       g_setup_err = "dg_batch_create: contexts must be non-NULL, of one precision and one device";
@@ -1020,7 +1045,7 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
       return DG_EINVAL;
     }
   }
-  DeviceGuard g(dev);
+  DeviceGuard dg_(dev);
   dg_batch* b = new (std::nothrow) dg_batch();
   if (!b) return DG_ENOMEM;
   b->dev = dev;
@@ -1032,8 +1057,9 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     return code;
   };
   std::vector<BatchInst> hinst(n);
-  std::vector<BatchItem> hop, htck;
-  const size_t rs = prec == DG_FP64 ? 8 : 4;
+  std::vector<std::vector<BatchItem>> hop(DG_NMAX + 1), htck(DG_NMAX + 1);
+  auto maxthr = prec == DG_FP64 ? batch_max_threads_f64 : batch_max_threads_f32;
+  std::vector<BatchGroup> byn(DG_NMAX + 1);
   for (int i = 0; i < n; ++i) {
     dg_ctx* c = ctxs[i];
     int rc;
@@ -1070,49 +1096,82 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
       fact *= (j + 1);
       I.tck.coef[j] = std::pow(dt[i], j + 1) / fact;
     }
-    const int n2 = c->n * c->n;
-    for (int e0 = 0; e0 < c->E; e0 += c->epb_op)
-      hop.push_back({i, e0, std::min(c->epb_op, c->E - e0), c->n, c->epb_op});
-    for (int e0 = 0; e0 < c->E; e0 += c->epb_tck)
-      htck.push_back({i, e0, std::min(c->epb_tck, c->E - e0), c->n, c->epb_tck});
-    b->block_op = std::max(b->block_op, c->epb_op * n2);
-    b->block_tck = std::max(b->block_tck, c->epb_tck * n2);
-    b->smem_op = std::max(b->smem_op, (size_t)c->epb_op * g_kt.smem[prec][c->n](0, 2));
-    b->smem_tck[1] = std::max(b->smem_tck[1], (size_t)c->epb_tck * g_kt.smem[prec][c->n](1, 2));
-    b->smem_tck[2] = std::max(b->smem_tck[2], (size_t)c->epb_tck * g_kt.smem[prec][c->n](1, 0));
+    const int nn = c->n, n2 = nn * nn;
+    const int eo = std::max(1, std::min(c->epb_op, maxthr(nn, 0) / n2));
+    const int et = std::max(1, std::min(c->epb_tck, maxthr(nn, 1) / n2));
+    // items are cut below, once each degree's launch shape is known
+    hop[nn].push_back({i, 0, c->E, nn, eo});
+    htck[nn].push_back({i, 0, c->E, nn, et});
+    BatchGroup& g = byn[nn];
+    g.n = nn;
+    g.block_op = std::max(g.block_op, eo * n2);
+    g.block_tck = std::max(g.block_tck, et * n2);
+    g.smem_op = std::max(g.smem_op, (size_t)eo * g_kt.smem[prec][nn](0, 2));
+    g.smem_tck[1] = std::max(g.smem_tck[1], (size_t)et * g_kt.smem[prec][nn](1, 2));
+    g.smem_tck[2] = std::max(g.smem_tck[2], (size_t)et * g_kt.smem[prec][nn](1, 0));
     b->ctx.push_back(c);
   }
-  (void)rs;
-  // largest work first: per-element cost grows like n^4
-  auto cost = [](const BatchItem& w) { return (double)w.ne * w.n * w.n * w.n * w.n; };
-  std::stable_sort(hop.begin(), hop.end(), [&](const BatchItem& x, const BatchItem& y) { return cost(x) > cost(y); });
-  std::stable_sort(htck.begin(), htck.end(), [&](const BatchItem& x, const BatchItem& y) { return cost(x) > cost(y); });
-  b->n_op = (int)hop.size();
-  b->n_tck = (int)htck.size();
-  int rc;
-  if ((rc = batch_alloc(b, (void**)&b->inst, sizeof(BatchInst) * n)) ||
-      (rc = batch_alloc(b, (void**)&b->items_op, sizeof(BatchItem) * hop.size())) ||
-      (rc = batch_alloc(b, (void**)&b->items_tck, sizeof(BatchItem) * htck.size())) ||
-      (rc = batch_alloc(b, (void**)&b->counters, sizeof(int) * dg_batch::kCounters)))
-    return bail(rc);
-  cudaStream_t st = S(stream);
-  cudaError_t e;
-  if ((e = cudaMemcpyAsync(b->inst, hinst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(b->items_op, hop.data(), sizeof(BatchItem) * hop.size(), cudaMemcpyHostToDevice, st)) ||
-      (e = cudaMemcpyAsync(b->items_tck, htck.data(), sizeof(BatchItem) * htck.size(), cudaMemcpyHostToDevice, st)) ||
-      (e = cudaStreamSynchronize(st))) {
-    b->fail(DG_ECUDA, cudaGetErrorString(e));
-    return bail(DG_ECUDA);
-  }
+  // Item order: largest solves first (balance at the end of a launch), and
+  // within a solve in element order, so that the blocks in flight sweep a
+  // contiguous range of one solve and neighbours' face values are still in L2.
+  std::vector<int> ecount(n);
+  for (int i = 0; i < n; ++i) ecount[i] = ctxs[i]->E;
+  auto by_size = [&](const BatchItem& x, const BatchItem& y) {
+    if (x.inst != y.inst) return ecount[x.inst] != ecount[y.inst] ? ecount[x.inst] > ecount[y.inst] : x.inst < y.inst;
+    return x.e0 < y.e0;
+  };
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   auto occ = prec == DG_FP64 ? batch_occupancy_f64 : batch_occupancy_f32;
-  b->grid_op = sms * std::max(1, occ(0, b->block_op, b->smem_op));
-  b->grid_tck[1] = sms * std::max(1, occ(1, b->block_tck, b->smem_tck[1]));
-  b->grid_tck[2] = sms * std::max(1, occ(2, b->block_tck, b->smem_tck[2]));
-  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+  int rc;
+  if ((rc = batch_alloc(b, (void**)&b->inst, sizeof(BatchInst) * n))) return bail(rc);
+  cudaStream_t st = S(stream);
+  cudaError_t e = cudaMemcpyAsync(b->inst, hinst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st);
+  for (int nn = 2; nn <= DG_NMAX && e == cudaSuccess; ++nn) {
+    if (hop[nn].empty()) continue;
+    BatchGroup g = byn[nn];
+    g.grid_op = sms * std::max(1, occ(nn, 0, g.block_op, g.smem_op));
+    g.grid_tck[1] = sms * std::max(1, occ(nn, 1, g.block_tck, g.smem_tck[1]));
+    g.grid_tck[2] = sms * std::max(1, occ(nn, 2, g.block_tck, g.smem_tck[2]));
+    // cut each solve into items of about (elements of the degree) / (8 x
+    // blocks) elements, in whole slices, so every block sees ~8 items
+    auto cut = [](std::vector<BatchItem>& v, int grid) {
+      long long tot = 0;
+      for (const auto& w : v) tot += w.ne;
+      std::vector<BatchItem> out;
+      for (const auto& w : v) {
+        long long per = std::max<long long>(w.epb, tot / (8LL * grid));
+        per = (per + w.epb - 1) / w.epb * w.epb;
+        for (int e0 = 0; e0 < w.ne; e0 += (int)per)
+          out.push_back({w.inst, e0, (int)std::min<long long>(per, w.ne - e0), w.n, w.epb});
+      }
+      v.swap(out);
+    };
+    cut(hop[nn], g.grid_op);
+    cut(htck[nn], std::max(g.grid_tck[1], g.grid_tck[2]));
+    std::sort(hop[nn].begin(), hop[nn].end(), by_size);
+    std::sort(htck[nn].begin(), htck[nn].end(), by_size);
+    g.n_op = (int)hop[nn].size();
+    g.n_tck = (int)htck[nn].size();
+    if ((rc = batch_alloc(b, (void**)&g.items_op, sizeof(BatchItem) * g.n_op)) ||
+        (rc = batch_alloc(b, (void**)&g.items_tck, sizeof(BatchItem) * g.n_tck)))
+      return bail(rc);
+    e = cudaMemcpyAsync(g.items_op, hop[nn].data(), sizeof(BatchItem) * g.n_op, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g.items_tck, htck[nn].data(), sizeof(BatchItem) * g.n_tck, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+    b->groups.push_back(g);
+  }
+  if (e == cudaSuccess)
+    if ((rc = batch_alloc(b, (void**)&b->counters, sizeof(int) * dg_batch::kCounters * b->groups.size())))
+      return bail(rc);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
     cudaGetLastError();
-    b->fail(DG_ECUDA, "stream creation failed");
+    b->fail(DG_ECUDA, cudaGetErrorString(e));
     return bail(DG_ECUDA);
   }
   *out = b;
@@ -1124,6 +1183,7 @@ static int batch_steps(dg_batch* b, int method, int red, int32_t nsteps, uintptr
   cudaStream_t st = S(stream);
   const int gi = method == 0 ? 2 : (red == 2 ? 1 : 0);
   const int chunks = nsteps / dg_batch::kChunk, rest = nsteps % dg_batch::kChunk;
+  const uint64_t per_chunk = (uint64_t)dg_batch::kChunk * (method == 0 ? 5 : 2) * b->groups.size();
   if (chunks > 0 && !b->gexec[gi]) {
     // capture kChunk steps once; the graph is replayed on the caller's stream
     cudaGraph_t graph = nullptr;
@@ -1148,7 +1208,7 @@ static int batch_steps(dg_batch* b, int method, int red, int32_t nsteps, uintptr
   for (int c = 0; c < chunks; ++c) {
     cudaError_t e = cudaGraphLaunch(b->gexec[gi], st);
     if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
-    b->launches += (uint64_t)dg_batch::kChunk * (method == 0 ? 5 : 2);
+    b->launches += per_chunk;
   }
   if (rest) return batch_launch_steps(b, method, red, rest, st);
   return DG_OK;
@@ -1168,10 +1228,16 @@ extern "C" int dg_batch_step_lsrk(dg_batch* b, int32_t nsteps, uintptr_t stream)
 extern "C" int dg_batch_info(const dg_batch* b, int32_t* n_inst, int32_t* n_items, int32_t* block,
                              int32_t* grid, uint64_t* launches) {
   if (!b) return DG_EINVAL;
+  int items = 0, blk = 0, grd = 0;
+  for (const auto& g : b->groups) {
+    items += g.n_op;
+    blk = std::max(blk, g.block_op);
+    grd += g.grid_op;
+  }
   if (n_inst) *n_inst = b->n;
-  if (n_items) *n_items = b->n_op;
-  if (block) *block = b->block_op;
-  if (grid) *grid = b->grid_op;
+  if (n_items) *n_items = items;
+  if (block) *block = blk;
+  if (grid) *grid = grd;
   if (launches) *launches = b->launches;
   return DG_OK;
 }

@@ -39,12 +39,14 @@ typedef cudaError_t (*OpFn)(const OpParams& p, int epi, int epb, cudaStream_t st
 typedef cudaError_t (*TckFn)(const TckParams& p, int red, int epb, cudaStream_t st);
 typedef cudaError_t (*EnergyFn)(const EnergyParams& p, int epb, cudaStream_t st);
 typedef int (*SmemFn)(int which, int red);  // bytes per element
+typedef int (*MaxThrFn)(int which);          // largest launchable block
 
 struct KernelTable {
   OpFn op[2][DG_NMAX + 1];
   TckFn tck[2][DG_NMAX + 1];
   EnergyFn energy[2][DG_NMAX + 1];
   SmemFn smem[2][DG_NMAX + 1];
+  MaxThrFn maxthr[2][DG_NMAX + 1];
 };
 
 // Each kernel translation unit registers its instantiations and uploads the
@@ -60,16 +62,19 @@ int upload_f32_hi(const double* d, const float* f);
 
 struct BatchItem;
 struct BatchInst;
-cudaError_t launch_batch_op_f64(const BatchItem* items, int nitems, const BatchInst* inst, int phase,
+// Batched persistent kernels, one launch per degree n (all items of degree n).
+cudaError_t launch_batch_op_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int phase,
                                 int* counter, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_batch_op_f32(const BatchItem* items, int nitems, const BatchInst* inst, int phase,
+cudaError_t launch_batch_op_f32(int n, const BatchItem* items, int nitems, const BatchInst* inst, int phase,
                                 int* counter, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_batch_tck_f64(const BatchItem* items, int nitems, const BatchInst* inst, int red,
+cudaError_t launch_batch_tck_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
                                  int* counter, int grid, int block, size_t smem, cudaStream_t st);
-cudaError_t launch_batch_tck_f32(const BatchItem* items, int nitems, const BatchInst* inst, int red,
+cudaError_t launch_batch_tck_f32(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
                                  int* counter, int grid, int block, size_t smem, cudaStream_t st);
-int batch_occupancy_f64(int which, int block, size_t smem);
-int batch_occupancy_f32(int which, int block, size_t smem);
+int batch_occupancy_f64(int n, int which, int block, size_t smem);
+int batch_occupancy_f32(int n, int which, int block, size_t smem);
+int batch_max_threads_f64(int n, int which);  // which: 0 operator, 1 predictor
+int batch_max_threads_f32(int n, int which);
 int upload_batch_f64(const double* d, const float* f);
 int upload_batch_f32(const double* d, const float* f);
 

@@ -704,9 +704,10 @@ __global__ void energy_kernel(const EnergyParams p) {
 
 // ---------------------------------------------------------------------------
 // Batched form: many independent solves (different meshes, degrees, time
-// steps) advanced by one persistent launch per phase.  A work item is a run
-// of consecutive elements of one instance; blocks take items from a counter
-// (dynamic scheduling, no waiting) and run the same per-element code as the
+// steps) advanced by persistent launches.  A work item is a run of
+// consecutive elements of one instance, processed one block's worth (epb
+// elements) at a time; blocks take items from a counter (dynamic
+// scheduling, no waiting) and run the same per-element code as the
 // single-solve kernels, so each instance's result does not depend on what
 // else is in the batch.
 // ---------------------------------------------------------------------------
@@ -720,7 +721,10 @@ struct BatchInst {
   TckParams tck;
 };
 
-template <typename Real>
+// One launch per degree present in the batch: every item has n == N, so the
+// block shape and register use are those of that degree alone; launches of
+// different degrees run concurrently (they belong to different solves).
+template <int N, typename Real, int EPI>
 __global__ void batch_op_kernel(const BatchItem* __restrict__ items, int nitems,
                                 const BatchInst* __restrict__ inst, int phase, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -734,26 +738,15 @@ __global__ void batch_op_kernel(const BatchItem* __restrict__ items, int nitems,
     if (it >= nitems) break;
     const BatchItem w = items[it];
     const OpParams& p = inst[w.inst].op[phase];
-    const bool lsrk = phase < 5;
-    switch (w.n) {
-#define DG_BATCH_OP(NN)                                          \
-  case NN:                                                       \
-    if (lsrk)                                                    \
-      op_block<NN, Real, EPI_LSRK>(p, w.e0, w.ne, sm);           \
-    else                                                         \
-      op_block<NN, Real, EPI_ADD>(p, w.e0, w.ne, sm);            \
-    break;
-      DG_BATCH_OP(2) DG_BATCH_OP(3) DG_BATCH_OP(4) DG_BATCH_OP(5) DG_BATCH_OP(6) DG_BATCH_OP(7)
-      DG_BATCH_OP(8)
-#undef DG_BATCH_OP
-      default:
-        break;
+    // the item's elements in slices of epb (one block's worth)
+    for (int e0 = w.e0; e0 < w.e0 + w.ne; e0 += w.epb) {
+      op_block<N, Real, EPI>(p, e0, min(w.epb, w.e0 + w.ne - e0), sm);
+      __syncthreads();  // shared memory is reused by the next slice
     }
-    __syncthreads();  // shared memory is reused by the next item
   }
 }
 
-template <typename Real, int RED>
+template <int N, typename Real, int RED>
 __global__ void batch_tck_kernel(const BatchItem* __restrict__ items, int nitems,
                                  const BatchInst* __restrict__ inst, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -766,19 +759,10 @@ __global__ void batch_tck_kernel(const BatchItem* __restrict__ items, int nitems
     __syncthreads();
     if (it >= nitems) break;
     const BatchItem w = items[it];
-    const TckParams& p = inst[w.inst].tck;
-    switch (w.n) {
-#define DG_BATCH_TCK(NN)                                   \
-  case NN:                                                 \
-    tck_block<NN, Real, RED>(p, w.e0, w.ne, w.epb, sm);    \
-    break;
-      DG_BATCH_TCK(2) DG_BATCH_TCK(3) DG_BATCH_TCK(4) DG_BATCH_TCK(5) DG_BATCH_TCK(6)
-      DG_BATCH_TCK(7) DG_BATCH_TCK(8)
-#undef DG_BATCH_TCK
-      default:
-        break;
+    for (int e0 = w.e0; e0 < w.e0 + w.ne; e0 += w.epb) {
+      tck_block<N, Real, RED>(inst[w.inst].tck, e0, min(w.epb, w.e0 + w.ne - e0), w.epb, sm);
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 

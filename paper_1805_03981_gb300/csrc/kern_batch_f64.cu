@@ -1,39 +1,113 @@
-// Batched persistent kernels (all degrees in one launch), double.
+// Batched persistent kernels (one launch per degree), double.
 #include "kern_inst.cuh"
 
 namespace dg {
-cudaError_t launch_batch_op_f64(const BatchItem* items, int nitems, const BatchInst* inst, int phase,
-                                    int* counter, int grid, int block, size_t smem, cudaStream_t st) {
-  batch_op_kernel<double><<<grid, block, smem, st>>>(items, nitems, inst, phase, counter);
-  return cudaGetLastError();
-}
-cudaError_t launch_batch_tck_f64(const BatchItem* items, int nitems, const BatchInst* inst, int red,
-                                     int* counter, int grid, int block, size_t smem, cudaStream_t st) {
-  if (red == 2)
-    batch_tck_kernel<double, 2><<<grid, block, smem, st>>>(items, nitems, inst, counter);
+namespace {
+
+template <int N>
+cudaError_t op_n(const BatchItem* items, int nitems, const BatchInst* inst, int phase, int* counter,
+                 int grid, int block, size_t smem, cudaStream_t st) {
+  if (phase < 5)
+    batch_op_kernel<N, double, EPI_LSRK><<<grid, block, smem, st>>>(items, nitems, inst, phase, counter);
   else
-    batch_tck_kernel<double, 0><<<grid, block, smem, st>>>(items, nitems, inst, counter);
+    batch_op_kernel<N, double, EPI_ADD><<<grid, block, smem, st>>>(items, nitems, inst, phase, counter);
   return cudaGetLastError();
 }
-// blocks per SM of the batched kernels (which: 0 operator, 1 predictor red=2, 2 predictor red=0)
-int batch_occupancy_f64(int which, int block, size_t smem) {
+template <int N>
+cudaError_t tck_n(const BatchItem* items, int nitems, const BatchInst* inst, int red, int* counter,
+                  int grid, int block, size_t smem, cudaStream_t st) {
+  if (red == 2)
+    batch_tck_kernel<N, double, 2><<<grid, block, smem, st>>>(items, nitems, inst, counter);
+  else
+    batch_tck_kernel<N, double, 0><<<grid, block, smem, st>>>(items, nitems, inst, counter);
+  return cudaGetLastError();
+}
+template <int N>
+int occ_n(int which, int block, size_t smem) {
   int nb = 0;
   if (which == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_op_kernel<double>, block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_op_kernel<N, double, EPI_LSRK>, block, smem);
   else if (which == 1)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tck_kernel<double, 2>, block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tck_kernel<N, double, 2>, block, smem);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tck_kernel<double, 0>, block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tck_kernel<N, double, 0>, block, smem);
   cudaGetLastError();
   return nb;
+}
+template <int N>
+int maxthr_n(int which) {
+  if (which == 0)
+    return min(kernel_max_threads(batch_op_kernel<N, double, EPI_LSRK>),
+               kernel_max_threads(batch_op_kernel<N, double, EPI_ADD>));
+  return min(kernel_max_threads(batch_tck_kernel<N, double, 2>), kernel_max_threads(batch_tck_kernel<N, double, 0>));
+}
+template <int N>
+cudaError_t allow_n() {
+  cudaError_t e;
+  if ((e = allow_smem(batch_op_kernel<N, double, EPI_LSRK>)) != cudaSuccess) return e;
+  if ((e = allow_smem(batch_op_kernel<N, double, EPI_ADD>)) != cudaSuccess) return e;
+  if ((e = allow_smem(batch_tck_kernel<N, double, 2>)) != cudaSuccess) return e;
+  return allow_smem(batch_tck_kernel<N, double, 0>);
+}
+
+}  // namespace
+
+#define DG_SWITCH_N(n, CALL) \
+  switch (n) {              \
+    case 2: return CALL(2);  \
+    case 3: return CALL(3);  \
+    case 4: return CALL(4);  \
+    case 5: return CALL(5);  \
+    case 6: return CALL(6);  \
+    case 7: return CALL(7);  \
+    case 8: return CALL(8);  \
+    default: break;          \
+  }
+
+cudaError_t launch_batch_op_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int phase,
+                                    int* counter, int grid, int block, size_t smem, cudaStream_t st) {
+#define C_(N) op_n<N>(items, nitems, inst, phase, counter, grid, block, smem, st)
+  DG_SWITCH_N(n, C_)
+#undef C_
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_batch_tck_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
+                                     int* counter, int grid, int block, size_t smem, cudaStream_t st) {
+#define C_(N) tck_n<N>(items, nitems, inst, red, counter, grid, block, smem, st)
+  DG_SWITCH_N(n, C_)
+#undef C_
+  return cudaErrorInvalidValue;
+}
+// blocks per SM (which: 0 operator, 1 predictor red=2, 2 predictor red=0)
+int batch_occupancy_f64(int n, int which, int block, size_t smem) {
+#define C_(N) occ_n<N>(which, block, smem)
+  DG_SWITCH_N(n, C_)
+#undef C_
+  return 0;
+}
+int batch_max_threads_f64(int n, int which) {
+#define C_(N) maxthr_n<N>(which)
+  DG_SWITCH_N(n, C_)
+#undef C_
+  return 0;
 }
 int upload_batch_f64(const double* d, const float* f) {
   cudaError_t e;
   if ((e = cudaMemcpyToSymbol(c_tab_d, d, sizeof(double) * DG_TAB_LEN)) != cudaSuccess) return (int)e;
   if ((e = cudaMemcpyToSymbol(c_tab_f, f, sizeof(float) * DG_TAB_LEN)) != cudaSuccess) return (int)e;
-  if ((e = allow_smem(batch_op_kernel<double>)) != cudaSuccess) return (int)e;
-  if ((e = allow_smem(batch_tck_kernel<double, 2>)) != cudaSuccess) return (int)e;
-  if ((e = allow_smem(batch_tck_kernel<double, 0>)) != cudaSuccess) return (int)e;
+  for (int n = 2; n <= DG_NMAX; ++n) {
+    cudaError_t r = cudaErrorInvalidValue;
+    switch (n) {
+      case 2: r = allow_n<2>(); break;
+      case 3: r = allow_n<3>(); break;
+      case 4: r = allow_n<4>(); break;
+      case 5: r = allow_n<5>(); break;
+      case 6: r = allow_n<6>(); break;
+      case 7: r = allow_n<7>(); break;
+      case 8: r = allow_n<8>(); break;
+    }
+    if (r != cudaSuccess) return (int)r;
+  }
   return 0;
 }
 }  // namespace dg

@@ -79,6 +79,29 @@ cudaError_t set_max_smem() {
   return allow_smem(energy_kernel<N, Real>);
 }
 
+// Largest block the kernel can launch with (registers per thread included).
+template <typename K>
+int kernel_max_threads(K kernel) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return fa.maxThreadsPerBlock;
+}
+
+// which: 0 operator (all epilogues), 1 predictor (both reductions), 2 energy
+template <int N, typename Real>
+int max_threads(int which) {
+  if (which == 0)
+    return min(kernel_max_threads(op_kernel<N, Real, EPI_WRITE>),
+               min(kernel_max_threads(op_kernel<N, Real, EPI_LSRK>),
+                   kernel_max_threads(op_kernel<N, Real, EPI_ADD>)));
+  if (which == 1)
+    return min(kernel_max_threads(tck_kernel<N, Real, 0>), kernel_max_threads(tck_kernel<N, Real, 2>));
+  return kernel_max_threads(energy_kernel<N, Real>);
+}
+
 template <int N, typename Real>
 void register_one(KernelTable* t) {
   const int pi = sizeof(Real) == 8 ? 0 : 1;
@@ -86,6 +109,7 @@ void register_one(KernelTable* t) {
   t->tck[pi][N] = &launch_tck<N, Real>;
   t->energy[pi][N] = &launch_energy<N, Real>;
   t->smem[pi][N] = &smem_bytes<N, Real>;
+  t->maxthr[pi][N] = &max_threads<N, Real>;
 }
 
 }  // namespace dg
