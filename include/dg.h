@@ -101,6 +101,14 @@ int dg_mesh_setup(const dg_mesh_desc* mesh, int k, int prec, double flux_alpha,
                   uintptr_t stream, dg_ctx** out);
 
 /*
+ * dg_mesh_setup with the coefficients given at once (rho, c as for
+ * dg_set_coefficients), so the geometry set-up runs once. rho and c are both
+ * NULL (rho = c = 1) or both given.
+ */
+int dg_mesh_setup_coef(const dg_mesh_desc* mesh, int k, int prec, double flux_alpha,
+                       const double* rho, const double* c, uintptr_t stream, dg_ctx** out);
+
+/*
  * Set the coefficients rho > 0 and c > 0 (Sec. 2, Eq. (1)) as host arrays
  * [E][(k+1)^3] of values at each element's GL solution nodes; each is the
  * degree-k polynomial through those values, and may jump between elements.
@@ -254,6 +262,71 @@ int dg_batch_info(const dg_batch* b, int32_t* n_inst, int32_t* n_items, int32_t*
                   int32_t* grid, uint64_t* launches);
 const char* dg_batch_last_error(const dg_batch* b);
 void dg_batch_destroy(dg_batch* b);
+
+/*
+ * Served form: continuous batching of solves on one GPU. An admission thread
+ * takes queued requests in arrival order while they fit the HBM budget (a
+ * request that does not fit lets later, smaller ones in) and sets them up on
+ * the device on its own stream while the GPU keeps stepping; a stepping
+ * thread keeps each admitted solve's geometry and state device-resident and
+ * advances all admitted solves together (dg_batch) in rounds of at most
+ * chunk_steps steps, ending a round when a solve finishes. Finished states are copied to the caller's
+ * buffer and their memory released; requests that arrived meanwhile join at
+ * the next round. Each result is bitwise identical to solving it alone.
+ */
+typedef struct dg_server dg_server;
+typedef struct {
+  int32_t device;      /* CUDA device index */
+  int32_t prec;        /* DG_FP32 or DG_FP64 */
+  int32_t max_active;  /* most solves admitted at once; 0 = only the budget limits */
+  int32_t chunk_steps; /* steps per round at most; 0 = 16 */
+  double max_active_dof; /* admit only while the admitted solves hold fewer
+                            DoFs than this (0 = no limit): enough to fill the
+                            GPU, so that early requests finish early */
+} dg_server_opts;
+typedef struct {
+  dg_mesh_desc mesh;   /* as for dg_mesh_setup; copied at submit */
+  int32_t k;
+  double flux_alpha;
+  const double* rho;   /* [E][(k+1)^3], copied at submit */
+  const double* c;     /* [E][(k+1)^3], copied at submit */
+  const void* U0;      /* host [E][4][(k+1)^3] in the server precision, copied */
+  void* U_out;         /* host buffer for the final state (server precision);
+                          caller-owned, must stay valid until dg_poll gives
+                          DG_OK for this request */
+  double dt;
+  int32_t nsteps;
+  int32_t method;      /* 0 = LSRK(5,4), 1 = ADER */
+  int32_t reduce_every;
+} dg_request;
+typedef struct {
+  double t_submit, t_admit, t_done; /* seconds, one monotonic clock */
+  int32_t status;                   /* DG_OK or the error of this solve */
+} dg_result;
+typedef struct {
+  int32_t queued, active, peak_active;
+  uint64_t completed, rounds, batches_built;
+  size_t hbm_used, hbm_peak;  /* budget accounting, bytes */
+  double dof_steps;           /* DoF-steps advanced so far */
+  double busy_s;              /* time spent in stepping rounds */
+} dg_server_stats_t;
+
+/* Device bytes the server reserves from its budget for one admitted solve
+ * (geometry, coefficients, state and all scratch); 0 for invalid sizes. */
+size_t dg_request_bytes(int32_t n_elem, int32_t k, int32_t geom_degree, int32_t prec);
+
+/* Start a server on opts->device with an HBM budget in bytes. */
+int dg_server_create(size_t hbm_budget, const dg_server_opts* opts, dg_server** out);
+/* Queue a request (never blocks on the GPU); DG_ENOMEM if it can never fit
+ * the budget, DG_EINVAL for a malformed request. */
+int dg_submit(dg_server* s, const dg_request* r, uint64_t* ticket);
+/* DG_EAGAIN until the request is finished (waiting up to timeout_ms), then
+ * DG_OK with *out filled; a ticket can be polled to completion once. */
+int dg_poll(dg_server* s, uint64_t ticket, dg_result* out, int32_t timeout_ms);
+int dg_server_stats(dg_server* s, dg_server_stats_t* out);
+/* Stop the scheduling thread and free everything; unfinished requests are
+ * dropped. */
+void dg_server_destroy(dg_server* s);
 
 /* Sizes: number of elements, degree, precision, bytes of one state. */
 int dg_info(const dg_ctx* ctx, int32_t* n_elem, int32_t* k, int32_t* prec,

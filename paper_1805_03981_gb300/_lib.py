@@ -15,6 +15,8 @@ EXPORTED_SYMBOLS = [
     "dg_profile_enable", "dg_profile_read", "dg_energy_noalloc",
     "dg_set_tiling", "dg_get_tiling", "dg_tune", "dg_batch_create", "dg_batch_step_ader",
     "dg_batch_step_lsrk", "dg_batch_info", "dg_batch_last_error", "dg_batch_destroy",
+    "dg_server_create", "dg_submit", "dg_poll", "dg_server_stats", "dg_server_destroy",
+    "dg_request_bytes", "dg_mesh_setup_coef",
 ]
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
 KINDS = ["operator", "lsrk_stage", "ader_update", "tck", "other"]
@@ -30,6 +32,30 @@ class MeshDesc(C.Structure):
     _fields_ = [("n_elem", C.c_int32), ("geom_degree", C.c_int32),
                 ("nodes", C.POINTER(C.c_double)), ("nbr", C.POINTER(C.c_int32)),
                 ("nbr_face", C.POINTER(C.c_int8)), ("orient", C.POINTER(C.c_int8))]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("device", C.c_int32), ("prec", C.c_int32), ("max_active", C.c_int32),
+                ("chunk_steps", C.c_int32), ("max_active_dof", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("mesh", MeshDesc), ("k", C.c_int32), ("flux_alpha", C.c_double),
+                ("rho", C.POINTER(C.c_double)), ("c", C.POINTER(C.c_double)), ("U0", C.c_void_p),
+                ("U_out", C.c_void_p), ("dt", C.c_double), ("nsteps", C.c_int32), ("method", C.c_int32),
+                ("reduce_every", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("status", C.c_int32)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int32), ("active", C.c_int32), ("peak_active", C.c_int32),
+                ("completed", C.c_uint64), ("rounds", C.c_uint64), ("batches_built", C.c_uint64),
+                ("hbm_used", C.c_size_t), ("hbm_peak", C.c_size_t), ("dof_steps", C.c_double),
+                ("busy_s", C.c_double)]
 
 
 _lib = None
@@ -52,6 +78,8 @@ def load_library():
     st = C.c_size_t  # uintptr_t stream
     sig = {
         "dg_mesh_setup": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.c_int, C.c_double, st, C.POINTER(vp)]),
+        "dg_mesh_setup_coef": (C.c_int, [C.POINTER(MeshDesc), C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double),
+                                         C.POINTER(C.c_double), st, C.POINTER(vp)]),
         "dg_set_coefficients": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), st]),
         "dg_apply_operator": (C.c_int, [vp, vp, vp, st]),
         "dg_step_lsrk": (C.c_int, [vp, vp, C.c_double, C.c_int32, st]),
@@ -80,6 +108,12 @@ def load_library():
                                     C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]),
         "dg_batch_last_error": (C.c_char_p, [vp]),
         "dg_batch_destroy": (None, [vp]),
+        "dg_server_create": (C.c_int, [C.c_size_t, C.POINTER(ServerOpts), C.POINTER(vp)]),
+        "dg_submit": (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+        "dg_poll": (C.c_int, [vp, C.c_uint64, C.POINTER(Result), C.c_int32]),
+        "dg_server_stats": (C.c_int, [vp, C.POINTER(ServerStats)]),
+        "dg_server_destroy": (None, [vp]),
+        "dg_request_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
         "dg_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
         "dg_last_error": (C.c_char_p, [vp]),
     }
@@ -294,6 +328,80 @@ class Batch:
         if getattr(self, "b", None):
             self.lib.dg_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server (include/dg.h, dg_server_*).
+
+    submit() copies the request's inputs and returns a ticket; poll() returns
+    None until the solve is done, then a dict with times and status; the
+    final state is in the host array given as ``out`` at submit."""
+
+    def __init__(self, hbm_budget, prec=DG_FP32, device=0, max_active=0, chunk_steps=0, max_active_dof=0.0):
+        self.lib = load_library()
+        self.prec = prec
+        self.np_dtype = np.float64 if prec == DG_FP64 else np.float32
+        o = ServerOpts(int(device), int(prec), int(max_active), int(chunk_steps), float(max_active_dof))
+        s = C.c_void_p()
+        rc = self.lib.dg_server_create(C.c_size_t(int(hbm_budget)), C.byref(o), C.byref(s))
+        if rc != 0:
+            raise DGError(rc, "dg_server_create failed")
+        self.s = s
+        self._outs = {}
+
+    def submit(self, mesh, k, rho, c, U0, dt, nsteps, method=1, reduce_every=2, alpha=1.0, out=None):
+        nodes = np.ascontiguousarray(mesh["nodes"], np.float64)
+        nbr = np.ascontiguousarray(mesh["nbr"], np.int32)
+        nbf = np.ascontiguousarray(mesh["nbr_face"], np.int8)
+        ori = np.ascontiguousarray(mesh["orient"], np.int8)
+        rho = np.ascontiguousarray(rho, np.float64)
+        c = np.ascontiguousarray(c, np.float64)
+        U0 = np.ascontiguousarray(U0, self.np_dtype)
+        if out is None:
+            out = np.empty_like(U0)
+        desc = MeshDesc(int(mesh["n_elem"]), int(mesh["geom_degree"]),
+                        nodes.ctypes.data_as(C.POINTER(C.c_double)), nbr.ctypes.data_as(C.POINTER(C.c_int32)),
+                        nbf.ctypes.data_as(C.POINTER(C.c_int8)), ori.ctypes.data_as(C.POINTER(C.c_int8)))
+        req = Request(desc, int(k), float(alpha), rho.ctypes.data_as(C.POINTER(C.c_double)),
+                      c.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(U0.ctypes.data),
+                      C.c_void_p(out.ctypes.data), float(dt), int(nsteps), int(method), int(reduce_every))
+        t = C.c_uint64()
+        rc = self.lib.dg_submit(self.s, C.byref(req), C.byref(t))
+        if rc != 0:
+            raise DGError(rc, "dg_submit rejected the request")
+        self._outs[t.value] = out
+        return t.value
+
+    def poll(self, ticket, timeout_ms=0):
+        r = Result()
+        rc = self.lib.dg_poll(self.s, C.c_uint64(ticket), C.byref(r), int(timeout_ms))
+        if rc == -5:
+            return None
+        if rc != 0:
+            raise DGError(rc, "dg_poll failed")
+        return {"t_submit": r.t_submit, "t_admit": r.t_admit, "t_done": r.t_done, "status": r.status,
+                "out": self._outs.pop(ticket)}
+
+    def request_bytes(self, n_elem, k, geom_degree=1):
+        return int(self.lib.dg_request_bytes(int(n_elem), int(k), int(geom_degree), int(self.prec)))
+
+    def stats(self):
+        st = ServerStats()
+        rc = self.lib.dg_server_stats(self.s, C.byref(st))
+        if rc != 0:
+            raise DGError(rc, "dg_server_stats failed")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.dg_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

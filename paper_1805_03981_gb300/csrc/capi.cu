@@ -462,8 +462,16 @@ const char* dg_last_error(const dg_ctx* ctx) {
   return ctx ? ctx->err.c_str() : g_setup_err.c_str();
 }
 
+int dg_mesh_setup_coef(const dg_mesh_desc* m, int k, int prec, double alpha, const double* rho,
+                       const double* c, uintptr_t stream, dg_ctx** out);
+
 int dg_mesh_setup(const dg_mesh_desc* m, int k, int prec, double alpha, uintptr_t stream,
                   dg_ctx** out) {
+  return dg_mesh_setup_coef(m, k, prec, alpha, nullptr, nullptr, stream, out);
+}
+
+int dg_mesh_setup_coef(const dg_mesh_desc* m, int k, int prec, double alpha, const double* rho_h,
+                       const double* c_h, uintptr_t stream, dg_ctx** out) {
   if (!out) return DG_EINVAL;
   *out = nullptr;
   g_setup_err.clear();
@@ -536,7 +544,21 @@ int dg_mesh_setup(const dg_mesh_desc* m, int k, int prec, double alpha, uintptr_
   std::memcpy(hpts.data() + 2 * DG_PTS_LEN, g_tab.xgl, sizeof(double) * DG_PTS_LEN);
   std::vector<double> hxq(DG_NMAX + 2, 0.0);
   gauss_lobatto(qc, hxq.data());
-  std::vector<double> ones((size_t)n3 * E, 1.0);
+  if ((rho_h == nullptr) != (c_h == nullptr)) {
+    g_setup_err = "rho and c must both be given or both be NULL";
+    delete ctx;
+    return DG_EINVAL;
+  }
+  if (rho_h)
+    for (size_t i = 0; i < (size_t)n3 * E; ++i)
+      if (!(rho_h[i] > 0.0) || !(c_h[i] > 0.0) || !std::isfinite(rho_h[i]) || !std::isfinite(c_h[i])) {
+        g_setup_err = "coefficients must be positive and finite";
+        delete ctx;
+        return DG_EINVAL;
+      }
+  std::vector<double> ones(rho_h ? 0 : (size_t)n3 * E, 1.0);
+  const double* rho_src = rho_h ? rho_h : ones.data();
+  const double* c_src = c_h ? c_h : ones.data();
   cudaError_t ce;
 #define DG_UP(dst, src, bytes)                                                            \
   if ((ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) { \
@@ -547,8 +569,8 @@ int dg_mesh_setup(const dg_mesh_desc* m, int k, int prec, double alpha, uintptr_
   DG_UP(ctx->nbr_face, m->nbr_face, 6 * (size_t)E);
   DG_UP(ctx->orient, m->orient, 6 * (size_t)E);
   DG_UP(ctx->nodes, m->nodes, sizeof(double) * 3 * qc * qc * qc * (size_t)E);
-  DG_UP(ctx->rho, ones.data(), sizeof(double) * n3 * (size_t)E);
-  DG_UP(ctx->c, ones.data(), sizeof(double) * n3 * (size_t)E);
+  DG_UP(ctx->rho, rho_src, sizeof(double) * n3 * (size_t)E);
+  DG_UP(ctx->c, c_src, sizeof(double) * n3 * (size_t)E);
   DG_UP(ctx->pts, hpts.data(), sizeof(double) * 3 * DG_PTS_LEN);
   DG_UP(ctx->xq, hxq.data(), sizeof(double) * (DG_NMAX + 2));
 #undef DG_UP
