@@ -7,14 +7,16 @@ one LSRK(5,4) time step and another by one ADER time step (order k+1 = 6,
 degree reduction every second derivative) at the same dt (Cr = 0.1), so a
 step processes 2 x 28.3M DoF-steps and runs every kernel of the hot path.
 
-Timing: W untimed warm-up steps, then K steps bracketed by a barrier and a
-device synchronisation, timed with CUDA events on the launching stream; the
-max over ranks is reported.  The state (226 MB) and geometry (1.8 GB) are
+Timing: W untimed warm-up steps, then K steps of each method (one stepper
+call per method, as a solve runs) bracketed by a barrier and a device
+synchronisation, timed with CUDA events on the launching stream; the max over
+ranks is reported.  The state (226 MB) and geometry (1.8 GB) are
 larger than L2, so no flush is needed between steps.  Per-kernel device time
 comes from the library's own event profiling on the same stream.
 
-e2e: the same steps through dg_solve_host, copying the state from pinned host
-memory to the device and back every step.
+e2e: every step, per method, dg_solve_host copies the state from pinned host
+memory to the device, advances one step and copies it back (also reported:
+K steps per dg_solve_host call).
 
 --impl reference: the FP64 CPU oracle on a bounded sample of the same recipe
 (4^3 elements), one LSRK and one ADER step per bench step, single thread.
@@ -56,6 +58,8 @@ def parse():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--size", type=int, default=32, help="elements per axis")
     ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--basis", default="g", choices=["g", "gl"],
+                    help="state inside the steppers: g = Gauss-point values (default), gl = the paper's storage")
     ap.add_argument("--workload", default="curved_pulse",
                     choices=["curved_pulse", "plane_wave", "batched", "served"])
     ap.add_argument("--lam", type=float, default=20.0, help="served: arrivals per second")
@@ -478,18 +482,24 @@ def main():
     if args.accuracy:
         return accuracy_study(args, cfg, dgw, torch)
     s = dgw.Solver(cfg["mesh"], k, prec, cfg["alpha"], cfg["rho"], cfg["c"])
+    s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
+    # autotune the tiling of this workload's kernels (results do not depend on it)
+    from paper_1805_03981_gb300 import autotune
+    tuned = {}
+    for kind, name in ((dgw.KIND_LSRK, "lsrk_stage"), (dgw.KIND_TCK, "tck")):
+        ms_c = s.tune(kind, autotune.CANDIDATES, reps=2)
+        tuned[name] = {str(c_): round(m, 4) for c_, m in zip(autotune.CANDIDATES, ms_c) if m > 0}
+    tiling = s.tiling()
     dof = 4 * (k + 1) ** 3 * N ** 3
     dt = cfg["dt"]
     U_l = s.to_device(cfg["U0"])
     U_a = s.to_device(cfg["U0"])
     stream = torch.cuda.current_stream()
 
-    def bench_step():
-        s.step_lsrk(U_l, dt, 1)
-        s.step_ader(U_a, dt, 1, 2)
-
-    for _ in range(args.warmup):
-        bench_step()
+    # one call per method advances K steps, as a solve does (with the Gauss
+    # basis the state changes basis once on entry and once on exit of a call)
+    s.step_lsrk(U_l, dt, args.warmup)
+    s.step_ader(U_a, dt, args.warmup, 2)
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
@@ -500,8 +510,8 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
-        bench_step()
+    s.step_lsrk(U_l, dt, args.steps)
+    s.step_ader(U_a, dt, args.steps, 2)
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1)
@@ -525,7 +535,7 @@ def main():
     avg_s = tot_ms * 1e-3 / max(nlaunch, 1)
     E = N ** 3
     nonwall = 1.0 if args.workload == "plane_wave" else 1.0 - 1.0 / N
-    flops = opcount.flops_per_element(dom, k + 1, 2, nonwall) * E
+    flops = opcount.flops_per_element(dom, k + 1, 2, nonwall, args.basis) * E
     byts = opcount.bytes_per_element(dom, k + 1, rsize, 2) * E
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm = peaks.get("hbm_gbs")
@@ -553,21 +563,28 @@ def main():
     out_l = torch.empty_like(Uh).pin_memory()
     out_a = torch.empty_like(Uh).pin_memory()
     in_l, in_a = Uh.clone().pin_memory(), Uh.clone().pin_memory()
-    for _ in range(1):
-        s.solve_host(0, in_l, out_l, dt, 1)
-        s.solve_host(1, in_a, out_a, dt, 1, 2)
+    s.solve_host(0, in_l, out_l, dt, 1)
+    s.solve_host(1, in_a, out_a, dt, 1, 2)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(args.steps):         # every step: state in from the host, one step, state out
         s.solve_host(0, in_l, out_l, dt, 1)
         s.solve_host(1, in_a, out_a, dt, 1, 2)
         in_l, out_l = out_l, in_l
         in_a, out_a = out_a, in_a
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    s.solve_host(0, in_l, out_l, dt, args.steps)
+    s.solve_host(1, in_a, out_a, dt, args.steps, 2)
+    barrier()
+    solve_s = max_over_ranks(time.perf_counter() - t0)
     state_bytes = s.info()["state_bytes"]
     e2e = {"value": world * 2 * dof * args.steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": 2 * state_bytes, "d2h_bytes_per_step": 2 * state_bytes}
+           "h2d_bytes_per_step": 2 * state_bytes, "d2h_bytes_per_step": 2 * state_bytes,
+           "note": "each step, per method: dg_solve_host copies the state in from pinned host memory, "
+                   "advances one step and copies it back",
+           "k_steps_per_call_value": world * 2 * dof * args.steps / solve_s}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "curved_pulse":
@@ -585,6 +602,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == dgw.DG_FP64 else "f32",
             "data": "synthetic",
             "config": {"workload": workload_desc(N, k, args.prec, args.workload), "elements": E, "k": k, "dof": dof,
+                       "state_basis_inside_steppers": "Gauss points (G)" if args.basis == "g" else "Gauss-Lobatto (GL)",
+                       "tiling_elements_per_block": {"operator": tiling[0], "tck": tiling[1]},
                        "l2": "inputs larger than L2 (state %d MB, %d MB device-resident incl. geometry), no flush"
                        % (state_bytes >> 20, s.device_bytes() >> 20),
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -148,6 +148,27 @@ int dg_step_ader(dg_ctx* ctx, void* U, double dt, int32_t nsteps,
                  int32_t reduce_every, uintptr_t stream);
 
 /*
+ * Representation of the state inside dg_step_lsrk and dg_step_ader (the
+ * state passed in and out is always GL nodal values):
+ *  DG_BASIS_GL  the paper's scheme: GL storage, so that a face needs only the
+ *               neighbour's (k+1)^2 face nodes, and an on-the-fly change to
+ *               the collocated Gauss basis inside each element (Sec. 3.1-3.2).
+ *  DG_BASIS_G   values at the Gauss points during the steps: the steppers
+ *               change basis once on entry and once on exit; the operator
+ *               then needs no basis change and a diagonal mass matrix, and a
+ *               face reads the neighbour's line of (k+1) values through each
+ *               face point. Same discrete scheme; fewer arithmetic operations
+ *               and more face data, the trade-off the paper measures
+ *               (Sec. 3.1), which favours G where arithmetic is scarce (FP64
+ *               on GB300).
+ * Default DG_BASIS_GL.
+ */
+#define DG_BASIS_GL 0
+#define DG_BASIS_G 1
+int dg_set_basis(dg_ctx* ctx, int basis);
+int dg_get_basis(const dg_ctx* ctx);
+
+/*
  * The predictor alone: Ubar (device, GL basis) = sum_j dt^{j+1}/(j+1)! T_j of
  * Eq. (6) for the state U. U and Ubar must not overlap.
  */
@@ -232,8 +253,9 @@ int dg_set_tiling(dg_ctx* ctx, int32_t epb_op, int32_t epb_tck);
 int dg_get_tiling(const dg_ctx* ctx, int32_t* epb_op, int32_t* epb_tck);
 
 /*
- * Measure one kernel kind (DG_KIND_LSRK, DG_KIND_ADER or DG_KIND_TCK) on this
- * context's mesh for each candidate elements-per-block value: ms_out[c] =
+ * Measure one kernel kind (DG_KIND_LSRK, DG_KIND_ADER or DG_KIND_TCK), in the
+ * variant the steppers use for the context's basis, on this context's mesh
+ * for each candidate elements-per-block value: ms_out[c] =
  * device ms per launch (average of reps), -1 for impossible candidates. The
  * fastest candidate is left set. Uses context scratch; synchronises.
  */

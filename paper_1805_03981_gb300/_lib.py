@@ -16,8 +16,9 @@ EXPORTED_SYMBOLS = [
     "dg_set_tiling", "dg_get_tiling", "dg_tune", "dg_batch_create", "dg_batch_step_ader",
     "dg_batch_step_lsrk", "dg_batch_info", "dg_batch_last_error", "dg_batch_destroy",
     "dg_server_create", "dg_submit", "dg_poll", "dg_server_stats", "dg_server_destroy",
-    "dg_request_bytes", "dg_mesh_setup_coef",
+    "dg_request_bytes", "dg_mesh_setup_coef", "dg_set_basis", "dg_get_basis",
 ]
+BASIS_GL, BASIS_G = 0, 1
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
 KINDS = ["operator", "lsrk_stage", "ader_update", "tck", "other"]
 
@@ -114,6 +115,8 @@ def load_library():
         "dg_server_stats": (C.c_int, [vp, C.POINTER(ServerStats)]),
         "dg_server_destroy": (None, [vp]),
         "dg_request_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+        "dg_set_basis": (C.c_int, [vp, C.c_int]),
+        "dg_get_basis": (C.c_int, [vp]),
         "dg_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
         "dg_last_error": (C.c_char_p, [vp]),
     }
@@ -266,6 +269,13 @@ class Solver:
         cnt = (C.c_int64 * len(KINDS))()
         self._check(self.lib.dg_profile_read(self.ctx, ms, cnt, int(bool(reset))))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KINDS)}
+
+    def set_basis(self, basis):
+        """BASIS_GL (paper's storage, default) or BASIS_G (Gauss values inside the steppers)."""
+        self._check(self.lib.dg_set_basis(self.ctx, int(basis)))
+
+    def basis(self):
+        return int(self.lib.dg_get_basis(self.ctx))
 
     def set_tiling(self, epb_op=0, epb_tck=0):
         self._check(self.lib.dg_set_tiling(self.ctx, int(epb_op), int(epb_tck)))

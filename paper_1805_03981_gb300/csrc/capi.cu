@@ -103,6 +103,7 @@ struct dg_ctx {
   size_t dev_bytes = 0;
   uint64_t launches = 0;
   int epb_op = 1, epb_tck = 1, epb_en = 1;
+  int basis = DG_BASIS_GL;  // representation of the state inside the steppers
   // profiling: event pairs recorded around launches while enabled
   bool prof = false;
   struct Rec {
@@ -316,8 +317,8 @@ OpParams op_params(const dg_ctx* ctx) {
   return p;
 }
 
-int launch_op(dg_ctx* ctx, const OpParams& p, int epi, cudaStream_t st) {
-  OpFn fn = g_kt.op[ctx->prec][ctx->n];
+int launch_op(dg_ctx* ctx, const OpParams& p, int epi, cudaStream_t st, bool gbasis = false) {
+  OpFn fn = gbasis ? g_kt.opg[ctx->prec][ctx->n] : g_kt.op[ctx->prec][ctx->n];
   const int kind = epi == EPI_WRITE ? DG_KIND_OPERATOR : (epi == EPI_LSRK ? DG_KIND_LSRK : DG_KIND_ADER);
   dg_ctx::Span span(ctx, kind, st);
   DG_CK(fn(p, epi, ctx->epb_op, st), "operator kernel launch");
@@ -326,9 +327,20 @@ int launch_op(dg_ctx* ctx, const OpParams& p, int epi, cudaStream_t st) {
   return DG_OK;
 }
 
-int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaStream_t st) {
+// In-place change of basis of a whole state (GL <-> G).
+int change_basis(dg_ctx* ctx, void* U, int to_g, cudaStream_t st) {
+  dg_ctx::Span span(ctx, DG_KIND_OTHER, st);
+  DG_CK(g_kt.basis[ctx->prec][ctx->n](U, ctx->E, to_g, ctx->epb_en, st), "basis kernel launch");
+  span.done();
+  ctx->launches++;
+  return DG_OK;
+}
+
+int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaStream_t st,
+               bool gbasis = false) {
   TckParams p;
   std::memset(&p, 0, sizeof(p));
+  p.gmode = gbasis ? 1 : 0;
   p.U = U;
   p.Ubar = Ubar;
   p.geoT = ctx->geoT;
@@ -372,6 +384,8 @@ int lsrk_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st) {
   if ((rc = ensure(ctx, &ctx->U3, "LSRK state"))) return rc;
   if ((rc = ensure(ctx, &ctx->dU, "LSRK register"))) return rc;
   OpParams p = op_params(ctx);
+  const bool g = ctx->basis == DG_BASIS_G && nsteps > 0;
+  if (g && (rc = change_basis(ctx, U, 1, st))) return rc;
   void* const chain[6] = {U, ctx->U2, ctx->U3, ctx->U2, ctx->U3, U};
   for (int s = 0; s < nsteps; ++s)
     for (int st5 = 0; st5 < 5; ++st5) {
@@ -383,8 +397,9 @@ int lsrk_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st) {
       p.cB = kLsrkB[st5];
       p.dt = dt;
       p.first = st5 == 0;
-      if ((rc = launch_op(ctx, p, EPI_LSRK, st))) return rc;
+      if ((rc = launch_op(ctx, p, EPI_LSRK, st, g))) return rc;
     }
+  if (g && (rc = change_basis(ctx, U, 0, st))) return rc;
   return DG_OK;
 }
 
@@ -392,13 +407,16 @@ int ader_steps(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_
   int rc;
   if ((rc = ensure(ctx, &ctx->Ubar, "ADER predictor"))) return rc;
   OpParams p = op_params(ctx);
+  const bool g = ctx->basis == DG_BASIS_G && nsteps > 0;
+  if (g && (rc = change_basis(ctx, U, 1, st))) return rc;
   for (int s = 0; s < nsteps; ++s) {
-    if ((rc = launch_tck(ctx, U, ctx->Ubar, dt, red, st))) return rc;
+    if ((rc = launch_tck(ctx, U, ctx->Ubar, dt, red, st, g))) return rc;
     p.U = ctx->Ubar;
     p.Uadd = U;
     p.out = U;
-    if ((rc = launch_op(ctx, p, EPI_ADD, st))) return rc;
+    if ((rc = launch_op(ctx, p, EPI_ADD, st, g))) return rc;
   }
+  if (g && (rc = change_basis(ctx, U, 0, st))) return rc;
   return DG_OK;
 }
 
@@ -724,6 +742,15 @@ int dg_solve_host(dg_ctx* ctx, int method, const void* Uh, void* Uout, double dt
   return DG_OK;
 }
 
+int dg_set_basis(dg_ctx* ctx, int basis) {
+  if (!ctx) return DG_EINVAL;
+  if (basis != DG_BASIS_GL && basis != DG_BASIS_G) return ctx->fail(DG_EINVAL, "basis must be DG_BASIS_GL or DG_BASIS_G");
+  ctx->basis = basis;
+  return DG_OK;
+}
+
+int dg_get_basis(const dg_ctx* ctx) { return ctx ? ctx->basis : DG_EINVAL; }
+
 int dg_info(const dg_ctx* ctx, int32_t* E, int32_t* k, int32_t* prec, size_t* bytes) {
   if (!ctx) return DG_EINVAL;
   if (E) *E = ctx->E;
@@ -915,10 +942,11 @@ extern "C" int dg_tune(dg_ctx* ctx, int kind, const int32_t* cand, int32_t ncand
     p.dt = 1e-3;
     for (int r = -1; r < reps; ++r) {  // one untimed launch first
       if (r == 0) cudaEventRecord(a, st);
+      const bool gb = ctx->basis == DG_BASIS_G;  // time the kernels the steppers use
       if (kind == DG_KIND_TCK)
-        rc = launch_tck(ctx, ctx->U2, ctx->Ubar, 1e-3, 2, st);
+        rc = launch_tck(ctx, ctx->U2, ctx->Ubar, 1e-3, 2, st, gb);
       else
-        rc = launch_op(ctx, p, kind == DG_KIND_LSRK ? EPI_LSRK : EPI_ADD, st);
+        rc = launch_op(ctx, p, kind == DG_KIND_LSRK ? EPI_LSRK : EPI_ADD, st, gb);
       if (rc) break;
     }
     if (rc) {  // launch configuration refused: not a candidate

@@ -38,11 +38,14 @@ cudaError_t launch_setup(const SetupParams& P, cudaStream_t st);
 typedef cudaError_t (*OpFn)(const OpParams& p, int epi, int epb, cudaStream_t st);
 typedef cudaError_t (*TckFn)(const TckParams& p, int red, int epb, cudaStream_t st);
 typedef cudaError_t (*EnergyFn)(const EnergyParams& p, int epb, cudaStream_t st);
+typedef cudaError_t (*BasisFn)(void* U, int E, int to_g, int epb, cudaStream_t st);
 typedef int (*SmemFn)(int which, int red);  // bytes per element
 typedef int (*MaxThrFn)(int which);          // largest launchable block
 
 struct KernelTable {
   OpFn op[2][DG_NMAX + 1];
+  OpFn opg[2][DG_NMAX + 1];  // operator on Gauss-basis states
+  BasisFn basis[2][DG_NMAX + 1];
   TckFn tck[2][DG_NMAX + 1];
   EnergyFn energy[2][DG_NMAX + 1];
   SmemFn smem[2][DG_NMAX + 1];

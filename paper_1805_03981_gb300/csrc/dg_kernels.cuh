@@ -387,16 +387,178 @@ __global__ void op_kernel(const OpParams p) {
 }
 
 // ---------------------------------------------------------------------------
+// The operator on states kept in the Gauss basis G (values at the (k+1)^3
+// Gauss points): no basis change of the own tile, M^-1 is the diagonal alone,
+// and a neighbour's trace at a face Gauss point is the l(+-1) contraction of
+// the neighbour's line through that point.  Same discrete operator as
+// op_block, other representation of the state (Sec. 3.1 weighs exactly this
+// choice of basis against the face data it needs).
+// ---------------------------------------------------------------------------
+template <int N, typename Real, int EPI>
+__device__ __forceinline__ void opg_block(const OpParams& p, const int e0, const int ne, Real* sm) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int SE = op_smem_per_elem<N>();
+  const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
+  const int a = t % N, b = t / N;
+  const int e = e0 + le;
+  const bool act = le < ne;
+  Real* su = sm + le * SE;
+  Real* sr = su + 4 * N3;
+  Real* snb = sr + 4 * N3;
+  const Real* __restrict__ U = static_cast<const Real*>(p.U);
+
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+    const int l = i / (4 * N3);
+    sm[l * SE + (i - l * 4 * N3)] = U[(size_t)e0 * 4 * N3 + i];
+  }
+  // neighbours' traces at this element's face Gauss points
+  int fmask = 0;
+  if (act) {
+#pragma unroll 1
+    for (int f = 0; f < 6; ++f) {
+      const int en = p.nbr[e * 6 + f];
+      if (en < 0) continue;
+      fmask |= 1 << f;
+      const int fn = p.nbr_face[e * 6 + f], o = p.orient[e * 6 + f];
+      const int uu = (o & 1) ? b : a, vv = (o & 1) ? a : b;
+      const int ip = (o & 2) ? N - 1 - uu : uu, jp = (o & 4) ? N - 1 - vv : vv;
+      const int dn = fn >> 1, sd = fn & 1;
+      const int t0 = dn == 0 ? 1 : 0, t1 = dn == 2 ? 1 : 2;
+      const int stride[3] = {1, N, N2};
+      const Real* src = U + (size_t)en * 4 * N3 + ip * stride[t0] + jp * stride[t1];
+      const int st = stride[dn];
+      constexpr int LF = OFF_LF(N);
+#pragma unroll
+      for (int fl = 0; fl < 4; ++fl) {
+        Real acc = tab<Real>(LF + sd * N) * src[fl * N3];
+#pragma unroll
+        for (int s = 1; s < N; ++s) acc = fma(tab<Real>(LF + sd * N + s), src[fl * N3 + s * st], acc);
+        snb[(f * 4 + fl) * N2 + t] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  const Real* gA = static_cast<const Real*>(p.geoA) + (size_t)e * 9 * N3;
+  const Real* gF = static_cast<const Real*>(p.geoF) + (size_t)e * 36 * N2;
+  const Real* gM = static_cast<const Real*>(p.geoM) + (size_t)e * 2 * N3;
+  if (act) {  // y
+    Real u[4][N], r[4][N];
+    const int base = line_base<1, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + N * s];
+    cell_face_dir<N, Real, 1>(u, r, gA, gF, snb, t, fmask);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + N * s] = r[fl][s];
+  }
+  __syncthreads();
+  if (act) {  // x
+    Real u[4][N], r[4][N];
+    const int base = line_base<0, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + s];
+    cell_face_dir<N, Real, 0>(u, r, gA, gF, snb, t, fmask);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + s] += r[fl][s];
+  }
+  __syncthreads();
+  if (act) {  // z, then the diagonal inverse mass
+    Real u[4][N], r[4][N];
+    const int base = line_base<2, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + N2 * s];
+    cell_face_dir<N, Real, 2>(u, r, gA, gF, snb, t, fmask);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+      const Real mp = __ldg(gM + base + N2 * s), mvv = __ldg(gM + N3 + base + N2 * s);
+      sr[base + N2 * s] = (r[0][s] + sr[base + N2 * s]) * mp;
+#pragma unroll
+      for (int fl = 1; fl < 4; ++fl)
+        sr[fl * N3 + base + N2 * s] = (r[fl][s] + sr[fl * N3 + base + N2 * s]) * mvv;
+    }
+  }
+  __syncthreads();
+  Real* __restrict__ out = static_cast<Real*>(p.out);
+  const Real* __restrict__ Uadd = static_cast<const Real*>(p.Uadd);
+  Real* __restrict__ dU = static_cast<Real*>(p.dU);
+  const Real cA = (Real)p.cA, cB = (Real)p.cB, dt = (Real)p.dt;
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+    const int l = i / (4 * N3);
+    const Real R = sm[l * SE + 4 * N3 + (i - l * 4 * N3)];
+    const size_t g = (size_t)e0 * 4 * N3 + i;
+    if (EPI == EPI_WRITE) {
+      out[g] = R;
+    } else if (EPI == EPI_ADD) {
+      out[g] = Uadd[g] + R;
+    } else {
+      const Real d = p.first ? dt * R : fma(cA, dU[g], dt * R);
+      dU[g] = d;
+      out[g] = fma(cB, d, Uadd[g]);
+    }
+  }
+}
+
+template <int N, typename Real, int EPI>
+__global__ void opg_kernel(const OpParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int epb = blockDim.x / (N * N);
+  const int e0 = blockIdx.x * epb;
+  opg_block<N, Real, EPI>(p, e0, min(epb, p.E - e0), reinterpret_cast<Real*>(smem_raw));
+}
+
+// In-place change of basis of whole states: GL -> G (to_g) or G -> GL.
+template <int N, typename Real>
+__global__ void basis_kernel(void* Uv, int E, int to_g) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  Real* U = static_cast<Real*>(Uv);
+  const int epb = blockDim.x / N2;
+  const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
+  const int e0 = blockIdx.x * epb;
+  const int ne = min(epb, E - e0);
+  Real* su = sm + le * 4 * N3;
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) sm[i] = U[(size_t)e0 * 4 * N3 + i];
+  __syncthreads();
+  const bool act = le < ne;
+  if (to_g) {
+    if (act) contract_tile<Real, 2, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+    __syncthreads();
+    if (act) contract_tile<Real, 0, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+    __syncthreads();
+    if (act) contract_tile<Real, 1, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+  } else {
+    if (act) contract_tile<Real, 2, N, N, N, N, OFF_VI(N), N3, N3>(su, su, t, N2);
+    __syncthreads();
+    if (act) contract_tile<Real, 0, N, N, N, N, OFF_VI(N), N3, N3>(su, su, t, N2);
+    __syncthreads();
+    if (act) contract_tile<Real, 1, N, N, N, N, OFF_VI(N), N3, N3>(su, su, t, N2);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) U[(size_t)e0 * 4 * N3 + i] = sm[i];
+}
+
+// ---------------------------------------------------------------------------
 // Taylor-Cauchy-Kowalevski predictor (Sec. 2.3 Eq. (6), Sec. 3.2 Alg. 2,
 // Sec. 3.3 Alg. 3).
 // ---------------------------------------------------------------------------
 struct TckParams {
-  const void* U;   // GL state
-  void* Ubar;      // GL predictor output
+  const void* U;   // state (GL, or G if gmode)
+  void* Ubar;      // predictor output (same basis as U)
   const void* geoT;
   long long geoT_stride;  // Reals per element
   double coef[DG_NMAX + 2];  // dt^{j+1} / (j+1)!
   int E;
+  int gmode;  // 1: U and Ubar hold Gauss-point values (no basis change)
 };
 
 // m-point levels visited with reduction every second derivative: N, N-2, ...
@@ -546,12 +708,14 @@ __device__ __forceinline__ void tck_block(const TckParams& p, const int e0, cons
   for (int i = t; i < tck_acc_off<N, RED>(NL); i += N2) acc[i] = Real(0);
   __syncthreads();
   // GL -> G (Sec. 3.2: the basis change is done per element on the fly)
-  contract_tile<Real, 2, N, N, N, N, OFF_V(N), N3, N3>(s0, s0, t, N2);
-  __syncthreads();
-  contract_tile<Real, 0, N, N, N, N, OFF_V(N), N3, N3>(s0, s0, t, N2);
-  __syncthreads();
-  contract_tile<Real, 1, N, N, N, N, OFF_V(N), N3, N3>(s0, s0, t, N2);
-  __syncthreads();
+  if (!p.gmode) {
+    contract_tile<Real, 2, N, N, N, N, OFF_V(N), N3, N3>(s0, s0, t, N2);
+    __syncthreads();
+    contract_tile<Real, 0, N, N, N, N, OFF_V(N), N3, N3>(s0, s0, t, N2);
+    __syncthreads();
+    contract_tile<Real, 1, N, N, N, N, OFF_V(N), N3, N3>(s0, s0, t, N2);
+    __syncthreads();
+  }
   tck_accumulate<N, Real, RED>(acc, s0, N3, (Real)p.coef[0], t, N2, N3);
 
   // Taylor terms j = 1 .. k+1 (k + 1 = N)
@@ -630,13 +794,21 @@ __device__ __forceinline__ void tck_block(const TckParams& p, const int e0, cons
     }
   }
   // G -> GL and store
+  Real* __restrict__ out = static_cast<Real*>(p.Ubar);
+  if (p.gmode) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+      const int l = i / (4 * N3);
+      out[(size_t)e0 * 4 * N3 + i] = sm[l * SE + 8 * N3 + (i - l * 4 * N3)];  // level-n accumulator
+    }
+    return;
+  }
   contract_tile<Real, 2, N, N, N, N, OFF_VI(N), N3, N3>(acc, s0, t, N2);
   __syncthreads();
   contract_tile<Real, 0, N, N, N, N, OFF_VI(N), N3, N3>(s0, s1, t, N2);
   __syncthreads();
   contract_tile<Real, 1, N, N, N, N, OFF_VI(N), N3, N3>(s1, s0, t, N2);
   __syncthreads();
-  Real* __restrict__ out = static_cast<Real*>(p.Ubar);
   for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
     const int l = i / (4 * N3);
     out[(size_t)e0 * 4 * N3 + i] = sm[l * SE + (i - l * 4 * N3)];

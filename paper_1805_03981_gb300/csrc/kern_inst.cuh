@@ -22,6 +22,28 @@ cudaError_t launch_op(const OpParams& p, int epi, int epb, cudaStream_t st) {
 }
 
 template <int N, typename Real>
+cudaError_t launch_opg(const OpParams& p, int epi, int epb, cudaStream_t st) {
+  const int threads = epb * N * N;
+  const size_t smem = (size_t)epb * op_smem_per_elem<N>() * sizeof(Real);
+  const int blocks = (p.E + epb - 1) / epb;
+  if (epi == EPI_WRITE)
+    opg_kernel<N, Real, EPI_WRITE><<<blocks, threads, smem, st>>>(p);
+  else if (epi == EPI_LSRK)
+    opg_kernel<N, Real, EPI_LSRK><<<blocks, threads, smem, st>>>(p);
+  else
+    opg_kernel<N, Real, EPI_ADD><<<blocks, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int N, typename Real>
+cudaError_t launch_basis(void* U, int E, int to_g, int epb, cudaStream_t st) {
+  const int threads = epb * N * N;
+  const size_t smem = (size_t)epb * 4 * N * N * N * sizeof(Real);
+  basis_kernel<N, Real><<<(E + epb - 1) / epb, threads, smem, st>>>(U, E, to_g);
+  return cudaGetLastError();
+}
+
+template <int N, typename Real>
 cudaError_t launch_tck(const TckParams& p, int red, int epb, cudaStream_t st) {
   const int threads = epb * N * N;
   const int blocks = (p.E + epb - 1) / epb;
@@ -74,6 +96,10 @@ cudaError_t set_max_smem() {
   if ((e = allow_smem(op_kernel<N, Real, EPI_WRITE>)) != cudaSuccess) return e;
   if ((e = allow_smem(op_kernel<N, Real, EPI_LSRK>)) != cudaSuccess) return e;
   if ((e = allow_smem(op_kernel<N, Real, EPI_ADD>)) != cudaSuccess) return e;
+  if ((e = allow_smem(opg_kernel<N, Real, EPI_WRITE>)) != cudaSuccess) return e;
+  if ((e = allow_smem(opg_kernel<N, Real, EPI_LSRK>)) != cudaSuccess) return e;
+  if ((e = allow_smem(opg_kernel<N, Real, EPI_ADD>)) != cudaSuccess) return e;
+  if ((e = allow_smem(basis_kernel<N, Real>)) != cudaSuccess) return e;
   if ((e = allow_smem(tck_kernel<N, Real, 0>)) != cudaSuccess) return e;
   if ((e = allow_smem(tck_kernel<N, Real, 2>)) != cudaSuccess) return e;
   return allow_smem(energy_kernel<N, Real>);
@@ -94,18 +120,23 @@ int kernel_max_threads(K kernel) {
 template <int N, typename Real>
 int max_threads(int which) {
   if (which == 0)
-    return min(kernel_max_threads(op_kernel<N, Real, EPI_WRITE>),
-               min(kernel_max_threads(op_kernel<N, Real, EPI_LSRK>),
-                   kernel_max_threads(op_kernel<N, Real, EPI_ADD>)));
+    return min(min(kernel_max_threads(op_kernel<N, Real, EPI_WRITE>),
+                   min(kernel_max_threads(op_kernel<N, Real, EPI_LSRK>),
+                       kernel_max_threads(op_kernel<N, Real, EPI_ADD>))),
+               min(kernel_max_threads(opg_kernel<N, Real, EPI_WRITE>),
+                   min(kernel_max_threads(opg_kernel<N, Real, EPI_LSRK>),
+                       kernel_max_threads(opg_kernel<N, Real, EPI_ADD>))));
   if (which == 1)
     return min(kernel_max_threads(tck_kernel<N, Real, 0>), kernel_max_threads(tck_kernel<N, Real, 2>));
-  return kernel_max_threads(energy_kernel<N, Real>);
+  return min(kernel_max_threads(energy_kernel<N, Real>), kernel_max_threads(basis_kernel<N, Real>));
 }
 
 template <int N, typename Real>
 void register_one(KernelTable* t) {
   const int pi = sizeof(Real) == 8 ? 0 : 1;
   t->op[pi][N] = &launch_op<N, Real>;
+  t->opg[pi][N] = &launch_opg<N, Real>;
+  t->basis[pi][N] = &launch_basis<N, Real>;
   t->tck[pi][N] = &launch_tck<N, Real>;
   t->energy[pi][N] = &launch_energy<N, Real>;
   t->smem[pi][N] = &smem_bytes<N, Real>;

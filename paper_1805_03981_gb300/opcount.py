@@ -16,9 +16,17 @@ def contraction(outputs, m):
     return 2 * m * outputs
 
 
-def operator_flops(n, curved=True, nonwall_frac=1.0):
-    """R = -M^-1 K U on one element: basis changes, cell terms, faces, M^-1."""
+def operator_flops(n, curved=True, nonwall_frac=1.0, basis="gl"):
+    """R = -M^-1 K U on one element: basis changes, cell terms, faces, M^-1.
+    basis "g": the state is held at the Gauss points (no basis changes; a
+    neighbour trace is one l(+-1) contraction of the neighbour's line)."""
     N3, N2 = n ** 3, n ** 2
+    if basis == "g":
+        f = 3 * N3 * (5 + 3) + 12 * contraction(N3, n) + 2 * 4 * N3
+        f += 6 * N2 * (4 * 2 * n + 5 + 5 + 2 + 4 + 4 + 3 + 4 * 2 * n)
+        f += nonwall_frac * 6 * 4 * contraction(N2, n)
+        f += 4 * N3
+        return f
     f = 0
     f += 12 * contraction(N3, n)            # GL -> G, 4 fields x 3 directions
     f += 3 * N3 * (5 + 3)                   # contravariant fluxes per direction
@@ -49,9 +57,9 @@ def tck_levels(n, red):
     return seq
 
 
-def tck_flops(n, red=2):
+def tck_flops(n, red=2, basis="gl"):
     N3 = n ** 3
-    f = 12 * contraction(N3, n) + 12 * contraction(N3, n)   # GL -> G, G -> GL
+    f = 0 if basis == "g" else 12 * contraction(N3, n) + 12 * contraction(N3, n)   # GL -> G, G -> GL
     f += 2 * 4 * N3                                          # first Taylor term
     m = n
     levels = [n]
@@ -97,13 +105,17 @@ def bytes_per_element(kind, n, rsize, red=2, first_stage=False):
         return 3 * vec + geometry_reals(n) * rsize + conn
     if kind == "tck":
         return 2 * vec + tck_geometry_reals(n, red) * rsize
+    if kind == "other":
+        return 2 * vec
     raise ValueError(kind)
 
 
-def flops_per_element(kind, n, red=2, nonwall_frac=1.0):
+def flops_per_element(kind, n, red=2, nonwall_frac=1.0, basis="gl"):
     if kind == "tck":
-        return tck_flops(n, red)
-    return operator_flops(n, nonwall_frac=nonwall_frac) + EPILOGUE_FLOPS[kind] * 4 * n ** 3
+        return tck_flops(n, red, basis)
+    if kind == "other":                       # change of basis of a whole state
+        return 12 * contraction(n ** 3, n)
+    return operator_flops(n, nonwall_frac=nonwall_frac, basis=basis) + EPILOGUE_FLOPS[kind] * 4 * n ** 3
 
 
 # --- the paper's model (Sec. 4.1), for comparison --------------------------
