@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--size", type=int, default=32, help="elements per axis")
     ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--tiling", default="", help="elements per block 'op,tck' instead of autotuning")
     ap.add_argument("--basis", default="g", choices=["g", "gl"],
                     help="state inside the steppers: g = Gauss-point values (default), gl = the paper's storage")
     ap.add_argument("--workload", default="curved_pulse",
@@ -485,10 +486,11 @@ def main():
     s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
     # autotune the tiling of this workload's kernels (results do not depend on it)
     from paper_1805_03981_gb300 import autotune
-    tuned = {}
-    for kind, name in ((dgw.KIND_LSRK, "lsrk_stage"), (dgw.KIND_TCK, "tck")):
-        ms_c = s.tune(kind, autotune.CANDIDATES, reps=2)
-        tuned[name] = {str(c_): round(m, 4) for c_, m in zip(autotune.CANDIDATES, ms_c) if m > 0}
+    if args.tiling:
+        s.set_tiling(*(int(x) for x in args.tiling.split(",")))
+    else:
+        for kind in (dgw.KIND_LSRK, dgw.KIND_TCK):
+            s.tune(kind, autotune.CANDIDATES, reps=2)
     tiling = s.tiling()
     dof = 4 * (k + 1) ** 3 * N ** 3
     dt = cfg["dt"]

@@ -66,6 +66,19 @@ __device__ __forceinline__ void mtv(const Real* in, Real* out) {
   }
 }
 
+// out[j] += sum_i M[i][j] in[i]  (accumulating transpose: an FMA chain that
+// starts from the running sum)
+template <typename Real, int OFF, int RI, int RO>
+__device__ __forceinline__ void mtv_acc(const Real* in, Real* out) {
+#pragma unroll
+  for (int j = 0; j < RO; ++j) {
+    Real acc = out[j];
+#pragma unroll
+    for (int i = 0; i < RI; ++i) acc = fma(tab<Real>(OFF + i * RO + j), in[i], acc);
+    out[j] = acc;
+  }
+}
+
 // Base index and stride of the line (a, b) along DIR in an X x Y x Z tile.
 template <int DIR, int X, int Y>
 __device__ __forceinline__ int line_base(int a, int b) {
@@ -140,7 +153,7 @@ __host__ __device__ constexpr int op_smem_per_elem() {
 // transposed applied to the contravariant fluxes) and the lifting of the
 // two faces normal to DIR.  u: Gauss-point values of (p, v) on the line;
 // r: contributions to the Gauss-basis residual along the line.
-template <int N, typename Real, int DIR>
+template <int N, typename Real, int DIR, bool ACC = false>
 __device__ __forceinline__ void cell_face_dir(const Real (&u)[4][N], Real (&r)[4][N],
                                               const Real* __restrict__ gA,
                                               const Real* __restrict__ gF, const Real* snb,
@@ -155,14 +168,20 @@ __device__ __forceinline__ void cell_face_dir(const Real (&u)[4][N], Real (&r)[4
   for (int s = 0; s < N; ++s)
     F[s] = fma(__ldg(A0 + N2 * s), u[1][s],
                fma(__ldg(A1 + N2 * s), u[2][s], __ldg(A2 + N2 * s) * u[3][s]));
-  mtv<Real, OFF_D(N), N, N>(F, r[0]);
+  if (ACC)
+    mtv_acc<Real, OFF_D(N), N, N>(F, r[0]);
+  else
+    mtv<Real, OFF_D(N), N, N>(F, r[0]);
   // velocity tests: flux A_{DIR i} p
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     const Real* Ai = i == 0 ? A0 : (i == 1 ? A1 : A2);
 #pragma unroll
     for (int s = 0; s < N; ++s) F[s] = __ldg(Ai + N2 * s) * u[0][s];
-    mtv<Real, OFF_D(N), N, N>(F, r[1 + i]);
+    if (ACC)
+      mtv_acc<Real, OFF_D(N), N, N>(F, r[1 + i]);
+    else
+      mtv<Real, OFF_D(N), N, N>(F, r[1 + i]);
   }
   // faces 2 DIR (xi_DIR = -1) and 2 DIR + 1 (xi_DIR = +1)
 #pragma unroll
@@ -319,12 +338,15 @@ __device__ __forceinline__ void op_block(const OpParams& p, const int e0, const 
 #pragma unroll
     for (int fl = 0; fl < 4; ++fl)
 #pragma unroll
-      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + s];
-    cell_face_dir<N, Real, 0>(u, r, gA, gF, snb, t, fmask);
+      for (int s = 0; s < N; ++s) {
+        u[fl][s] = su[fl * N3 + base + s];
+        r[fl][s] = sr[fl * N3 + base + s];
+      }
+    cell_face_dir<N, Real, 0, true>(u, r, gA, gF, snb, t, fmask);
 #pragma unroll
     for (int fl = 0; fl < 4; ++fl)
 #pragma unroll
-      for (int s = 0; s < N; ++s) sr[fl * N3 + base + s] += r[fl][s];
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + s] = r[fl][s];
   }
   __syncthreads();
   // 5. z, then inverse mass (diagonal in G, Sec. 3.1) and G -> GL along z
@@ -334,14 +356,17 @@ __device__ __forceinline__ void op_block(const OpParams& p, const int e0, const 
 #pragma unroll
     for (int fl = 0; fl < 4; ++fl)
 #pragma unroll
-      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + N2 * s];
-    cell_face_dir<N, Real, 2>(u, r, gA, gF, snb, t, fmask);
+      for (int s = 0; s < N; ++s) {
+        u[fl][s] = su[fl * N3 + base + N2 * s];
+        r[fl][s] = sr[fl * N3 + base + N2 * s];
+      }
+    cell_face_dir<N, Real, 2, true>(u, r, gA, gF, snb, t, fmask);
 #pragma unroll
     for (int s = 0; s < N; ++s) {
       const Real mp = __ldg(gM + base + N2 * s), mvv = __ldg(gM + N3 + base + N2 * s);
-      r[0][s] = (r[0][s] + sr[base + N2 * s]) * mp;
+      r[0][s] *= mp;
 #pragma unroll
-      for (int fl = 1; fl < 4; ++fl) r[fl][s] = (r[fl][s] + sr[fl * N3 + base + N2 * s]) * mvv;
+      for (int fl = 1; fl < 4; ++fl) r[fl][s] *= mvv;
     }
 #pragma unroll
     for (int fl = 0; fl < 4; ++fl) {
@@ -461,12 +486,15 @@ __device__ __forceinline__ void opg_block(const OpParams& p, const int e0, const
 #pragma unroll
     for (int fl = 0; fl < 4; ++fl)
 #pragma unroll
-      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + s];
-    cell_face_dir<N, Real, 0>(u, r, gA, gF, snb, t, fmask);
+      for (int s = 0; s < N; ++s) {
+        u[fl][s] = su[fl * N3 + base + s];
+        r[fl][s] = sr[fl * N3 + base + s];
+      }
+    cell_face_dir<N, Real, 0, true>(u, r, gA, gF, snb, t, fmask);
 #pragma unroll
     for (int fl = 0; fl < 4; ++fl)
 #pragma unroll
-      for (int s = 0; s < N; ++s) sr[fl * N3 + base + s] += r[fl][s];
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + s] = r[fl][s];
   }
   __syncthreads();
   if (act) {  // z, then the diagonal inverse mass
@@ -475,15 +503,17 @@ __device__ __forceinline__ void opg_block(const OpParams& p, const int e0, const
 #pragma unroll
     for (int fl = 0; fl < 4; ++fl)
 #pragma unroll
-      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + N2 * s];
-    cell_face_dir<N, Real, 2>(u, r, gA, gF, snb, t, fmask);
+      for (int s = 0; s < N; ++s) {
+        u[fl][s] = su[fl * N3 + base + N2 * s];
+        r[fl][s] = sr[fl * N3 + base + N2 * s];
+      }
+    cell_face_dir<N, Real, 2, true>(u, r, gA, gF, snb, t, fmask);
 #pragma unroll
     for (int s = 0; s < N; ++s) {
       const Real mp = __ldg(gM + base + N2 * s), mvv = __ldg(gM + N3 + base + N2 * s);
-      sr[base + N2 * s] = (r[0][s] + sr[base + N2 * s]) * mp;
+      sr[base + N2 * s] = r[0][s] * mp;
 #pragma unroll
-      for (int fl = 1; fl < 4; ++fl)
-        sr[fl * N3 + base + N2 * s] = (r[fl][s] + sr[fl * N3 + base + N2 * s]) * mvv;
+      for (int fl = 1; fl < 4; ++fl) sr[fl * N3 + base + N2 * s] = r[fl][s] * mvv;
     }
   }
   __syncthreads();
@@ -618,14 +648,18 @@ __device__ __forceinline__ void tck_derivative(const Real* src, Real* dst, const
 #pragma unroll
       for (int s = 0; s < M; ++s) {
         const Real j0 = __ldg(J0 + M2 * s), j1 = __ldg(J1 + M2 * s), j2 = __ldg(J2 + M2 * s);
-        Real tp = fma(j0, d[1][s], fma(j1, d[2][s], j2 * d[3][s]));
-        Real tv0 = j0 * d[0][s], tv1 = j1 * d[0][s], tv2 = j2 * d[0][s];
         const int idx = base + st * s;
-        if (dir > 0) {
-          tp += dst[idx];
-          tv0 += dst[FS + idx];
-          tv1 += dst[2 * FS + idx];
-          tv2 += dst[3 * FS + idx];
+        Real tp, tv0, tv1, tv2;
+        if (dir > 0) {  // continue the sums of the previous directions
+          tp = fma(j0, d[1][s], fma(j1, d[2][s], fma(j2, d[3][s], dst[idx])));
+          tv0 = fma(j0, d[0][s], dst[FS + idx]);
+          tv1 = fma(j1, d[0][s], dst[2 * FS + idx]);
+          tv2 = fma(j2, d[0][s], dst[3 * FS + idx]);
+        } else {
+          tp = fma(j0, d[1][s], fma(j1, d[2][s], j2 * d[3][s]));
+          tv0 = j0 * d[0][s];
+          tv1 = j1 * d[0][s];
+          tv2 = j2 * d[0][s];
         }
         if (dir == 2) {  // coefficients: -rho c^2 (p), -1/rho (v)
           const Real cp = __ldg(g + 9 * M3 + idx), cv = __ldg(g + 10 * M3 + idx);
