@@ -99,6 +99,24 @@ def workload_desc(N, k, prec, name="curved_pulse"):
             f"reduction every 2nd derivative) step, {prec.upper()}")
 
 
+# ------------------------------------------------------------------ ranks
+def reduce_max(x, world, device):
+    """Max of a float over all ranks of the default process group."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, ms_max, world):
+    """Whole-job throughput: every rank's units over the slowest rank's time
+    (replicas: each rank runs the same workload)."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -467,11 +485,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, world, "cuda")
 
     prec = dgw.DG_FP64 if args.prec == "fp64" else dgw.DG_FP32
     if args.workload == "batched":
@@ -522,7 +536,7 @@ def main():
     s.profile(False)
     clk = clocks.stop()
     ms_max = max_over_ranks(ms)
-    value = world * 2 * dof * args.steps / (ms_max * 1e-3)
+    value = job_value(2 * dof * args.steps, ms_max, world)
 
     # per-method rates from the profile (device time per kind)
     t_lsrk = prof["lsrk_stage"][0]
