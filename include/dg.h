@@ -20,7 +20,8 @@
  * - State layout: U[E][4][(k+1)^3], fields (p, v_x, v_y, v_z), nodes
  *   lexicographic with the first reference axis fastest. Element-local node
  *   values in the GL basis. Device states are caller-owned device pointers in
- *   the context's precision (double for DG_FP64, float for DG_FP32).
+ *   the context's precision (double for DG_FP64, float for DG_FP32), 16-byte
+ *   aligned (DG_EINVAL otherwise).
  * - Streams are passed as uintptr_t holding a cudaStream_t (0 = legacy
  *   default stream). All device work of a call is enqueued on that stream;
  *   calls return once the work is enqueued unless stated otherwise.
@@ -349,6 +350,14 @@ int dg_server_stats(dg_server* s, dg_server_stats_t* out);
 /* Stop the scheduling thread and free everything; unfinished requests are
  * dropped. */
 void dg_server_destroy(dg_server* s);
+
+/*
+ * Device status: DG_ETIMEOUT if, since the last check, a kernel of this
+ * context gave up a bounded wait (its shared-memory staging did not complete
+ * in time; that block's results were discarded), else DG_OK. Synchronises
+ * the stream and clears the status. dg_solve_host checks it itself.
+ */
+int dg_check_device(dg_ctx* ctx, uintptr_t stream);
 
 /* Sizes: number of elements, degree, precision, bytes of one state. */
 int dg_info(const dg_ctx* ctx, int32_t* n_elem, int32_t* k, int32_t* prec,

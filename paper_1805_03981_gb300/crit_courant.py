@@ -1,0 +1,71 @@
+"""Critical Courant numbers of the GPU schemes by simulation (the paper's
+Sec. 4.6 "iterative procedure", Table crit-Cr).
+
+On a periodic Cartesian mesh with rho = c = 1 and the upwind flux, a seeded
+random state is advanced for ``steps`` steps at Cr = c dt k^1.5 / h; the run
+is unstable when the discrete energy grows by more than ``growth`` (default
+1% over 1000 steps).  Bisection on Cr brackets the limit.
+
+    python -m paper_1805_03981_gb300.crit_courant --k 1,4,7
+"""
+import argparse
+import json
+
+import numpy as np
+
+
+def _setup(k, N, prec):
+    import synth
+    from . import _lib
+    mesh = synth.cube_mesh(N, q=1, periodic=True)
+    n3 = (k + 1) ** 3
+    ones = np.ones((N ** 3, n3))
+    s = _lib.Solver(mesh, k, prec, 1.0, ones, ones)
+    U0 = synth.configs.random_state(N ** 3, k, 1234)
+    return s, U0, 1.0 / N
+
+
+def stable(s, U0, h, k, cr, method, steps, growth):
+    import torch
+    U = s.to_device(U0)
+    e0 = s.energy(U)
+    dt = cr * h / k ** 1.5
+    if method == "lsrk":
+        s.step_lsrk(U, dt, steps)
+    else:
+        s.step_ader(U, dt, steps, 2)
+    torch.cuda.synchronize()
+    e1 = s.energy(U)
+    return bool(np.isfinite(e1) and e1 <= e0 * (1.0 + growth))
+
+
+def critical(k, method, N=4, steps=1000, growth=0.01, lo=0.02, hi=1.2, tol=2e-3, prec=None):
+    from . import _lib
+    s, U0, h = _setup(k, N, _lib.DG_FP64 if prec is None else prec)
+    if method == "ader":
+        hi = min(hi, 0.6)
+    while hi - lo > tol:
+        mid = 0.5 * (lo + hi)
+        if stable(s, U0, h, k, mid, method, steps, growth):
+            lo = mid
+        else:
+            hi = mid
+    s.close()
+    return 0.5 * (lo + hi)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--k", default="1,4,7")
+    ap.add_argument("--N", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=1000)
+    a = ap.parse_args()
+    out = {}
+    for k in (int(x) for x in a.k.split(",")):
+        out[k] = {m: critical(k, m, a.N, a.steps) for m in ("lsrk", "ader")}
+    print(json.dumps({"crit_courant_3d": out, "mesh": f"{a.N}^3 periodic Cartesian, rho=c=1, upwind",
+                      "criterion": f"energy growth <= 1 percent over {a.steps} steps from a seeded random state"}))
+
+
+if __name__ == "__main__":
+    main()

@@ -313,6 +313,7 @@ OpParams op_params(const dg_ctx* ctx) {
   p.geoA = ctx->geoA;
   p.geoM = ctx->geoM;
   p.geoF = ctx->geoF;
+  p.err = ctx->bad;
   p.E = ctx->E;
   return p;
 }
@@ -372,6 +373,8 @@ int check_state_ptr(dg_ctx* ctx, const void* p, const char* what) {
   }
   if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
     return ctx->fail(DG_EINVAL, "%s is not device memory", what);
+  if (reinterpret_cast<uintptr_t>(p) % 16 != 0)  // bulk copies read states directly
+    return ctx->fail(DG_EINVAL, "%s must be 16-byte aligned", what);
   return DG_OK;
 }
 
@@ -551,9 +554,9 @@ int dg_mesh_setup_coef(const dg_mesh_desc* m, int k, int prec, double alpha, con
       (rc = ctx->alloc(&ctx->pts, sizeof(double) * 3 * DG_PTS_LEN, "points")) ||
       (rc = ctx->alloc(&ctx->xq, sizeof(double) * (DG_NMAX + 2), "geometry points")) ||
       (rc = ctx->alloc(&ctx->bad, sizeof(int), "flag")) ||
-      (rc = ctx->alloc(&ctx->geoA, rs * 9 * n3 * (size_t)E, "cell metric")) ||
-      (rc = ctx->alloc(&ctx->geoM, rs * 2 * n3 * (size_t)E, "mass diagonal")) ||
-      (rc = ctx->alloc(&ctx->geoF, rs * 36 * n * n * (size_t)E, "face data")) ||
+      (rc = ctx->alloc(&ctx->geoA, rs * geo_stride_A(n) * (size_t)E, "cell metric")) ||
+      (rc = ctx->alloc(&ctx->geoM, rs * geo_stride_M(n) * (size_t)E, "mass diagonal")) ||
+      (rc = ctx->alloc(&ctx->geoF, rs * geo_stride_F(n) * (size_t)E, "face data")) ||
       (rc = ctx->alloc(&ctx->geoT, rs * (size_t)ctx->tstride * E, "predictor geometry")))
     return bail(rc);
   std::vector<double> hpts(3 * DG_PTS_LEN);
@@ -739,7 +742,7 @@ int dg_solve_host(dg_ctx* ctx, int method, const void* Uh, void* Uout, double dt
   if (rc) return rc;
   DG_CK(cudaMemcpyAsync(Uout, ctx->Uh, b, cudaMemcpyDeviceToHost, st), "copy out");
   DG_CK(cudaStreamSynchronize(st), "solve");
-  return DG_OK;
+  return dg_check_device(ctx, stream);
 }
 
 int dg_set_basis(dg_ctx* ctx, int basis) {
@@ -750,6 +753,21 @@ int dg_set_basis(dg_ctx* ctx, int basis) {
 }
 
 int dg_get_basis(const dg_ctx* ctx) { return ctx ? ctx->basis : DG_EINVAL; }
+
+int dg_check_device(dg_ctx* ctx, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  DeviceGuard g(ctx->dev);
+  cudaStream_t st = S(stream);
+  int flag = 0;
+  DG_CK(cudaMemcpyAsync(&flag, ctx->bad, sizeof(int), cudaMemcpyDeviceToHost, st), "read status");
+  DG_CK(cudaStreamSynchronize(st), "status");
+  if (flag) {
+    DG_CK(cudaMemsetAsync(ctx->bad, 0, sizeof(int), st), "clear status");
+    DG_CK(cudaStreamSynchronize(st), "status");
+    return ctx->fail(DG_ETIMEOUT, "a bounded device wait gave up (its results were discarded)");
+  }
+  return DG_OK;
+}
 
 int dg_info(const dg_ctx* ctx, int32_t* E, int32_t* k, int32_t* prec, size_t* bytes) {
   if (!ctx) return DG_EINVAL;

@@ -42,6 +42,50 @@ __device__ __forceinline__ double tab<double>(int i) { return c_tab_d[i]; }
 template <>
 __device__ __forceinline__ float tab<float>(int i) { return c_tab_f[i]; }
 
+// ---- bulk asynchronous copies global -> shared, completed on an mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// size and both addresses must be multiples of 16 bytes
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for phase `parity` of the barrier, giving up after a bounded number of
+// polls: then the error flag is set, a second bounded wait lets the block's
+// own copies land, and false is returned.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  if (err) atomicExch(err, 2);
+  for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) break;
+  return false;
+}
+
 // out[i] = sum_j M[i][j] in[j];  M is RO x RI at table offset OFF.
 template <typename Real, int OFF, int RO, int RI>
 __device__ __forceinline__ void mv(const Real* in, Real* out) {
@@ -137,9 +181,10 @@ struct OpParams {
   const int32_t* nbr;
   const int8_t* nbr_face;
   const int8_t* orient;
-  const void* geoA;  // [E][3 d][3 i][n^3] line-major per d: w adj(J)_{d i}
-  const void* geoM;  // [E][2][n^3]: rho c^2 / (w detJ), 1 / (rho w detJ)
-  const void* geoF;  // [E][6 f][6][n^2]: nw_x, nw_y, nw_z, Z-/(Z-+Z+), b, c
+  const void* geoA;  // [E][3 d][3 i][n^3] line-major per d: w adj(J)_{d i}   (stride geo_stride_A)
+  const void* geoM;  // [E][2][n^3]: rho c^2 / (w detJ), 1 / (rho w detJ)    (stride geo_stride_M)
+  const void* geoF;  // [E][6 f][6][n^2]: nw_x, nw_y, nw_z, Z-/(Z-+Z+), b, c (stride geo_stride_F)
+  int* err;          // set (non-zero) if a bounded wait gave up
   int E;
 };
 
@@ -153,7 +198,15 @@ __host__ __device__ constexpr int op_smem_per_elem() {
 // transposed applied to the contravariant fluxes) and the lifting of the
 // two faces normal to DIR.  u: Gauss-point values of (p, v) on the line;
 // r: contributions to the Gauss-basis residual along the line.
-template <int N, typename Real, int DIR, bool ACC = false>
+template <typename Real, bool SMEM>
+__device__ __forceinline__ Real geo_ld(const Real* p) {
+  if constexpr (SMEM)
+    return *p;
+  else
+    return __ldg(p);
+}
+
+template <int N, typename Real, int DIR, bool ACC = false, bool SMEM = false>
 __device__ __forceinline__ void cell_face_dir(const Real (&u)[4][N], Real (&r)[4][N],
                                               const Real* __restrict__ gA,
                                               const Real* __restrict__ gF, const Real* snb,
@@ -166,8 +219,8 @@ __device__ __forceinline__ void cell_face_dir(const Real (&u)[4][N], Real (&r)[4
   // pressure test: flux sum_i A_{DIR i} v_i
 #pragma unroll
   for (int s = 0; s < N; ++s)
-    F[s] = fma(__ldg(A0 + N2 * s), u[1][s],
-               fma(__ldg(A1 + N2 * s), u[2][s], __ldg(A2 + N2 * s) * u[3][s]));
+    F[s] = fma(geo_ld<Real, SMEM>(A0 + N2 * s), u[1][s],
+               fma(geo_ld<Real, SMEM>(A1 + N2 * s), u[2][s], geo_ld<Real, SMEM>(A2 + N2 * s) * u[3][s]));
   if (ACC)
     mtv_acc<Real, OFF_D(N), N, N>(F, r[0]);
   else
@@ -177,7 +230,7 @@ __device__ __forceinline__ void cell_face_dir(const Real (&u)[4][N], Real (&r)[4
   for (int i = 0; i < 3; ++i) {
     const Real* Ai = i == 0 ? A0 : (i == 1 ? A1 : A2);
 #pragma unroll
-    for (int s = 0; s < N; ++s) F[s] = __ldg(Ai + N2 * s) * u[0][s];
+    for (int s = 0; s < N; ++s) F[s] = geo_ld<Real, SMEM>(Ai + N2 * s) * u[0][s];
     if (ACC)
       mtv_acc<Real, OFF_D(N), N, N>(F, r[1 + i]);
     else
@@ -197,8 +250,8 @@ __device__ __forceinline__ void cell_face_dir(const Real (&u)[4][N], Real (&r)[4
       um[fl] = acc;
     }
     const Real* fc = gF + f * 6 * N2 + t;
-    const Real nw0 = __ldg(fc), nw1 = __ldg(fc + N2), nw2 = __ldg(fc + 2 * N2);
-    const Real a2 = __ldg(fc + 3 * N2), bb = __ldg(fc + 4 * N2), cc = __ldg(fc + 5 * N2);
+    const Real nw0 = geo_ld<Real, SMEM>(fc), nw1 = geo_ld<Real, SMEM>(fc + N2), nw2 = geo_ld<Real, SMEM>(fc + 2 * N2);
+    const Real a2 = geo_ld<Real, SMEM>(fc + 3 * N2), bb = geo_ld<Real, SMEM>(fc + 4 * N2), cc = geo_ld<Real, SMEM>(fc + 5 * N2);
     const Real vnm = fma(nw0, um[1], fma(nw1, um[2], nw2 * um[3]));
     Real pp, vnp;
     if ((fmask >> f) & 1) {
@@ -307,9 +360,9 @@ __device__ __forceinline__ void op_block(const OpParams& p, const int e0, const 
   }
   __syncthreads();
 
-  const Real* gA = static_cast<const Real*>(p.geoA) + (size_t)e * 9 * N3;
-  const Real* gF = static_cast<const Real*>(p.geoF) + (size_t)e * 36 * N2;
-  const Real* gM = static_cast<const Real*>(p.geoM) + (size_t)e * 2 * N3;
+  const Real* gA = static_cast<const Real*>(p.geoA) + (size_t)e * geo_stride_A(N);
+  const Real* gF = static_cast<const Real*>(p.geoF) + (size_t)e * geo_stride_F(N);
+  const Real* gM = static_cast<const Real*>(p.geoM) + (size_t)e * geo_stride_M(N);
 
   // 3. y: finish GL -> G along y in registers, then the y cell/face terms
   if (act) {
@@ -463,9 +516,9 @@ __device__ __forceinline__ void opg_block(const OpParams& p, const int e0, const
     }
   }
   __syncthreads();
-  const Real* gA = static_cast<const Real*>(p.geoA) + (size_t)e * 9 * N3;
-  const Real* gF = static_cast<const Real*>(p.geoF) + (size_t)e * 36 * N2;
-  const Real* gM = static_cast<const Real*>(p.geoM) + (size_t)e * 2 * N3;
+  const Real* gA = static_cast<const Real*>(p.geoA) + (size_t)e * geo_stride_A(N);
+  const Real* gF = static_cast<const Real*>(p.geoF) + (size_t)e * geo_stride_F(N);
+  const Real* gM = static_cast<const Real*>(p.geoM) + (size_t)e * geo_stride_M(N);
   if (act) {  // y
     Real u[4][N], r[4][N];
     const int base = line_base<1, N, N>(a, b);
@@ -537,12 +590,171 @@ __device__ __forceinline__ void opg_block(const OpParams& p, const int e0, const
   }
 }
 
+// Shared-memory layout of the staged Gauss-basis operator, per block of epb
+// elements: [U][R][neighbour traces][geoA][geoM][geoF][X], X = the LSRK
+// register (or the state the ADER update adds to); every region 16-byte
+// aligned.
+template <int N>
+__host__ __device__ constexpr int opgs_smem_per_elem() {
+  return 4 * N * N * N * 3 + 24 * N * N + geo_stride_A(N) + geo_stride_M(N) + geo_stride_F(N);
+}
+
+// The Gauss-basis operator with its inputs staged: one thread issues bulk
+// asynchronous copies of the block's elements (state, LSRK register or added
+// state, cell metric, mass diagonal, face data; each a contiguous run in
+// global memory) into shared memory, so the block's whole input is in flight
+// at once; the phases then read shared memory.  Neighbour lines are still
+// read from global memory (mostly L2 hits).
+template <int N, typename Real, int EPI>
+__device__ __forceinline__ void opgs_block(const OpParams& p, const int e0, const int ne, const int epb,
+                                           Real* sm) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int GA = geo_stride_A(N), GM = geo_stride_M(N), GF = geo_stride_F(N);
+  __shared__ __align__(8) uint64_t bar;
+  const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
+  const int a = t % N, b = t / N;
+  const int e = e0 + le;
+  const bool act = le < ne;
+  Real* suA = sm;
+  Real* srA = suA + epb * 4 * N3;
+  Real* snA = srA + epb * 4 * N3;
+  Real* gAA = snA + epb * 24 * N2;
+  Real* gMA = gAA + epb * GA;
+  Real* gFA = gMA + epb * GM;
+  Real* sxA = gFA + epb * GF;
+  const bool need_x = (EPI == EPI_LSRK && !p.first) || EPI == EPI_ADD;
+  const Real* __restrict__ U = static_cast<const Real*>(p.U);
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t sb = ne * 4 * N3 * sizeof(Real);
+    const uint32_t tot = sb * (need_x ? 2 : 1) + ne * (GA + GM + GF) * sizeof(Real);
+    mbar_expect_tx(&bar, tot);
+    bulk_copy_g2s(suA, U + (size_t)e0 * 4 * N3, sb, &bar);
+    bulk_copy_g2s(gAA, static_cast<const Real*>(p.geoA) + (size_t)e0 * GA, ne * GA * sizeof(Real), &bar);
+    bulk_copy_g2s(gMA, static_cast<const Real*>(p.geoM) + (size_t)e0 * GM, ne * GM * sizeof(Real), &bar);
+    bulk_copy_g2s(gFA, static_cast<const Real*>(p.geoF) + (size_t)e0 * GF, ne * GF * sizeof(Real), &bar);
+    if (need_x) {
+      const Real* X = EPI == EPI_LSRK ? static_cast<const Real*>(p.dU) : static_cast<const Real*>(p.Uadd);
+      bulk_copy_g2s(sxA, X + (size_t)e0 * 4 * N3, sb, &bar);
+    }
+  }
+  Real* su = suA + le * 4 * N3;
+  Real* sr = srA + le * 4 * N3;
+  Real* snb = snA + le * 24 * N2;
+  // neighbours' traces from global memory while the copies are in flight
+  int fmask = 0;
+  if (act) {
+    int en[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) en[f] = p.nbr[e * 6 + f];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      if (en[f] < 0) continue;
+      fmask |= 1 << f;
+      const int fn = p.nbr_face[e * 6 + f], o = p.orient[e * 6 + f];
+      const int uu = (o & 1) ? b : a, vv = (o & 1) ? a : b;
+      const int ip = (o & 2) ? N - 1 - uu : uu, jp = (o & 4) ? N - 1 - vv : vv;
+      const int dn = fn >> 1, sd = fn & 1;
+      const int t0 = dn == 0 ? 1 : 0, t1 = dn == 2 ? 1 : 2;
+      const int st = dn == 0 ? 1 : (dn == 1 ? N : N2);
+      const int s0 = t0 == 0 ? 1 : (t0 == 1 ? N : N2), s1 = t1 == 1 ? N : N2;
+      const Real* src = U + (size_t)en[f] * 4 * N3 + ip * s0 + jp * s1;
+      constexpr int LF = OFF_LF(N);
+#pragma unroll
+      for (int fl = 0; fl < 4; ++fl) {
+        Real acc = tab<Real>(LF + sd * N) * __ldg(src + fl * N3);
+#pragma unroll
+        for (int s = 1; s < N; ++s) acc = fma(tab<Real>(LF + sd * N + s), __ldg(src + fl * N3 + s * st), acc);
+        snb[(f * 4 + fl) * N2 + t] = acc;
+      }
+    }
+  }
+  const bool ok = mbar_wait_bounded(&bar, 0, p.err);
+  __syncthreads();
+  const Real* gA = gAA + le * GA;
+  const Real* gF = gFA + le * GF;
+  const Real* gM = gMA + le * GM;
+  if (act && ok) {  // y
+    Real u[4][N], r[4][N];
+    const int base = line_base<1, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + N * s];
+    cell_face_dir<N, Real, 1, false, true>(u, r, gA, gF, snb, t, fmask);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + N * s] = r[fl][s];
+  }
+  __syncthreads();
+  if (act && ok) {  // x
+    Real u[4][N], r[4][N];
+    const int base = line_base<0, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) {
+        u[fl][s] = su[fl * N3 + base + s];
+        r[fl][s] = sr[fl * N3 + base + s];
+      }
+    cell_face_dir<N, Real, 0, true, true>(u, r, gA, gF, snb, t, fmask);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + s] = r[fl][s];
+  }
+  __syncthreads();
+  if (act && ok) {  // z, then the diagonal inverse mass
+    Real u[4][N], r[4][N];
+    const int base = line_base<2, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) {
+        u[fl][s] = su[fl * N3 + base + N2 * s];
+        r[fl][s] = sr[fl * N3 + base + N2 * s];
+      }
+    cell_face_dir<N, Real, 2, true, true>(u, r, gA, gF, snb, t, fmask);
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+      const Real mp = gM[base + N2 * s], mvv = gM[N3 + base + N2 * s];
+      sr[base + N2 * s] = r[0][s] * mp;
+#pragma unroll
+      for (int fl = 1; fl < 4; ++fl) sr[fl * N3 + base + N2 * s] = r[fl][s] * mvv;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_inval(&bar);
+  if (!ok) return;
+  Real* __restrict__ out = static_cast<Real*>(p.out);
+  Real* __restrict__ dU = static_cast<Real*>(p.dU);
+  const Real cA = (Real)p.cA, cB = (Real)p.cB, dt = (Real)p.dt;
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+    const Real R = srA[i];
+    const size_t g = (size_t)e0 * 4 * N3 + i;
+    if (EPI == EPI_WRITE) {
+      out[g] = R;
+    } else if (EPI == EPI_ADD) {
+      out[g] = sxA[i] + R;
+    } else {  // LSRK: the stage input is the staged state
+      const Real d = p.first ? dt * R : fma(cA, sxA[i], dt * R);
+      dU[g] = d;
+      out[g] = fma(cB, d, suA[i]);
+    }
+  }
+}
+
 template <int N, typename Real, int EPI>
 __global__ void opg_kernel(const OpParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int epb = blockDim.x / (N * N);
   const int e0 = blockIdx.x * epb;
-  opg_block<N, Real, EPI>(p, e0, min(epb, p.E - e0), reinterpret_cast<Real*>(smem_raw));
+  if constexpr (sizeof(Real) == 4)
+    opgs_block<N, Real, EPI>(p, e0, min(epb, p.E - e0), epb, reinterpret_cast<Real*>(smem_raw));
+  else
+    opg_block<N, Real, EPI>(p, e0, min(epb, p.E - e0), reinterpret_cast<Real*>(smem_raw));
 }
 
 // In-place change of basis of whole states: GL -> G (to_g) or G -> GL.
@@ -892,7 +1104,7 @@ __global__ void energy_kernel(const EnergyParams p) {
   __syncthreads();
   double s = 0.0;
   if (act) {
-    const Real* gM = static_cast<const Real*>(p.geoM) + (size_t)e * 2 * N3;
+    const Real* gM = static_cast<const Real*>(p.geoM) + (size_t)e * geo_stride_M(N);
     for (int q = t; q < N3; q += N2) {
       const double pp = su[q], vx = su[N3 + q], vy = su[2 * N3 + q], vz = su[3 * N3 + q];
       s += pp * pp / (double)gM[q] + (vx * vx + vy * vy + vz * vz) / (double)gM[N3 + q];

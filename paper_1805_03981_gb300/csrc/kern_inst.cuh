@@ -22,9 +22,14 @@ cudaError_t launch_op(const OpParams& p, int epi, int epb, cudaStream_t st) {
 }
 
 template <int N, typename Real>
+constexpr int opg_smem_per_elem() {
+  return sizeof(Real) == 4 ? opgs_smem_per_elem<N>() : op_smem_per_elem<N>();
+}
+
+template <int N, typename Real>
 cudaError_t launch_opg(const OpParams& p, int epi, int epb, cudaStream_t st) {
   const int threads = epb * N * N;
-  const size_t smem = (size_t)epb * op_smem_per_elem<N>() * sizeof(Real);
+  const size_t smem = (size_t)epb * opg_smem_per_elem<N, Real>() * sizeof(Real);
   const int blocks = (p.E + epb - 1) / epb;
   if (epi == EPI_WRITE)
     opg_kernel<N, Real, EPI_WRITE><<<blocks, threads, smem, st>>>(p);
@@ -69,7 +74,7 @@ cudaError_t launch_energy(const EnergyParams& p, int epb, cudaStream_t st) {
 // which: 0 operator, 1 predictor, 2 energy
 template <int N, typename Real>
 int smem_bytes(int which, int red) {
-  if (which == 0) return op_smem_per_elem<N>() * (int)sizeof(Real);
+  if (which == 0) return max(op_smem_per_elem<N>(), opg_smem_per_elem<N, Real>()) * (int)sizeof(Real);
   if (which == 1)
     return (red == 2 ? tck_smem_per_elem<N, 2>() : tck_smem_per_elem<N, 0>()) * (int)sizeof(Real);
   return 4 * N * N * N * (int)sizeof(Real);

@@ -69,7 +69,7 @@ size_t estimate_bytes(int E, int k, int q, int prec) {
   b += (size_t)E * (4 * 6 + 6 + 6);                  // connectivity
   b += (size_t)E * 3 * qc * qc * qc * 8;             // geometry nodes
   b += (size_t)E * 2 * n3 * 8;                       // rho, c
-  b += (size_t)E * (11 * n3 + 36 * n * n + tck) * rs;  // geometry and coefficients
+  b += (size_t)E * (11 * n3 + 36 * n * n + 24 + tck) * rs;  // geometry and coefficients (padded)
   b += 5 * state;                                    // U2, U3, dU, Ubar and U
   return b + (1 << 20);
 }

@@ -8,6 +8,7 @@
 //   geoA [3 d][3 i][n^3] line-major per d   w adj(J)_{d i} = w detJ (J^-1)_{d i}
 //   geoM [2][n^3]                            rho c^2/(w detJ), 1/(rho w detJ)
 //   geoF [6 f][6][n^2]                       nw = w_f adj(J)_{d .} (+-1),
+//   (per-element strides geo_stride_A/M/F of tables.h: padded to 8 values)
 //                                            Z-/(Z-+Z+), alpha Z- Z+/((Z-+Z+)|nw|),
 //                                            alpha |nw|/(Z-+Z+)
 //   geoT per level m = n, n-2, ... >= 2: [3 d][3 i][m^3] J^-1_{d i} line-major,
@@ -127,10 +128,10 @@ __global__ void setup_kernel(const SetupParams P) {
       const double r = nodal_at(rho, xgl, n, xi), c = nodal_at(cc, xgl, n, xi);
       for (int d = 0; d < 3; ++d)
         for (int i = 0; i < 3; ++i)
-          put(P.geoA, (size_t)e * 9 * n3 + (d * 3 + i) * n3 + line_major(d, n, x, y, z), w * A[d][i],
+          put(P.geoA, (size_t)e * geo_stride_A(n) + (d * 3 + i) * n3 + line_major(d, n, x, y, z), w * A[d][i],
               P.prec);
-      put(P.geoM, (size_t)e * 2 * n3 + it, r * c * c / (w * det), P.prec);
-      put(P.geoM, (size_t)e * 2 * n3 + n3 + it, 1.0 / (r * w * det), P.prec);
+      put(P.geoM, (size_t)e * geo_stride_M(n) + it, r * c * c / (w * det), P.prec);
+      put(P.geoM, (size_t)e * geo_stride_M(n) + n3 + it, 1.0 / (r * w * det), P.prec);
     } else if (it < ncell + nface) {
       const int k = it - ncell;
       const int f = k / n2, ij = k - f * n2, i = ij % n, j = ij / n;
@@ -161,7 +162,7 @@ __global__ void setup_kernel(const SetupParams P) {
         zp = nodal_at(P.rho + (size_t)en * n3, xgl, n, xn) * nodal_at(P.c + (size_t)en * n3, xgl, n, xn);
       }
       const double zs = zm + zp;
-      const size_t fb = (size_t)e * 36 * n2 + (size_t)f * 6 * n2 + ij;
+      const size_t fb = (size_t)e * geo_stride_F(n) + (size_t)f * 6 * n2 + ij;
       put(P.geoF, fb, nw[0], P.prec);
       put(P.geoF, fb + n2, nw[1], P.prec);
       put(P.geoF, fb + 2 * n2, nw[2], P.prec);

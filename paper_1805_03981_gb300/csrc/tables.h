@@ -44,6 +44,14 @@ constexpr int DG_TAB_LEN = dg_tab_base(DG_NMAX + 1);
 DG_HD constexpr int dg_pts_off(int c) { return c * (c - 1) / 2; }
 constexpr int DG_PTS_LEN = dg_pts_off(DG_NMAX + 2);
 
+// Per-element strides (in values) of the operator's geometry arrays, padded
+// to multiples of 8 values so that every element's block starts on a 32-byte
+// boundary (bulk asynchronous copies need 16-byte alignment).
+DG_HD constexpr int dg_pad8(int x) { return (x + 7) / 8 * 8; }
+DG_HD constexpr int geo_stride_A(int n) { return dg_pad8(9 * n * n * n); }
+DG_HD constexpr int geo_stride_M(int n) { return dg_pad8(2 * n * n * n); }
+DG_HD constexpr int geo_stride_F(int n) { return dg_pad8(36 * n * n); }
+
 namespace dg {
 
 struct HostTables {

@@ -201,4 +201,16 @@ def test_gauss_basis_steppers_match_oracle(k, method):
     else:
         s32.step_ader(V, dt, 3, 2)
     torch.cuda.synchronize()
+    s32.check_device()
     assert rel_l2(V.cpu().numpy(), ref) < 2e-5
+
+
+def test_misaligned_state_rejected():
+    torch = _cuda()
+    cfg = _curved(2, 2, seed=3)
+    s, _ = pair(cfg)
+    n = cfg["U0"].size
+    buf = torch.zeros(n + 1, dtype=torch.float64, device="cuda")
+    view = buf[1:].view(cfg["U0"].shape)          # 8-byte offset
+    with pytest.raises(dgw.DGError):
+        s.step_lsrk(view, 0.001, 1)
