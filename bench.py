@@ -551,8 +551,9 @@ def main():
     avg_s = tot_ms * 1e-3 / max(nlaunch, 1)
     E = N ** 3
     nonwall = 1.0 if args.workload == "plane_wave" else 1.0 - 1.0 / N
-    flops = opcount.flops_per_element(dom, k + 1, 2, nonwall, args.basis) * E
-    byts = opcount.bytes_per_element(dom, k + 1, rsize, 2) * E
+    aff = s.is_affine()
+    flops = opcount.flops_per_element(dom, k + 1, 2, nonwall, args.basis, aff) * E
+    byts = opcount.bytes_per_element(dom, k + 1, rsize, 2, affine=aff and (args.basis == "g" or dom == "tck")) * E
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
     hbm = peaks.get("hbm_gbs")
     if prec == dgw.DG_FP64:
@@ -620,6 +621,7 @@ def main():
             "config": {"workload": workload_desc(N, k, args.prec, args.workload), "elements": E, "k": k, "dof": dof,
                        "state_basis_inside_steppers": "Gauss points (G)" if args.basis == "g" else "Gauss-Lobatto (GL)",
                        "tiling_elements_per_block": {"operator": tiling[0], "tck": tiling[1]},
+                       "affine_compact_kernels": s.is_affine(),
                        "l2": "inputs larger than L2 (state %d MB, %d MB device-resident incl. geometry), no flush"
                        % (state_bytes >> 20, s.device_bytes() >> 20),
                        "parallelism": "replicas" if world > 1 else "single"},

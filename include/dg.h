@@ -170,6 +170,15 @@ int dg_set_basis(dg_ctx* ctx, int basis);
 int dg_get_basis(const dg_ctx* ctx);
 
 /*
+ * 1 if every element is an affine image of the reference cube and the
+ * coefficients are constant within each element (checked at set-up and at
+ * dg_set_coefficients), else 0. Such meshes get compact per-element data
+ * (metric, mass and face constants times Gauss weights) in the Gauss-basis
+ * operator and in the predictor: same scheme, much less data to read.
+ */
+int dg_is_affine(const dg_ctx* ctx);
+
+/*
  * The predictor alone: Ubar (device, GL basis) = sum_j dt^{j+1}/(j+1)! T_j of
  * Eq. (6) for the state U. U and Ubar must not overlap.
  */

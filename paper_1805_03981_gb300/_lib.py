@@ -17,6 +17,7 @@ EXPORTED_SYMBOLS = [
     "dg_batch_step_lsrk", "dg_batch_info", "dg_batch_last_error", "dg_batch_destroy",
     "dg_server_create", "dg_submit", "dg_poll", "dg_server_stats", "dg_server_destroy",
     "dg_request_bytes", "dg_mesh_setup_coef", "dg_set_basis", "dg_get_basis", "dg_check_device",
+    "dg_is_affine",
 ]
 BASIS_GL, BASIS_G = 0, 1
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
@@ -117,6 +118,7 @@ def load_library():
         "dg_request_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
         "dg_set_basis": (C.c_int, [vp, C.c_int]),
         "dg_check_device": (C.c_int, [vp, st]),
+        "dg_is_affine": (C.c_int, [vp]),
         "dg_get_basis": (C.c_int, [vp]),
         "dg_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
         "dg_last_error": (C.c_char_p, [vp]),
@@ -274,6 +276,9 @@ class Solver:
     def check_device(self, stream=None):
         """Raise DGError(DG_ETIMEOUT) if a bounded device wait gave up."""
         self._check(self.lib.dg_check_device(self.ctx, _stream(stream)))
+
+    def is_affine(self):
+        return bool(self.lib.dg_is_affine(self.ctx))
 
     def set_basis(self, basis):
         """BASIS_GL (paper's storage, default) or BASIS_G (Gauss values inside the steppers)."""

@@ -92,6 +92,10 @@ struct dg_ctx {
   void* geoM = nullptr;
   void* geoF = nullptr;
   void* geoT = nullptr;
+  void* geoK = nullptr;   // compact affine data (affine meshes only)
+  void* geoKT = nullptr;
+  bool geo_affine = false;  // every element is an affine image of the cube
+  bool affine = false;      // ... and has constant coefficients: compact kernels
   int tstride = 0;
   void* U2 = nullptr;    // LSRK intermediate stage states
   void* U3 = nullptr;
@@ -265,6 +269,45 @@ int validate_mesh(const dg_mesh_desc* m, std::string* err) {
   return DG_OK;
 }
 
+// Is every element the affine image of the reference cube?  The geometry
+// nodes must lie on the affine map through the corners (-1,-1,-1), (+1,-1,-1),
+// (-1,+1,-1), (-1,-1,+1).
+bool mesh_is_affine(const dg_mesh_desc* m) {
+  const int q = m->geom_degree, c = q + 1;
+  std::vector<double> xq(DG_NMAX + 2);
+  gauss_lobatto(c, xq.data());
+  for (int e = 0; e < m->n_elem; ++e) {
+    const double* X = m->nodes + (size_t)e * c * c * c * 3;
+    auto node = [&](int i, int j, int k) { return X + 3 * (i + c * j + c * c * k); };
+    const double *x0 = node(0, 0, 0), *xa = node(q, 0, 0), *xb = node(0, q, 0), *xc = node(0, 0, q);
+    double scale = 0.0;
+    for (int d = 0; d < 3; ++d)
+      scale = std::max(scale, std::fabs(xa[d] - x0[d]) + std::fabs(xb[d] - x0[d]) + std::fabs(xc[d] - x0[d]));
+    for (int k = 0; k < c; ++k)
+      for (int j = 0; j < c; ++j)
+        for (int i = 0; i < c; ++i) {
+          const double* y = node(i, j, k);
+          const double s = 0.5 * (xq[i] + 1), t = 0.5 * (xq[j] + 1), u = 0.5 * (xq[k] + 1);
+          for (int d = 0; d < 3; ++d) {
+            const double aff = x0[d] + s * (xa[d] - x0[d]) + t * (xb[d] - x0[d]) + u * (xc[d] - x0[d]);
+            if (std::fabs(y[d] - aff) > 1e-12 * scale) return false;
+          }
+        }
+  }
+  return true;
+}
+
+// Are the nodal coefficient values constant within every element?
+bool coef_constant(const double* rho, const double* c, int E, int n3) {
+  if (!rho) return true;
+  for (int e = 0; e < E; ++e)
+    for (int i = 1; i < n3; ++i) {
+      const size_t a = (size_t)e * n3, b = a + i;
+      if (rho[b] != rho[a] || c[b] != c[a]) return false;
+    }
+  return true;
+}
+
 int pick_epb(int n, int bytes_per_elem, int target_threads, int max_threads) {
   int epb = target_threads / (n * n);
   if (epb < 1) epb = 1;
@@ -291,6 +334,8 @@ int run_setup(dg_ctx* ctx, cudaStream_t st) {
   P.geoM = ctx->geoM;
   P.geoF = ctx->geoF;
   P.geoT = ctx->geoT;
+  P.geoK = ctx->affine ? ctx->geoK : nullptr;
+  P.geoKT = ctx->affine ? ctx->geoKT : nullptr;
   P.tstride = ctx->tstride;
   P.prec = ctx->prec;
   P.bad = ctx->bad;
@@ -313,13 +358,15 @@ OpParams op_params(const dg_ctx* ctx) {
   p.geoA = ctx->geoA;
   p.geoM = ctx->geoM;
   p.geoF = ctx->geoF;
+  p.geoK = ctx->geoK;
   p.err = ctx->bad;
   p.E = ctx->E;
   return p;
 }
 
 int launch_op(dg_ctx* ctx, const OpParams& p, int epi, cudaStream_t st, bool gbasis = false) {
-  OpFn fn = gbasis ? g_kt.opg[ctx->prec][ctx->n] : g_kt.op[ctx->prec][ctx->n];
+  OpFn fn = gbasis ? (ctx->affine ? g_kt.opga[ctx->prec][ctx->n] : g_kt.opg[ctx->prec][ctx->n])
+                   : g_kt.op[ctx->prec][ctx->n];
   const int kind = epi == EPI_WRITE ? DG_KIND_OPERATOR : (epi == EPI_LSRK ? DG_KIND_LSRK : DG_KIND_ADER);
   dg_ctx::Span span(ctx, kind, st);
   DG_CK(fn(p, epi, ctx->epb_op, st), "operator kernel launch");
@@ -342,6 +389,8 @@ int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaS
   TckParams p;
   std::memset(&p, 0, sizeof(p));
   p.gmode = gbasis ? 1 : 0;
+  p.aff = ctx->affine ? 1 : 0;
+  p.geoKT = ctx->geoKT;
   p.U = U;
   p.Ubar = Ubar;
   p.geoT = ctx->geoT;
@@ -559,6 +608,13 @@ int dg_mesh_setup_coef(const dg_mesh_desc* m, int k, int prec, double alpha, con
       (rc = ctx->alloc(&ctx->geoF, rs * geo_stride_F(n) * (size_t)E, "face data")) ||
       (rc = ctx->alloc(&ctx->geoT, rs * (size_t)ctx->tstride * E, "predictor geometry")))
     return bail(rc);
+  ctx->geo_affine = mesh_is_affine(m);
+  if (ctx->geo_affine) {
+    if ((rc = ctx->alloc(&ctx->geoK, rs * DG_AFF_OP * (size_t)E, "affine operator data")) ||
+        (rc = ctx->alloc(&ctx->geoKT, rs * DG_AFF_TCK * (size_t)E, "affine predictor data")))
+      return bail(rc);
+    ctx->affine = coef_constant(rho_h, c_h, E, n3);
+  }
   std::vector<double> hpts(3 * DG_PTS_LEN);
   std::memcpy(hpts.data(), g_tab.xg, sizeof(double) * DG_PTS_LEN);
   std::memcpy(hpts.data() + DG_PTS_LEN, g_tab.wg, sizeof(double) * DG_PTS_LEN);
@@ -615,6 +671,7 @@ int dg_set_coefficients(dg_ctx* ctx, const double* rho, const double* c, uintptr
   cudaStream_t st = S(stream);
   DG_CK(cudaMemcpyAsync(ctx->rho, rho, sizeof(double) * cnt, cudaMemcpyHostToDevice, st), "upload rho");
   DG_CK(cudaMemcpyAsync(ctx->c, c, sizeof(double) * cnt, cudaMemcpyHostToDevice, st), "upload c");
+  ctx->affine = ctx->geo_affine && coef_constant(rho, c, ctx->E, ctx->n * ctx->n * ctx->n);
   return run_setup(ctx, st);
 }
 
@@ -753,6 +810,8 @@ int dg_set_basis(dg_ctx* ctx, int basis) {
 }
 
 int dg_get_basis(const dg_ctx* ctx) { return ctx ? ctx->basis : DG_EINVAL; }
+
+int dg_is_affine(const dg_ctx* ctx) { return ctx ? (ctx->affine ? 1 : 0) : DG_EINVAL; }
 
 int dg_check_device(dg_ctx* ctx, uintptr_t stream) {
   if (!ctx) return DG_EINVAL;

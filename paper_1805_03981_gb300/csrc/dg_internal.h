@@ -28,6 +28,8 @@ struct SetupParams {
   void* geoM;
   void* geoF;
   void* geoT;
+  void* geoK;   // compact affine operator data, or nullptr
+  void* geoKT;  // compact affine predictor data, or nullptr
   int tstride;
   int prec;  // 0 double, 1 float
   int* bad;  // set to 1 if det J <= 0 anywhere
@@ -44,7 +46,8 @@ typedef int (*MaxThrFn)(int which);          // largest launchable block
 
 struct KernelTable {
   OpFn op[2][DG_NMAX + 1];
-  OpFn opg[2][DG_NMAX + 1];  // operator on Gauss-basis states
+  OpFn opg[2][DG_NMAX + 1];   // operator on Gauss-basis states
+  OpFn opga[2][DG_NMAX + 1];  // same, affine elements with constant coefficients
   BasisFn basis[2][DG_NMAX + 1];
   TckFn tck[2][DG_NMAX + 1];
   EnergyFn energy[2][DG_NMAX + 1];

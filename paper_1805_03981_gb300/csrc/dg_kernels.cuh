@@ -184,6 +184,7 @@ struct OpParams {
   const void* geoA;  // [E][3 d][3 i][n^3] line-major per d: w adj(J)_{d i}   (stride geo_stride_A)
   const void* geoM;  // [E][2][n^3]: rho c^2 / (w detJ), 1 / (rho w detJ)    (stride geo_stride_M)
   const void* geoF;  // [E][6 f][6][n^2]: nw_x, nw_y, nw_z, Z-/(Z-+Z+), b, c (stride geo_stride_F)
+  const void* geoK;  // [E][DG_AFF_OP] compact data of affine elements (affine kernels only)
   int* err;          // set (non-zero) if a bounded wait gave up
   int E;
 };
@@ -757,6 +758,251 @@ __global__ void opg_kernel(const OpParams p) {
     opg_block<N, Real, EPI>(p, e0, min(epb, p.E - e0), reinterpret_cast<Real*>(smem_raw));
 }
 
+
+// ---------------------------------------------------------------------------
+// Affine elements with element-wise constant coefficients: the metric, the
+// mass diagonal and the face data are per-element constants times Gauss
+// weights (w at a cell point, w_f = w_i w_j at a face point), read from the
+// compact block of DG_AFF_OP values (see setup.cu).  With a constant metric
+// the velocity tests need one contraction of w p per direction,
+// distributed with adj(J)_{d i}.
+// ---------------------------------------------------------------------------
+template <int N, typename Real, int DIR, bool ACC, bool SMEM>
+__device__ __forceinline__ void cell_face_dir_aff(const Real (&u)[4][N], Real (&r)[4][N],
+                                                  const Real* __restrict__ g, const Real wab,
+                                                  const Real iwab, const Real* snb, int t, int fmask) {
+  constexpr int N2 = N * N;
+  constexpr int W = OFF_W(N);
+  const Real a0 = geo_ld<Real, SMEM>(g + DIR * 3), a1 = geo_ld<Real, SMEM>(g + DIR * 3 + 1),
+             a2 = geo_ld<Real, SMEM>(g + DIR * 3 + 2);
+  Real F[N], DG[N];
+#pragma unroll
+  for (int s = 0; s < N; ++s)
+    F[s] = (wab * tab<Real>(W + s)) * fma(a0, u[1][s], fma(a1, u[2][s], a2 * u[3][s]));
+  if (ACC)
+    mtv_acc<Real, OFF_D(N), N, N>(F, r[0]);
+  else
+    mtv<Real, OFF_D(N), N, N>(F, r[0]);
+#pragma unroll
+  for (int s = 0; s < N; ++s) F[s] = (wab * tab<Real>(W + s)) * u[0][s];
+  mtv<Real, OFF_D(N), N, N>(F, DG);
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (ACC) {
+      r[1][j] = fma(a0, DG[j], r[1][j]);
+      r[2][j] = fma(a1, DG[j], r[2][j]);
+      r[3][j] = fma(a2, DG[j], r[3][j]);
+    } else {
+      r[1][j] = a0 * DG[j];
+      r[2][j] = a1 * DG[j];
+      r[3][j] = a2 * DG[j];
+    }
+  }
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    const int f = 2 * DIR + sd;
+    constexpr int LF = OFF_LF(N);
+    Real um[4];
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl) {
+      Real acc = tab<Real>(LF + sd * N) * u[fl][0];
+#pragma unroll
+      for (int s = 1; s < N; ++s) acc = fma(tab<Real>(LF + sd * N + s), u[fl][s], acc);
+      um[fl] = acc;
+    }
+    const Real* fc = g + 11 + f * 6;
+    const Real nw0 = wab * geo_ld<Real, SMEM>(fc), nw1 = wab * geo_ld<Real, SMEM>(fc + 1),
+               nw2 = wab * geo_ld<Real, SMEM>(fc + 2);
+    const Real ca2 = geo_ld<Real, SMEM>(fc + 3), bb = iwab * geo_ld<Real, SMEM>(fc + 4),
+               cc = wab * geo_ld<Real, SMEM>(fc + 5);
+    const Real vnm = fma(nw0, um[1], fma(nw1, um[2], nw2 * um[3]));
+    Real pp, vnp;
+    if ((fmask >> f) & 1) {
+      const Real* nb = snb + f * 4 * N2 + t;
+      pp = nb[0];
+      vnp = fma(nw0, nb[N2], fma(nw1, nb[2 * N2], nw2 * nb[3 * N2]));
+    } else {
+      pp = um[0];
+      vnp = -vnm;
+    }
+    const Real dp = um[0] - pp, dvn = vnm - vnp;
+    const Real pstar = fma(-ca2, dp, fma(bb, dvn, um[0]));
+    const Real flp = fma(ca2, dvn, fma(cc, dp, vnp));
+    const Real g0 = nw0 * pstar, g1 = nw1 * pstar, g2 = nw2 * pstar;
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+      const Real l = tab<Real>(LF + sd * N + s);
+      r[0][s] = fma(-l, flp, r[0][s]);
+      r[1][s] = fma(-l, g0, r[1][s]);
+      r[2][s] = fma(-l, g1, r[2][s]);
+      r[3][s] = fma(-l, g2, r[3][s]);
+    }
+  }
+}
+
+template <int N>
+__host__ __device__ constexpr int opga_smem_per_elem(bool stage) {
+  return 4 * N * N * N * (stage ? 3 : 2) + 24 * N * N + (stage ? DG_AFF_OP : 0);
+}
+
+// Gauss-basis operator on affine elements.  STAGE: the block's state, LSRK
+// register (or added state) and compact geometry come in by bulk
+// asynchronous copies on an mbarrier (as opgs_block); otherwise the state is
+// copied flat and the compact data read through the read-only path.
+template <int N, typename Real, int EPI, bool STAGE>
+__device__ __forceinline__ void opga_block(const OpParams& p, const int e0, const int ne, const int epb,
+                                           Real* sm) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  __shared__ __align__(8) uint64_t bar;
+  const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
+  const int a = t % N, b = t / N;
+  const int e = e0 + le;
+  const bool act = le < ne;
+  Real* suA = sm;
+  Real* srA = suA + epb * 4 * N3;
+  Real* snA = srA + epb * 4 * N3;
+  Real* gKA = snA + epb * 24 * N2;  // STAGE only
+  Real* sxA = gKA + epb * DG_AFF_OP;  // STAGE only
+  const bool need_x = (EPI == EPI_LSRK && !p.first) || EPI == EPI_ADD;
+  const Real* __restrict__ U = static_cast<const Real*>(p.U);
+  if constexpr (STAGE) {
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const uint32_t sb = ne * 4 * N3 * sizeof(Real);
+      const uint32_t gb = ne * DG_AFF_OP * sizeof(Real);
+      mbar_expect_tx(&bar, sb * (need_x ? 2 : 1) + gb);
+      bulk_copy_g2s(suA, U + (size_t)e0 * 4 * N3, sb, &bar);
+      bulk_copy_g2s(gKA, static_cast<const Real*>(p.geoK) + (size_t)e0 * DG_AFF_OP, gb, &bar);
+      if (need_x) {
+        const Real* X = EPI == EPI_LSRK ? static_cast<const Real*>(p.dU) : static_cast<const Real*>(p.Uadd);
+        bulk_copy_g2s(sxA, X + (size_t)e0 * 4 * N3, sb, &bar);
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) suA[i] = U[(size_t)e0 * 4 * N3 + i];
+  }
+  Real* su = suA + le * 4 * N3;
+  Real* sr = srA + le * 4 * N3;
+  Real* snb = snA + le * 24 * N2;
+  // weights of this thread's line: the two fixed coordinates are (a, b)
+  const Real wab = tab<Real>(OFF_W(N) + a) * tab<Real>(OFF_W(N) + b);
+  const Real iwab = tab<Real>(OFF_IW(N) + a) * tab<Real>(OFF_IW(N) + b);
+  int fmask = 0;
+  if (act) {
+    int en[6];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) en[f] = p.nbr[e * 6 + f];
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      if (en[f] < 0) continue;
+      fmask |= 1 << f;
+      const int fn = p.nbr_face[e * 6 + f], o = p.orient[e * 6 + f];
+      const int uu = (o & 1) ? b : a, vv = (o & 1) ? a : b;
+      const int ip = (o & 2) ? N - 1 - uu : uu, jp = (o & 4) ? N - 1 - vv : vv;
+      const int dn = fn >> 1, sd = fn & 1;
+      const int t0 = dn == 0 ? 1 : 0, t1 = dn == 2 ? 1 : 2;
+      const int st = dn == 0 ? 1 : (dn == 1 ? N : N2);
+      const int s0 = t0 == 0 ? 1 : (t0 == 1 ? N : N2), s1 = t1 == 1 ? N : N2;
+      const Real* src = U + (size_t)en[f] * 4 * N3 + ip * s0 + jp * s1;
+      constexpr int LF = OFF_LF(N);
+#pragma unroll
+      for (int fl = 0; fl < 4; ++fl) {
+        Real acc = tab<Real>(LF + sd * N) * __ldg(src + fl * N3);
+#pragma unroll
+        for (int s = 1; s < N; ++s) acc = fma(tab<Real>(LF + sd * N + s), __ldg(src + fl * N3 + s * st), acc);
+        snb[(f * 4 + fl) * N2 + t] = acc;
+      }
+    }
+  }
+  bool ok = true;
+  if constexpr (STAGE) ok = mbar_wait_bounded(&bar, 0, p.err);
+  __syncthreads();
+  const Real* gK = STAGE ? gKA + le * DG_AFF_OP : static_cast<const Real*>(p.geoK) + (size_t)(act ? e : 0) * DG_AFF_OP;
+  if (act && ok) {  // y
+    Real u[4][N], r[4][N];
+    const int base = line_base<1, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) u[fl][s] = su[fl * N3 + base + N * s];
+    cell_face_dir_aff<N, Real, 1, false, STAGE>(u, r, gK, wab, iwab, snb, t, fmask);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + N * s] = r[fl][s];
+  }
+  __syncthreads();
+  if (act && ok) {  // x
+    Real u[4][N], r[4][N];
+    const int base = line_base<0, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) {
+        u[fl][s] = su[fl * N3 + base + s];
+        r[fl][s] = sr[fl * N3 + base + s];
+      }
+    cell_face_dir_aff<N, Real, 0, true, STAGE>(u, r, gK, wab, iwab, snb, t, fmask);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) sr[fl * N3 + base + s] = r[fl][s];
+  }
+  __syncthreads();
+  if (act && ok) {  // z, then the diagonal inverse mass m / w
+    Real u[4][N], r[4][N];
+    const int base = line_base<2, N, N>(a, b);
+#pragma unroll
+    for (int fl = 0; fl < 4; ++fl)
+#pragma unroll
+      for (int s = 0; s < N; ++s) {
+        u[fl][s] = su[fl * N3 + base + N2 * s];
+        r[fl][s] = sr[fl * N3 + base + N2 * s];
+      }
+    cell_face_dir_aff<N, Real, 2, true, STAGE>(u, r, gK, wab, iwab, snb, t, fmask);
+    const Real mpab = geo_ld<Real, STAGE>(gK + 9) * iwab, mvab = geo_ld<Real, STAGE>(gK + 10) * iwab;
+#pragma unroll
+    for (int s = 0; s < N; ++s) {
+      const Real iw = tab<Real>(OFF_IW(N) + s);
+      const Real mp = mpab * iw, mvv = mvab * iw;
+      sr[base + N2 * s] = r[0][s] * mp;
+#pragma unroll
+      for (int fl = 1; fl < 4; ++fl) sr[fl * N3 + base + N2 * s] = r[fl][s] * mvv;
+    }
+  }
+  __syncthreads();
+  if constexpr (STAGE) {
+    if (threadIdx.x == 0) mbar_inval(&bar);
+  }
+  if (!ok) return;
+  Real* __restrict__ out = static_cast<Real*>(p.out);
+  Real* __restrict__ dU = static_cast<Real*>(p.dU);
+  const Real* __restrict__ Uadd = static_cast<const Real*>(p.Uadd);
+  const Real cA = (Real)p.cA, cB = (Real)p.cB, dt = (Real)p.dt;
+  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+    const Real R = srA[i];
+    const size_t g = (size_t)e0 * 4 * N3 + i;
+    if (EPI == EPI_WRITE) {
+      out[g] = R;
+    } else if (EPI == EPI_ADD) {
+      out[g] = (STAGE ? sxA[i] : Uadd[g]) + R;
+    } else {
+      const Real d = p.first ? dt * R : fma(cA, STAGE ? sxA[i] : dU[g], dt * R);
+      dU[g] = d;
+      out[g] = fma(cB, d, suA[i]);
+    }
+  }
+}
+
+template <int N, typename Real, int EPI>
+__global__ void opga_kernel(const OpParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int epb = blockDim.x / (N * N);
+  const int e0 = blockIdx.x * epb;
+  opga_block<N, Real, EPI, sizeof(Real) == 4>(p, e0, min(epb, p.E - e0), epb, reinterpret_cast<Real*>(smem_raw));
+}
+
 // In-place change of basis of whole states: GL -> G (to_g) or G -> GL.
 template <int N, typename Real>
 __global__ void basis_kernel(void* Uv, int E, int to_g) {
@@ -801,6 +1047,8 @@ struct TckParams {
   double coef[DG_NMAX + 2];  // dt^{j+1} / (j+1)!
   int E;
   int gmode;  // 1: U and Ubar hold Gauss-point values (no basis change)
+  int aff;    // 1: affine elements with constant coefficients (geoKT)
+  const void* geoKT;  // [E][DG_AFF_TCK]: J^-1 (9), -rho c^2, -1/rho
 };
 
 // m-point levels visited with reduction every second derivative: N, N-2, ...
@@ -890,6 +1138,62 @@ __device__ __forceinline__ void tck_derivative(const Real* src, Real* dst, const
   }
 }
 
+// The derivative step on an affine element with constant coefficients:
+// J^-1 is constant, so the pressure equation differentiates the combination
+// sum_i (J^-1)_{d i} v_i once per direction, and the velocity equations share
+// one derivative of p per direction (two contractions per direction instead
+// of four).  g: the element's DG_AFF_TCK values.
+template <int M, typename Real, int FS>
+__device__ __forceinline__ void tck_derivative_aff(const Real* src, Real* dst, const Real* __restrict__ g,
+                                                   int t, int nthr) {
+  constexpr int M2 = M * M;
+  const Real cp = __ldg(g + 9), cv = __ldg(g + 10);
+#pragma unroll
+  for (int dir = 0; dir < 3; ++dir) {
+    const Real j0 = __ldg(g + dir * 3), j1 = __ldg(g + dir * 3 + 1), j2 = __ldg(g + dir * 3 + 2);
+    for (int l = t; l < M2; l += nthr) {
+      const int a = l % M, b = l / M;
+      const int base = dir == 0 ? M * a + M2 * b : (dir == 1 ? a + M2 * b : a + M * b);
+      const int st = dir == 0 ? 1 : (dir == 1 ? M : M2);
+      Real q0[M], w[M], dp[M], dw[M];
+#pragma unroll
+      for (int s = 0; s < M; ++s) {
+        q0[s] = src[base + st * s];
+        w[s] = fma(j0, src[FS + base + st * s], fma(j1, src[2 * FS + base + st * s], j2 * src[3 * FS + base + st * s]));
+      }
+      mv<Real, OFF_D(M), M, M>(q0, dp);
+      mv<Real, OFF_D(M), M, M>(w, dw);
+#pragma unroll
+      for (int s = 0; s < M; ++s) {
+        const int idx = base + st * s;
+        Real tp, tv0, tv1, tv2;
+        if (dir > 0) {
+          tp = dw[s] + dst[idx];
+          tv0 = fma(j0, dp[s], dst[FS + idx]);
+          tv1 = fma(j1, dp[s], dst[2 * FS + idx]);
+          tv2 = fma(j2, dp[s], dst[3 * FS + idx]);
+        } else {
+          tp = dw[s];
+          tv0 = j0 * dp[s];
+          tv1 = j1 * dp[s];
+          tv2 = j2 * dp[s];
+        }
+        if (dir == 2) {
+          tp *= cp;
+          tv0 *= cv;
+          tv1 *= cv;
+          tv2 *= cv;
+        }
+        dst[idx] = tp;
+        dst[FS + idx] = tv0;
+        dst[2 * FS + idx] = tv1;
+        dst[3 * FS + idx] = tv2;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Reference L2 projection M^3 -> (M-2)^3 (Alg. 3): three contractions,
 // src (M^3, field stride FS) -> tmp -> src ... result in dst.
 template <int M, typename Real, int FS>
@@ -946,6 +1250,7 @@ __device__ __forceinline__ void tck_block(const TckParams& p, const int e0, cons
   Real* acc = s1 + 4 * N3;  // per-level accumulators (field stride m^3)
   const Real* __restrict__ U = static_cast<const Real*>(p.U);
   const Real* geo = static_cast<const Real*>(p.geoT) + (size_t)(act ? e : 0) * p.geoT_stride;
+  const Real* geoK = p.aff ? static_cast<const Real*>(p.geoKT) + (size_t)(act ? e : 0) * DG_AFF_TCK : nullptr;
 
   for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
     const int l = i / (4 * N3);
@@ -973,9 +1278,14 @@ __device__ __forceinline__ void tck_block(const TckParams& p, const int e0, cons
     const Real* g = geo + tck_geo_level_off(N, lvl);
     // derivative at the current m (T_{j-1} in cur, field stride N3)
     switch (m) {
-#define DG_TCK_DERIV(MM)                                                 \
-  case MM:                                                               \
-    if constexpr (MM <= N) tck_derivative<MM, Real, N3>(cur, nxt, g, t, N2); \
+#define DG_TCK_DERIV(MM)                                                         \
+  case MM:                                                                       \
+    if constexpr (MM <= N) {                                                     \
+      if (p.aff)                                                                 \
+        tck_derivative_aff<MM, Real, N3>(cur, nxt, geoK, t, N2);                 \
+      else                                                                       \
+        tck_derivative<MM, Real, N3>(cur, nxt, g, t, N2);                        \
+    }                                                                            \
     break;
       DG_TCK_DERIV(2) DG_TCK_DERIV(3) DG_TCK_DERIV(4) DG_TCK_DERIV(5) DG_TCK_DERIV(6)
       DG_TCK_DERIV(7) DG_TCK_DERIV(8)

@@ -41,6 +41,20 @@ cudaError_t launch_opg(const OpParams& p, int epi, int epb, cudaStream_t st) {
 }
 
 template <int N, typename Real>
+cudaError_t launch_opga(const OpParams& p, int epi, int epb, cudaStream_t st) {
+  const int threads = epb * N * N;
+  const size_t smem = (size_t)epb * opga_smem_per_elem<N>(sizeof(Real) == 4) * sizeof(Real);
+  const int blocks = (p.E + epb - 1) / epb;
+  if (epi == EPI_WRITE)
+    opga_kernel<N, Real, EPI_WRITE><<<blocks, threads, smem, st>>>(p);
+  else if (epi == EPI_LSRK)
+    opga_kernel<N, Real, EPI_LSRK><<<blocks, threads, smem, st>>>(p);
+  else
+    opga_kernel<N, Real, EPI_ADD><<<blocks, threads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <int N, typename Real>
 cudaError_t launch_basis(void* U, int E, int to_g, int epb, cudaStream_t st) {
   const int threads = epb * N * N;
   const size_t smem = (size_t)epb * 4 * N * N * N * sizeof(Real);
@@ -74,7 +88,10 @@ cudaError_t launch_energy(const EnergyParams& p, int epb, cudaStream_t st) {
 // which: 0 operator, 1 predictor, 2 energy
 template <int N, typename Real>
 int smem_bytes(int which, int red) {
-  if (which == 0) return max(op_smem_per_elem<N>(), opg_smem_per_elem<N, Real>()) * (int)sizeof(Real);
+  if (which == 0)
+    return max(max(op_smem_per_elem<N>(), opg_smem_per_elem<N, Real>()),
+               opga_smem_per_elem<N>(sizeof(Real) == 4)) *
+           (int)sizeof(Real);
   if (which == 1)
     return (red == 2 ? tck_smem_per_elem<N, 2>() : tck_smem_per_elem<N, 0>()) * (int)sizeof(Real);
   return 4 * N * N * N * (int)sizeof(Real);
@@ -105,6 +122,9 @@ cudaError_t set_max_smem() {
   if ((e = allow_smem(opg_kernel<N, Real, EPI_LSRK>)) != cudaSuccess) return e;
   if ((e = allow_smem(opg_kernel<N, Real, EPI_ADD>)) != cudaSuccess) return e;
   if ((e = allow_smem(basis_kernel<N, Real>)) != cudaSuccess) return e;
+  if ((e = allow_smem(opga_kernel<N, Real, EPI_WRITE>)) != cudaSuccess) return e;
+  if ((e = allow_smem(opga_kernel<N, Real, EPI_LSRK>)) != cudaSuccess) return e;
+  if ((e = allow_smem(opga_kernel<N, Real, EPI_ADD>)) != cudaSuccess) return e;
   if ((e = allow_smem(tck_kernel<N, Real, 0>)) != cudaSuccess) return e;
   if ((e = allow_smem(tck_kernel<N, Real, 2>)) != cudaSuccess) return e;
   return allow_smem(energy_kernel<N, Real>);
@@ -128,9 +148,11 @@ int max_threads(int which) {
     return min(min(kernel_max_threads(op_kernel<N, Real, EPI_WRITE>),
                    min(kernel_max_threads(op_kernel<N, Real, EPI_LSRK>),
                        kernel_max_threads(op_kernel<N, Real, EPI_ADD>))),
-               min(kernel_max_threads(opg_kernel<N, Real, EPI_WRITE>),
-                   min(kernel_max_threads(opg_kernel<N, Real, EPI_LSRK>),
-                       kernel_max_threads(opg_kernel<N, Real, EPI_ADD>))));
+               min(min(kernel_max_threads(opg_kernel<N, Real, EPI_WRITE>),
+                       min(kernel_max_threads(opg_kernel<N, Real, EPI_LSRK>),
+                           kernel_max_threads(opg_kernel<N, Real, EPI_ADD>))),
+                   min(kernel_max_threads(opga_kernel<N, Real, EPI_LSRK>),
+                       kernel_max_threads(opga_kernel<N, Real, EPI_ADD>))));
   if (which == 1)
     return min(kernel_max_threads(tck_kernel<N, Real, 0>), kernel_max_threads(tck_kernel<N, Real, 2>));
   return min(kernel_max_threads(energy_kernel<N, Real>), kernel_max_threads(basis_kernel<N, Real>));
@@ -141,6 +163,7 @@ void register_one(KernelTable* t) {
   const int pi = sizeof(Real) == 8 ? 0 : 1;
   t->op[pi][N] = &launch_op<N, Real>;
   t->opg[pi][N] = &launch_opg<N, Real>;
+  t->opga[pi][N] = &launch_opga<N, Real>;
   t->basis[pi][N] = &launch_basis<N, Real>;
   t->tck[pi][N] = &launch_tck<N, Real>;
   t->energy[pi][N] = &launch_energy<N, Real>;

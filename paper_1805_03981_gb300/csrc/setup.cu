@@ -196,11 +196,69 @@ __global__ void setup_kernel(const SetupParams P) {
   }
 }
 
+// Compact data of an affine element with constant coefficients (one thread
+// per element), in the context precision:
+//   geoK  [48]: adj(J)_{d i} (9), rho c^2 / detJ, 1 / (rho detJ),
+//               per face: nw0 = +-adj(J)_{d .} (3), Z-/(Z-+Z+),
+//               alpha Z- Z+ / ((Z-+Z+) |nw0|), alpha |nw0| / (Z-+Z+)
+//   geoKT [16]: J^-1_{d i} (9), -rho c^2, -1/rho
+// At a point with Gauss weight w (face: w_f) the per-point values of the
+// general layout are w adj(J), m / w, w_f nw0, b0 / w_f and c0 w_f.
+__global__ void setup_affine_kernel(const SetupParams P) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= P.E) return;
+  const int n = P.n, n3 = n * n * n;
+  const double* xgl = P.pts + 2 * DG_PTS_LEN + dg_pts_off(n);
+  const double ctr[3] = {0.0, 0.0, 0.0};
+  double J[3][3], A[3][3];
+  jacobian(P, e, ctr, J);
+  const double det = adjugate(J, A);
+  if (!(det > 0.0)) atomicExch(P.bad, 1);
+  const double r = nodal_at(P.rho + (size_t)e * n3, xgl, n, ctr);
+  const double c = nodal_at(P.c + (size_t)e * n3, xgl, n, ctr);
+  const size_t kb = (size_t)e * DG_AFF_OP, tb = (size_t)e * DG_AFF_TCK;
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i < 3; ++i) {
+      put(P.geoK, kb + d * 3 + i, A[d][i], P.prec);
+      put(P.geoKT, tb + d * 3 + i, A[d][i] / det, P.prec);
+    }
+  put(P.geoK, kb + 9, r * c * c / det, P.prec);
+  put(P.geoK, kb + 10, 1.0 / (r * det), P.prec);
+  put(P.geoKT, tb + 9, -r * c * c, P.prec);
+  put(P.geoKT, tb + 10, -1.0 / r, P.prec);
+  const double zm = r * c;
+  for (int f = 0; f < 6; ++f) {
+    const int d = f >> 1;
+    const double side = (f & 1) ? 1.0 : -1.0;
+    const double nw[3] = {side * A[d][0], side * A[d][1], side * A[d][2]};
+    const double s = sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
+    double zp = zm;
+    const int en = P.nbr[e * 6 + f];
+    if (en >= 0)
+      zp = nodal_at(P.rho + (size_t)en * n3, xgl, n, ctr) * nodal_at(P.c + (size_t)en * n3, xgl, n, ctr);
+    const double zs = zm + zp;
+    const size_t fb = kb + 11 + f * 6;
+    put(P.geoK, fb, nw[0], P.prec);
+    put(P.geoK, fb + 1, nw[1], P.prec);
+    put(P.geoK, fb + 2, nw[2], P.prec);
+    put(P.geoK, fb + 3, zm / zs, P.prec);
+    put(P.geoK, fb + 4, P.alpha * zm * zp / (zs * s), P.prec);
+    put(P.geoK, fb + 5, P.alpha * s / zs, P.prec);
+  }
+  put(P.geoK, kb + 47, 0.0, P.prec);
+  for (int i = 11; i < DG_AFF_TCK; ++i) put(P.geoKT, tb + i, 0.0, P.prec);
+}
+
 }  // namespace
 
 cudaError_t launch_setup(const SetupParams& P, cudaStream_t st) {
   setup_kernel<<<P.E, 128, 0, st>>>(P);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && P.geoK) {
+    setup_affine_kernel<<<(P.E + 127) / 128, 128, 0, st>>>(P);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace dg

@@ -129,6 +129,8 @@ int build_tables(HostTables* t) {
     for (int a = 0; a < c; ++a) {
       LF[a] = lagrange(xg.data(), c, a, -1.0);
       LF[c + a] = lagrange(xg.data(), c, a, 1.0);
+      t->tab[OFF_W(c) + a] = wg[a];
+      t->tab[OFF_IW(c) + a] = 1.0 / wg[a];
     }
     if (c > 2) {
       const int r = c - 2;

@@ -13,6 +13,7 @@
 //                  P[a][b] = w^c_b l^{c-2}_a(x^c_b) / w^{c-2}_a  (Sec. 3.3)
 //   IU [c][c-2]    prolongation Gauss(c-2) -> Gauss(c):
 //                  IU[q][b] = l^{c-2}_b(x^c_q)
+//   W  [c]         Gauss weights; IW [c] their inverses
 // The projection and prolongation blocks are empty for c <= 2.
 #pragma once
 
@@ -25,7 +26,7 @@
 #endif
 
 DG_HD constexpr int dg_tab_block(int c) {
-  return 3 * c * c + 2 * c + (c > 2 ? 2 * c * (c - 2) : 0);
+  return 3 * c * c + 2 * c + (c > 2 ? 2 * c * (c - 2) : 0) + 2 * c;
 }
 DG_HD constexpr int dg_tab_base(int c) {
   return c <= 1 ? 0 : dg_tab_base(c - 1) + dg_tab_block(c - 1);
@@ -36,6 +37,13 @@ DG_HD constexpr int OFF_D(int c) { return dg_tab_base(c) + 2 * c * c; }
 DG_HD constexpr int OFF_LF(int c) { return dg_tab_base(c) + 3 * c * c; }
 DG_HD constexpr int OFF_P(int c) { return dg_tab_base(c) + 3 * c * c + 2 * c; }
 DG_HD constexpr int OFF_IU(int c) { return OFF_P(c) + (c > 2 ? c * (c - 2) : 0); }
+DG_HD constexpr int OFF_W(int c) { return OFF_IU(c) + (c > 2 ? c * (c - 2) : 0); }
+DG_HD constexpr int OFF_IW(int c) { return OFF_W(c) + c; }
+
+// Compact per-element data of affine elements with element-wise constant
+// coefficients (see setup.cu): operator block and predictor block sizes.
+constexpr int DG_AFF_OP = 48;
+constexpr int DG_AFF_TCK = 16;
 constexpr int DG_TAB_LEN = dg_tab_base(DG_NMAX + 1);
 
 // Raw points for the geometry set-up: for each count c in [1, DG_NMAX],

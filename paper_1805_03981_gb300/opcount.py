@@ -16,11 +16,19 @@ def contraction(outputs, m):
     return 2 * m * outputs
 
 
-def operator_flops(n, curved=True, nonwall_frac=1.0, basis="gl"):
+def operator_flops(n, curved=True, nonwall_frac=1.0, basis="gl", affine=False):
     """R = -M^-1 K U on one element: basis changes, cell terms, faces, M^-1.
     basis "g": the state is held at the Gauss points (no basis changes; a
-    neighbour trace is one l(+-1) contraction of the neighbour's line)."""
+    neighbour trace is one l(+-1) contraction of the neighbour's line).
+    affine (with basis "g"): constant metric; per direction one contraction
+    of w sum_i adj_{d i} v_i and one of w p, distributed with adj_{d i}."""
     N3, N2 = n ** 3, n ** 2
+    if basis == "g" and affine:
+        f = 3 * N3 * (7 + 2 + 6) + 6 * contraction(N3, n) + 4 * N3
+        f += 6 * N2 * (4 * 2 * n + 5 + 5 + 2 + 4 + 4 + 3 + 4 * 2 * n + 5)
+        f += nonwall_frac * 6 * 4 * contraction(N2, n)
+        f += 6 * N3
+        return f
     if basis == "g":
         f = 3 * N3 * (5 + 3) + 12 * contraction(N3, n) + 2 * 4 * N3
         f += 6 * N2 * (4 * 2 * n + 5 + 5 + 2 + 4 + 4 + 3 + 4 * 2 * n)
@@ -57,9 +65,10 @@ def tck_levels(n, red):
     return seq
 
 
-def tck_flops(n, red=2, basis="gl"):
+def tck_flops(n, red=2, basis="gl", affine=False):
     N3 = n ** 3
     f = 0 if basis == "g" else 12 * contraction(N3, n) + 12 * contraction(N3, n)   # GL -> G, G -> GL
+    deriv_contr, deriv_pt = (6, 36) if affine else (12, 36)
     f += 2 * 4 * N3                                          # first Taylor term
     m = n
     levels = [n]
@@ -68,7 +77,7 @@ def tck_flops(n, red=2, basis="gl"):
             break
         if m > 1:
             m3 = m ** 3
-            f += 12 * contraction(m3, m) + 36 * m3           # derivatives + chain rule
+            f += deriv_contr * contraction(m3, m) + deriv_pt * m3   # derivatives + chain rule
         if red == 2 and j % 2 == 0:
             if m - 2 < 1:
                 break
@@ -94,28 +103,33 @@ def tck_geometry_reals(n, red=2):
     return 11 * sum(m ** 3 for m in lv)
 
 
-def bytes_per_element(kind, n, rsize, red=2, first_stage=False):
+AFF_OP, AFF_TCK = 48, 16   # compact per-element values of affine elements
+
+
+def bytes_per_element(kind, n, rsize, red=2, first_stage=False, affine=False):
     vec = 4 * n ** 3 * rsize
     conn = 6 * (4 + 1 + 1)
+    geo = (AFF_OP if affine else geometry_reals(n)) * rsize
     if kind == "operator":
-        return 2 * vec + geometry_reals(n) * rsize + conn
+        return 2 * vec + geo + conn
     if kind == "lsrk_stage":
-        return (3 if first_stage else 4) * vec + geometry_reals(n) * rsize + conn
+        return (3 if first_stage else 4) * vec + geo + conn
     if kind == "ader_update":
-        return 3 * vec + geometry_reals(n) * rsize + conn
+        return 3 * vec + geo + conn
     if kind == "tck":
-        return 2 * vec + tck_geometry_reals(n, red) * rsize
+        return 2 * vec + (AFF_TCK if affine else tck_geometry_reals(n, red)) * rsize
     if kind == "other":
         return 2 * vec
     raise ValueError(kind)
 
 
-def flops_per_element(kind, n, red=2, nonwall_frac=1.0, basis="gl"):
+def flops_per_element(kind, n, red=2, nonwall_frac=1.0, basis="gl", affine=False):
     if kind == "tck":
-        return tck_flops(n, red, basis)
+        return tck_flops(n, red, basis, affine)
     if kind == "other":                       # change of basis of a whole state
         return 12 * contraction(n ** 3, n)
-    return operator_flops(n, nonwall_frac=nonwall_frac, basis=basis) + EPILOGUE_FLOPS[kind] * 4 * n ** 3
+    return (operator_flops(n, nonwall_frac=nonwall_frac, basis=basis, affine=affine and basis == "g")
+            + EPILOGUE_FLOPS[kind] * 4 * n ** 3)
 
 
 # --- the paper's model (Sec. 4.1), for comparison --------------------------

@@ -214,3 +214,63 @@ def test_misaligned_state_rejected():
     view = buf[1:].view(cfg["U0"].shape)          # 8-byte offset
     with pytest.raises(dgw.DGError):
         s.step_lsrk(view, 0.001, 1)
+
+
+def _affine_piecewise(N, k, seed, periodic=True):
+    from oracle_helpers import SHEAR, linear_map
+    mesh = synth.cube_mesh(N, q=1, periodic=periodic, deform=linear_map(SHEAR))
+    rng = np.random.default_rng(seed)
+    E, n3 = N ** 3, (k + 1) ** 3
+    rho = rng.uniform(0.6, 1.6, size=(E, 1)) * np.ones((1, n3))   # constant per element, jumps between
+    c = rng.uniform(0.6, 1.6, size=(E, 1)) * np.ones((1, n3))
+    return {"mesh": mesh, "k": k, "rho": rho, "c": c, "alpha": 1.0,
+            "U0": synth.configs.random_state(E, k, seed + 1)}
+
+
+def test_affine_detection():
+    _cuda()
+    cfg = _affine_piecewise(2, 3, 1)
+    s, _ = pair(cfg)
+    assert s.is_affine()
+    x = synth.solution_node_positions(cfg["mesh"], 3)
+    rho, c = synth.fields.cfg2_coefficients(x)
+    s.set_coefficients(rho, c)                    # varies inside elements
+    assert not s.is_affine()
+    s.set_coefficients(cfg["rho"], cfg["c"])
+    assert s.is_affine()
+    curved = _curved(2, 3, seed=2)
+    sc, _ = pair(curved)
+    assert not sc.is_affine()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("basis", ["g", "gl"])
+def test_affine_steppers_match_oracle(k, basis):
+    """Affine elements with element-wise constant coefficients (impedance
+    jumps across faces) run the compact-data kernels: same parity."""
+    torch = _cuda()
+    cfg = _affine_piecewise(3 if k <= 4 else 2, k, seed=40 + k, periodic=(k % 2 == 0))
+    s, o = pair(cfg)
+    assert s.is_affine()
+    s.set_basis(dgw.BASIS_G if basis == "g" else dgw.BASIS_GL)
+    dt = 0.003
+    for method in ("lsrk", "ader"):
+        U = s.to_device(cfg["U0"])
+        if method == "lsrk":
+            s.step_lsrk(U, dt, 3)
+            ref = o.lsrk(cfg["U0"], dt, 3)
+        else:
+            s.step_ader(U, dt, 3, 2)
+            ref = o.ader(cfg["U0"], dt, 3, 2)
+        torch.cuda.synchronize()
+        assert rel_l2(U.cpu().numpy(), ref) < 1e-12, method
+        s32 = dgw.Solver(cfg["mesh"], k, dgw.DG_FP32, 1.0, cfg["rho"], cfg["c"])
+        s32.set_basis(s.basis())
+        V = s32.to_device(cfg["U0"])
+        if method == "lsrk":
+            s32.step_lsrk(V, dt, 3)
+        else:
+            s32.step_ader(V, dt, 3, 2)
+        torch.cuda.synchronize()
+        s32.check_device()
+        assert rel_l2(V.cpu().numpy(), ref) < 2e-5, method

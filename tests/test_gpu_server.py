@@ -45,21 +45,26 @@ def test_alone_equals_mix_equals_solver(prec):
     torch = _cuda()
     target = _req(11, 4, 3, 21)
     others = [_req(20 + i, N, k, s, m) for i, (N, k, s, m) in
-              enumerate([(3, 5, 9, 1), (5, 2, 30, 1), (2, 7, 13, 1), (4, 4, 17, 0), (3, 3, 25, 0)])]
+              enumerate([(3, 5, 3000, 1), (5, 2, 3000, 1), (2, 7, 13, 1), (4, 4, 17, 0), (3, 3, 25, 0)])]
     srv = dgw.Server(8 << 30, prec=prec, chunk_steps=5)
     alone = _wait(srv, _submit(srv, target, prec))
     assert alone["status"] == 0
-    # the mix: two solves first, the target while they run, the rest after it
+    # the mix: two long solves first; the target once they run; the rest after it
     t = [_submit(srv, o, prec) for o in others[:2]]
-    time.sleep(0.05)
+    t0 = time.time()
+    while srv.stats()["active"] < 2:
+        assert time.time() - t0 < 60
+        time.sleep(0.001)
     tt = _submit(srv, target, prec)
     t += [_submit(srv, o, prec) for o in others[2:]]
     mixed = _wait(srv, tt)
     rest = [_wait(srv, x) for x in t]
     assert all(r["status"] == 0 for r in rest)
     assert np.array_equal(alone["out"], mixed["out"])
+    # the target's solve overlapped with the long ones
+    assert mixed["t_admit"] < min(r["t_done"] for r in rest[:2])
     st = srv.stats()
-    assert st["completed"] == 1 + 1 + len(others) and st["peak_active"] >= 2
+    assert st["completed"] == 1 + 1 + len(others) and st["peak_active"] >= 3
     srv.close()
     s = dgw.Solver(target["mesh"], target["k"], prec, 1.0, target["rho"], target["c"])
     U = s.to_device(target["U0"])
