@@ -296,19 +296,21 @@ def batched_bench(args, dgw, torch):
     steps = args.steps
     t_gen = time.perf_counter() - t_gen
     out = {"workload": f"batched: {n} instances, N~U{{4..24}}^3 curved hexahedra, k~U{{2..7}}, seeded rho/c/pulses, "
-                       f"ADER order k+1", "total_dof": total, "steps": steps,
+                       f"ADER order k+1", "total_dof": total, "steps": steps, "state_basis": args.basis,
            "k_histogram": {str(k): sum(1 for c in cfgs if c["k"] == k) for k in range(2, 8)}}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
     t_setup = time.perf_counter()
     solvers = [dgw.Solver(c["mesh"], c["k"], dgw.DG_FP32, 1.0, c["rho"], c["c"]) for c in cfgs]
-    if table:
-        for s in solvers:
+    for s in solvers:
+        s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
+        if table:
             autotune.apply(s, table)
     states = [s.to_device(c["U0"]) for s, c in zip(solvers, cfgs)]
     out["setup_s"] = time.perf_counter() - t_setup
     out["host_generation_s"] = t_gen
     b = dgw.Batch(solvers, states, [c["dt"] for c in cfgs])
+    b.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL, convert_each_call=True)
     b.step_ader(8, 2)
     torch.cuda.synchronize()
     ev0.record(stream)
@@ -338,6 +340,7 @@ def batched_bench(args, dgw, torch):
     ms64 = 0.0
     for c in cfgs:
         s = dgw.Solver(c["mesh"], c["k"], dgw.DG_FP64, 1.0, c["rho"], c["c"])
+        s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
         U = s.to_device(c["U0"])
         s.step_ader(U, c["dt"], 1, 2)
         torch.cuda.synchronize()
@@ -440,6 +443,7 @@ def served_bench(args, dgw, torch):
         i = next(j for j, c in enumerate(reqs) if c["k"] == k)
         c = reqs[i]
         s = dgw.Solver(c["mesh"], k, dgw.DG_FP64, 1.0, c["rho"], c["c"])
+        s.set_basis(dgw.BASIS_G)
         U = s.to_device(c["U0"].astype(np.float64))
         s.step_ader(U, c["dt"], 1, 2)
         torch.cuda.synchronize()

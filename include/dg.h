@@ -178,6 +178,9 @@ int dg_get_basis(const dg_ctx* ctx);
  */
 int dg_is_affine(const dg_ctx* ctx);
 
+/* In-place change of basis of a device state: GL -> G (to_g != 0) or G -> GL. */
+int dg_change_basis(dg_ctx* ctx, void* U, int to_g, uintptr_t stream);
+
 /*
  * The predictor alone: Ubar (device, GL basis) = sum_j dt^{j+1}/(j+1)! T_j of
  * Eq. (6) for the state U. U and Ubar must not overlap.
@@ -290,6 +293,16 @@ int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double* dt, int32
                     uintptr_t stream, dg_batch** out);
 int dg_batch_step_ader(dg_batch* b, int32_t nsteps, int32_t reduce_every, uintptr_t stream);
 int dg_batch_step_lsrk(dg_batch* b, int32_t nsteps, uintptr_t stream);
+/*
+ * State basis of a batch's steps (DG_BASIS_GL default, or DG_BASIS_G as for
+ * dg_set_basis). With DG_BASIS_G and convert_each_call != 0 every step call
+ * changes the states to the Gauss basis on entry and back on exit; with 0 the
+ * states stay in whatever basis the caller keeps them in, and the caller
+ * changes basis with dg_batch_convert or dg_change_basis (a solve's result
+ * then does not depend on how its steps are split into calls).
+ */
+int dg_batch_set_basis(dg_batch* b, int basis, int convert_each_call);
+int dg_batch_convert(dg_batch* b, int to_g, uintptr_t stream);
 int dg_batch_info(const dg_batch* b, int32_t* n_inst, int32_t* n_items, int32_t* block,
                   int32_t* grid, uint64_t* launches);
 const char* dg_batch_last_error(const dg_batch* b);

@@ -17,7 +17,7 @@ EXPORTED_SYMBOLS = [
     "dg_batch_step_lsrk", "dg_batch_info", "dg_batch_last_error", "dg_batch_destroy",
     "dg_server_create", "dg_submit", "dg_poll", "dg_server_stats", "dg_server_destroy",
     "dg_request_bytes", "dg_mesh_setup_coef", "dg_set_basis", "dg_get_basis", "dg_check_device",
-    "dg_is_affine",
+    "dg_is_affine", "dg_change_basis", "dg_batch_set_basis", "dg_batch_convert",
 ]
 BASIS_GL, BASIS_G = 0, 1
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
@@ -119,6 +119,9 @@ def load_library():
         "dg_set_basis": (C.c_int, [vp, C.c_int]),
         "dg_check_device": (C.c_int, [vp, st]),
         "dg_is_affine": (C.c_int, [vp]),
+        "dg_change_basis": (C.c_int, [vp, vp, C.c_int, st]),
+        "dg_batch_set_basis": (C.c_int, [vp, C.c_int, C.c_int]),
+        "dg_batch_convert": (C.c_int, [vp, C.c_int, st]),
         "dg_get_basis": (C.c_int, [vp]),
         "dg_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
         "dg_last_error": (C.c_char_p, [vp]),
@@ -277,6 +280,10 @@ class Solver:
         """Raise DGError(DG_ETIMEOUT) if a bounded device wait gave up."""
         self._check(self.lib.dg_check_device(self.ctx, _stream(stream)))
 
+    def change_basis(self, U, to_g, stream=None):
+        self._check(self.lib.dg_change_basis(self.ctx, self._state(U), int(bool(to_g)), _stream(stream)))
+        return U
+
     def is_affine(self):
         return bool(self.lib.dg_is_affine(self.ctx))
 
@@ -332,6 +339,12 @@ class Batch:
     def _check(self, rc):
         if rc != 0:
             raise DGError(rc, self.lib.dg_batch_last_error(self.b).decode())
+
+    def set_basis(self, basis, convert_each_call=True):
+        self._check(self.lib.dg_batch_set_basis(self.b, int(basis), int(bool(convert_each_call))))
+
+    def convert(self, to_g, stream=None):
+        self._check(self.lib.dg_batch_convert(self.b, int(bool(to_g)), _stream(stream)))
 
     def step_ader(self, nsteps, reduce_every=2, stream=None):
         self._check(self.lib.dg_batch_step_ader(self.b, int(nsteps), int(reduce_every), _stream(stream)))

@@ -813,6 +813,14 @@ int dg_get_basis(const dg_ctx* ctx) { return ctx ? ctx->basis : DG_EINVAL; }
 
 int dg_is_affine(const dg_ctx* ctx) { return ctx ? (ctx->affine ? 1 : 0) : DG_EINVAL; }
 
+int dg_change_basis(dg_ctx* ctx, void* U, int to_g, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  int rc;
+  if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
+  DeviceGuard g(ctx->dev);
+  return change_basis(ctx, U, to_g ? 1 : 0, S(stream));
+}
+
 int dg_check_device(dg_ctx* ctx, uintptr_t stream) {
   if (!ctx) return DG_EINVAL;
   DeviceGuard g(ctx->dev);
@@ -1054,6 +1062,7 @@ extern "C" int dg_tune(dg_ctx* ctx, int kind, const int32_t* cand, int32_t ncand
 // Solves of one degree in a batch: their work items and launch shape.
 struct BatchGroup {
   int n = 0;
+  int aff = 0;  // affine elements with constant coefficients (compact kernels in the Gauss basis)
   BatchItem* items_op = nullptr;
   BatchItem* items_tck = nullptr;
   int n_op = 0, n_tck = 0;
@@ -1069,7 +1078,10 @@ struct dg_batch {
   std::vector<BatchGroup> groups;
   std::vector<void*> allocs;
   BatchInst* inst = nullptr;
-  int* counters = nullptr;  // kCounters per group
+  std::vector<BatchInst> hinst;  // host copy (re-uploaded when the basis changes)
+  int* counters = nullptr;  // kCounters + 2 per group
+  int basis = DG_BASIS_GL;
+  bool convert_each_call = true;
   cudaEvent_t fork = nullptr;
   cudaStream_t cap = nullptr;  // private stream used for graph capture
   cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};  // ADER red 0, ADER red 2, LSRK
@@ -1078,6 +1090,7 @@ struct dg_batch {
   std::string err;
   static constexpr int kChunk = 8;  // steps per captured graph
   static constexpr int kCounters = 5 * kChunk;
+  static constexpr int kSlots = kCounters + 2;  // + the two changes of basis
 
   int fail(int code, const char* msg) {
     err = msg;
@@ -1116,7 +1129,7 @@ int batch_alloc(dg_batch* b, void** p, size_t bytes) {
 // its phases on its own stream, and `st` waits for all of them.
 int batch_launch_steps(dg_batch* b, int method, int red, int steps, cudaStream_t st) {
   const int ng = (int)b->groups.size();
-  cudaError_t e = cudaMemsetAsync(b->counters, 0, sizeof(int) * dg_batch::kCounters * ng, st);
+  cudaError_t e = cudaMemsetAsync(b->counters, 0, sizeof(int) * dg_batch::kSlots * ng, st);
   if (e == cudaSuccess) e = cudaEventRecord(b->fork, st);
   if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
   const int ti = red == 2 ? 1 : 2;
@@ -1124,21 +1137,44 @@ int batch_launch_steps(dg_batch* b, int method, int red, int steps, cudaStream_t
   auto tck = b->prec == DG_FP64 ? launch_batch_tck_f64 : launch_batch_tck_f32;
   for (int gi = 0; gi < ng && e == cudaSuccess; ++gi) {
     BatchGroup& g = b->groups[gi];
-    int* cnt = b->counters + gi * dg_batch::kCounters;
+    int* cnt = b->counters + gi * dg_batch::kSlots;
+    const int mode = b->basis == DG_BASIS_G ? (g.aff ? 2 : 1) : 0;
     e = cudaStreamWaitEvent(g.s, b->fork, 0);
     for (int s = 0; s < steps && e == cudaSuccess; ++s) {
       if (method == 1) {  // ADER: predictor, then update
         e = tck(g.n, g.items_tck, g.n_tck, b->inst, red, cnt++, g.grid_tck[ti], g.block_tck, g.smem_tck[ti], g.s);
         if (e == cudaSuccess)
-          e = op(g.n, g.items_op, g.n_op, b->inst, 5, cnt++, g.grid_op, g.block_op, g.smem_op, g.s);
+          e = op(g.n, g.items_op, g.n_op, b->inst, 5, cnt++, g.grid_op, g.block_op, g.smem_op, g.s, mode);
         b->launches += 2;
       } else {
         for (int ph = 0; ph < 5 && e == cudaSuccess; ++ph) {
-          e = op(g.n, g.items_op, g.n_op, b->inst, ph, cnt++, g.grid_op, g.block_op, g.smem_op, g.s);
+          e = op(g.n, g.items_op, g.n_op, b->inst, ph, cnt++, g.grid_op, g.block_op, g.smem_op, g.s, mode);
           b->launches += 1;
         }
       }
     }
+    if (e == cudaSuccess) e = cudaEventRecord(g.done, g.s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g.done, 0);
+  }
+  if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
+  return DG_OK;
+}
+
+// In-place change of basis of every solve's state (GL -> G if to_g).
+int batch_convert(dg_batch* b, int to_g, cudaStream_t st) {
+  const int ng = (int)b->groups.size();
+  auto conv = b->prec == DG_FP64 ? launch_batch_basis_f64 : launch_batch_basis_f32;
+  cudaError_t e = cudaSuccess;
+  for (int gi = 0; gi < ng && e == cudaSuccess; ++gi)
+    e = cudaMemsetAsync(b->counters + gi * dg_batch::kSlots + dg_batch::kCounters + to_g, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaEventRecord(b->fork, st);
+  for (int gi = 0; gi < ng && e == cudaSuccess; ++gi) {
+    BatchGroup& g = b->groups[gi];
+    e = cudaStreamWaitEvent(g.s, b->fork, 0);
+    if (e == cudaSuccess)
+      e = conv(g.n, g.items_op, g.n_op, b->inst, to_g, b->counters + gi * dg_batch::kSlots + dg_batch::kCounters + to_g,
+               g.grid_op, g.block_op, g.smem_op, g.s);
+    b->launches += 1;
     if (e == cudaSuccess) e = cudaEventRecord(g.done, g.s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g.done, 0);
   }
@@ -1184,9 +1220,10 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     return code;
   };
   std::vector<BatchInst> hinst(n);
-  std::vector<std::vector<BatchItem>> hop(DG_NMAX + 1), htck(DG_NMAX + 1);
+  // groups: index 2 n + aff
+  std::vector<std::vector<BatchItem>> hop(2 * (DG_NMAX + 1)), htck(2 * (DG_NMAX + 1));
   auto maxthr = prec == DG_FP64 ? batch_max_threads_f64 : batch_max_threads_f32;
-  std::vector<BatchGroup> byn(DG_NMAX + 1);
+  std::vector<BatchGroup> byn(2 * (DG_NMAX + 1));
   for (int i = 0; i < n; ++i) {
     dg_ctx* c = ctxs[i];
     int rc;
@@ -1218,19 +1255,22 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     I.tck.geoT = c->geoT;
     I.tck.geoT_stride = c->tstride;
     I.tck.E = c->E;
+    I.tck.aff = c->affine ? 1 : 0;
+    I.tck.geoKT = c->geoKT;
     double fact = 1.0;
     for (int j = 0; j <= c->n; ++j) {
       fact *= (j + 1);
       I.tck.coef[j] = std::pow(dt[i], j + 1) / fact;
     }
-    const int nn = c->n, n2 = nn * nn;
+    const int nn = c->n, n2 = nn * nn, gk = 2 * nn + (c->affine ? 1 : 0);
     const int eo = std::max(1, std::min(c->epb_op, maxthr(nn, 0) / n2));
     const int et = std::max(1, std::min(c->epb_tck, maxthr(nn, 1) / n2));
-    // items are cut below, once each degree's launch shape is known
-    hop[nn].push_back({i, 0, c->E, nn, eo});
-    htck[nn].push_back({i, 0, c->E, nn, et});
-    BatchGroup& g = byn[nn];
+    // items are cut below, once each group's launch shape is known
+    hop[gk].push_back({i, 0, c->E, nn, eo});
+    htck[gk].push_back({i, 0, c->E, nn, et});
+    BatchGroup& g = byn[gk];
     g.n = nn;
+    g.aff = c->affine ? 1 : 0;
     g.block_op = std::max(g.block_op, eo * n2);
     g.block_tck = std::max(g.block_tck, et * n2);
     g.smem_op = std::max(g.smem_op, (size_t)eo * g_kt.smem[prec][nn](0, 2));
@@ -1254,9 +1294,10 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
   if ((rc = batch_alloc(b, (void**)&b->inst, sizeof(BatchInst) * n))) return bail(rc);
   cudaStream_t st = S(stream);
   cudaError_t e = cudaMemcpyAsync(b->inst, hinst.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, st);
-  for (int nn = 2; nn <= DG_NMAX && e == cudaSuccess; ++nn) {
-    if (hop[nn].empty()) continue;
-    BatchGroup g = byn[nn];
+  for (int gk = 4; gk < 2 * (DG_NMAX + 1) && e == cudaSuccess; ++gk) {
+    if (hop[gk].empty()) continue;
+    const int nn = gk / 2;
+    BatchGroup g = byn[gk];
     g.grid_op = sms * std::max(1, occ(nn, 0, g.block_op, g.smem_op));
     g.grid_tck[1] = sms * std::max(1, occ(nn, 1, g.block_tck, g.smem_tck[1]));
     g.grid_tck[2] = sms * std::max(1, occ(nn, 2, g.block_tck, g.smem_tck[2]));
@@ -1274,24 +1315,24 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
       }
       v.swap(out);
     };
-    cut(hop[nn], g.grid_op);
-    cut(htck[nn], std::max(g.grid_tck[1], g.grid_tck[2]));
-    std::sort(hop[nn].begin(), hop[nn].end(), by_size);
-    std::sort(htck[nn].begin(), htck[nn].end(), by_size);
-    g.n_op = (int)hop[nn].size();
-    g.n_tck = (int)htck[nn].size();
+    cut(hop[gk], g.grid_op);
+    cut(htck[gk], std::max(g.grid_tck[1], g.grid_tck[2]));
+    std::sort(hop[gk].begin(), hop[gk].end(), by_size);
+    std::sort(htck[gk].begin(), htck[gk].end(), by_size);
+    g.n_op = (int)hop[gk].size();
+    g.n_tck = (int)htck[gk].size();
     if ((rc = batch_alloc(b, (void**)&g.items_op, sizeof(BatchItem) * g.n_op)) ||
         (rc = batch_alloc(b, (void**)&g.items_tck, sizeof(BatchItem) * g.n_tck)))
       return bail(rc);
-    e = cudaMemcpyAsync(g.items_op, hop[nn].data(), sizeof(BatchItem) * g.n_op, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(g.items_op, hop[gk].data(), sizeof(BatchItem) * g.n_op, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(g.items_tck, htck[nn].data(), sizeof(BatchItem) * g.n_tck, cudaMemcpyHostToDevice, st);
+      e = cudaMemcpyAsync(g.items_tck, htck[gk].data(), sizeof(BatchItem) * g.n_tck, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
     b->groups.push_back(g);
   }
   if (e == cudaSuccess)
-    if ((rc = batch_alloc(b, (void**)&b->counters, sizeof(int) * dg_batch::kCounters * b->groups.size())))
+    if ((rc = batch_alloc(b, (void**)&b->counters, sizeof(int) * dg_batch::kSlots * b->groups.size())))
       return bail(rc);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -1301,6 +1342,7 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     b->fail(DG_ECUDA, cudaGetErrorString(e));
     return bail(DG_ECUDA);
   }
+  b->hinst = std::move(hinst);
   *out = b;
   return DG_OK;
 }
@@ -1311,6 +1353,11 @@ static int batch_steps(dg_batch* b, int method, int red, int32_t nsteps, uintptr
   const int gi = method == 0 ? 2 : (red == 2 ? 1 : 0);
   const int chunks = nsteps / dg_batch::kChunk, rest = nsteps % dg_batch::kChunk;
   const uint64_t per_chunk = (uint64_t)dg_batch::kChunk * (method == 0 ? 5 : 2) * b->groups.size();
+  const bool conv = b->basis == DG_BASIS_G && b->convert_each_call && nsteps > 0;
+  if (conv) {
+    const int rc = batch_convert(b, 1, st);
+    if (rc) return rc;
+  }
   if (chunks > 0 && !b->gexec[gi]) {
     // capture kChunk steps once; the graph is replayed on the caller's stream
     cudaGraph_t graph = nullptr;
@@ -1337,8 +1384,35 @@ static int batch_steps(dg_batch* b, int method, int red, int32_t nsteps, uintptr
     if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
     b->launches += per_chunk;
   }
-  if (rest) return batch_launch_steps(b, method, red, rest, st);
+  if (rest) {
+    const int rc = batch_launch_steps(b, method, red, rest, st);
+    if (rc) return rc;
+  }
+  if (conv) return batch_convert(b, 0, st);
   return DG_OK;
+}
+
+extern "C" int dg_batch_set_basis(dg_batch* b, int basis, int convert_each_call) {
+  if (!b) return DG_EINVAL;
+  if (basis != DG_BASIS_GL && basis != DG_BASIS_G) return b->fail(DG_EINVAL, "basis must be DG_BASIS_GL or DG_BASIS_G");
+  DeviceGuard g(b->dev);
+  b->basis = basis;
+  b->convert_each_call = convert_each_call != 0;
+  for (auto& I : b->hinst) I.tck.gmode = basis == DG_BASIS_G ? 1 : 0;
+  cudaError_t e = cudaMemcpy(b->inst, b->hinst.data(), sizeof(BatchInst) * b->hinst.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return b->fail(DG_ECUDA, cudaGetErrorString(e));
+  for (auto& x : b->gexec)  // captured graphs refer to the old kernels
+    if (x) {
+      cudaGraphExecDestroy(x);
+      x = nullptr;
+    }
+  return DG_OK;
+}
+
+extern "C" int dg_batch_convert(dg_batch* b, int to_g, uintptr_t stream) {
+  if (!b) return DG_EINVAL;
+  DeviceGuard g(b->dev);
+  return batch_convert(b, to_g ? 1 : 0, S(stream));
 }
 
 extern "C" int dg_batch_step_ader(dg_batch* b, int32_t nsteps, int32_t red, uintptr_t stream) {

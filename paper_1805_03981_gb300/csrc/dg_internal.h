@@ -70,9 +70,13 @@ struct BatchItem;
 struct BatchInst;
 // Batched persistent kernels, one launch per degree n (all items of degree n).
 cudaError_t launch_batch_op_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int phase,
-                                int* counter, int grid, int block, size_t smem, cudaStream_t st);
+                                int* counter, int grid, int block, size_t smem, cudaStream_t st, int mode);
 cudaError_t launch_batch_op_f32(int n, const BatchItem* items, int nitems, const BatchInst* inst, int phase,
-                                int* counter, int grid, int block, size_t smem, cudaStream_t st);
+                                int* counter, int grid, int block, size_t smem, cudaStream_t st, int mode);
+cudaError_t launch_batch_basis_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int to_g,
+                                   int* counter, int grid, int block, size_t smem, cudaStream_t st);
+cudaError_t launch_batch_basis_f32(int n, const BatchItem* items, int nitems, const BatchInst* inst, int to_g,
+                                   int* counter, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_batch_tck_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
                                  int* counter, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_batch_tck_f32(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,

@@ -1452,7 +1452,9 @@ struct BatchInst {
 // One launch per degree present in the batch: every item has n == N, so the
 // block shape and register use are those of that degree alone; launches of
 // different degrees run concurrently (they belong to different solves).
-template <int N, typename Real, int EPI>
+// MODE: 0 GL states (op_block), 1 Gauss-basis states (opgs/opg_block),
+// 2 Gauss-basis states on affine elements (opga_block).
+template <int N, typename Real, int EPI, int MODE>
 __global__ void batch_op_kernel(const BatchItem* __restrict__ items, int nitems,
                                 const BatchInst* __restrict__ inst, int phase, int* counter) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1468,8 +1470,60 @@ __global__ void batch_op_kernel(const BatchItem* __restrict__ items, int nitems,
     const OpParams& p = inst[w.inst].op[phase];
     // the item's elements in slices of epb (one block's worth)
     for (int e0 = w.e0; e0 < w.e0 + w.ne; e0 += w.epb) {
-      op_block<N, Real, EPI>(p, e0, min(w.epb, w.e0 + w.ne - e0), sm);
+      const int ne = min(w.epb, w.e0 + w.ne - e0);
+      if constexpr (MODE == 0)
+        op_block<N, Real, EPI>(p, e0, ne, sm);
+      else if constexpr (MODE == 2)
+        opga_block<N, Real, EPI, sizeof(Real) == 4>(p, e0, ne, w.epb, sm);
+      else if constexpr (sizeof(Real) == 4)
+        opgs_block<N, Real, EPI>(p, e0, ne, w.epb, sm);
+      else
+        opg_block<N, Real, EPI>(p, e0, ne, sm);
       __syncthreads();  // shared memory is reused by the next slice
+    }
+  }
+}
+
+// In-place change of basis of the states of a batch's solves of degree N
+// (GL -> G if to_g, else G -> GL), over the same work items.
+template <int N, typename Real>
+__global__ void batch_basis_kernel(const BatchItem* __restrict__ items, int nitems,
+                                   const BatchInst* __restrict__ inst, int to_g, int* counter) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real* sm = reinterpret_cast<Real*>(smem_raw);
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const BatchItem w = items[it];
+    Real* U = static_cast<Real*>(const_cast<void*>(inst[w.inst].tck.U));
+    for (int e0 = w.e0; e0 < w.e0 + w.ne; e0 += w.epb) {
+      const int ne = min(w.epb, w.e0 + w.ne - e0);
+      const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
+      const bool act = le < ne;
+      Real* su = sm + le * 4 * N3;
+      for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) sm[i] = U[(size_t)e0 * 4 * N3 + i];
+      __syncthreads();
+      if (to_g) {
+        if (act) contract_tile<Real, 2, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+        __syncthreads();
+        if (act) contract_tile<Real, 0, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+        __syncthreads();
+        if (act) contract_tile<Real, 1, N, N, N, N, OFF_V(N), N3, N3>(su, su, t, N2);
+      } else {
+        if (act) contract_tile<Real, 2, N, N, N, N, OFF_VI(N), N3, N3>(su, su, t, N2);
+        __syncthreads();
+        if (act) contract_tile<Real, 0, N, N, N, N, OFF_VI(N), N3, N3>(su, su, t, N2);
+        __syncthreads();
+        if (act) contract_tile<Real, 1, N, N, N, N, OFF_VI(N), N3, N3>(su, su, t, N2);
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) U[(size_t)e0 * 4 * N3 + i] = sm[i];
+      __syncthreads();
     }
   }
 }

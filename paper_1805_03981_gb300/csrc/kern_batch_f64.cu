@@ -4,13 +4,26 @@
 namespace dg {
 namespace {
 
+template <int N, int MODE>
+cudaError_t op_nm(const BatchItem* items, int nitems, const BatchInst* inst, int phase, int* counter,
+                  int grid, int block, size_t smem, cudaStream_t st) {
+  if (phase < 5)
+    batch_op_kernel<N, double, EPI_LSRK, MODE><<<grid, block, smem, st>>>(items, nitems, inst, phase, counter);
+  else
+    batch_op_kernel<N, double, EPI_ADD, MODE><<<grid, block, smem, st>>>(items, nitems, inst, phase, counter);
+  return cudaGetLastError();
+}
 template <int N>
 cudaError_t op_n(const BatchItem* items, int nitems, const BatchInst* inst, int phase, int* counter,
-                 int grid, int block, size_t smem, cudaStream_t st) {
-  if (phase < 5)
-    batch_op_kernel<N, double, EPI_LSRK><<<grid, block, smem, st>>>(items, nitems, inst, phase, counter);
-  else
-    batch_op_kernel<N, double, EPI_ADD><<<grid, block, smem, st>>>(items, nitems, inst, phase, counter);
+                 int grid, int block, size_t smem, cudaStream_t st, int mode) {
+  if (mode == 1) return op_nm<N, 1>(items, nitems, inst, phase, counter, grid, block, smem, st);
+  if (mode == 2) return op_nm<N, 2>(items, nitems, inst, phase, counter, grid, block, smem, st);
+  return op_nm<N, 0>(items, nitems, inst, phase, counter, grid, block, smem, st);
+}
+template <int N>
+cudaError_t basis_n(const BatchItem* items, int nitems, const BatchInst* inst, int to_g, int* counter,
+                    int grid, int block, size_t smem, cudaStream_t st) {
+  batch_basis_kernel<N, double><<<grid, block, smem, st>>>(items, nitems, inst, to_g, counter);
   return cudaGetLastError();
 }
 template <int N>
@@ -26,7 +39,7 @@ template <int N>
 int occ_n(int which, int block, size_t smem) {
   int nb = 0;
   if (which == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_op_kernel<N, double, EPI_LSRK>, block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_op_kernel<N, double, EPI_LSRK, 1>, block, smem);
   else if (which == 1)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tck_kernel<N, double, 2>, block, smem);
   else
@@ -37,15 +50,23 @@ int occ_n(int which, int block, size_t smem) {
 template <int N>
 int maxthr_n(int which) {
   if (which == 0)
-    return min(kernel_max_threads(batch_op_kernel<N, double, EPI_LSRK>),
-               kernel_max_threads(batch_op_kernel<N, double, EPI_ADD>));
+    return min(min(min(kernel_max_threads(batch_op_kernel<N, double, EPI_LSRK, 0>),
+                       kernel_max_threads(batch_op_kernel<N, double, EPI_ADD, 0>)),
+                   min(kernel_max_threads(batch_op_kernel<N, double, EPI_LSRK, 1>),
+                       kernel_max_threads(batch_op_kernel<N, double, EPI_ADD, 1>))),
+               min(min(kernel_max_threads(batch_op_kernel<N, double, EPI_LSRK, 2>),
+                       kernel_max_threads(batch_op_kernel<N, double, EPI_ADD, 2>)),
+                   kernel_max_threads(batch_basis_kernel<N, double>)));
   return min(kernel_max_threads(batch_tck_kernel<N, double, 2>), kernel_max_threads(batch_tck_kernel<N, double, 0>));
 }
 template <int N>
 cudaError_t allow_n() {
   cudaError_t e;
-  if ((e = allow_smem(batch_op_kernel<N, double, EPI_LSRK>)) != cudaSuccess) return e;
-  if ((e = allow_smem(batch_op_kernel<N, double, EPI_ADD>)) != cudaSuccess) return e;
+  for (cudaError_t r : {allow_smem(batch_op_kernel<N, double, EPI_LSRK, 0>), allow_smem(batch_op_kernel<N, double, EPI_ADD, 0>),
+                        allow_smem(batch_op_kernel<N, double, EPI_LSRK, 1>), allow_smem(batch_op_kernel<N, double, EPI_ADD, 1>),
+                        allow_smem(batch_op_kernel<N, double, EPI_LSRK, 2>), allow_smem(batch_op_kernel<N, double, EPI_ADD, 2>)})
+    if (r != cudaSuccess) return r;
+  if ((e = allow_smem(batch_basis_kernel<N, double>)) != cudaSuccess) return e;
   if ((e = allow_smem(batch_tck_kernel<N, double, 2>)) != cudaSuccess) return e;
   return allow_smem(batch_tck_kernel<N, double, 0>);
 }
@@ -65,8 +86,8 @@ cudaError_t allow_n() {
   }
 
 cudaError_t launch_batch_op_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int phase,
-                                    int* counter, int grid, int block, size_t smem, cudaStream_t st) {
-#define C_(N) op_n<N>(items, nitems, inst, phase, counter, grid, block, smem, st)
+                                    int* counter, int grid, int block, size_t smem, cudaStream_t st, int mode) {
+#define C_(N) op_n<N>(items, nitems, inst, phase, counter, grid, block, smem, st, mode)
   DG_SWITCH_N(n, C_)
 #undef C_
   return cudaErrorInvalidValue;
@@ -74,6 +95,14 @@ cudaError_t launch_batch_op_f64(int n, const BatchItem* items, int nitems, const
 cudaError_t launch_batch_tck_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
                                      int* counter, int grid, int block, size_t smem, cudaStream_t st) {
 #define C_(N) tck_n<N>(items, nitems, inst, red, counter, grid, block, smem, st)
+  DG_SWITCH_N(n, C_)
+#undef C_
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_batch_basis_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst,
+                                       int to_g, int* counter, int grid, int block, size_t smem,
+                                       cudaStream_t st) {
+#define C_(N) basis_n<N>(items, nitems, inst, to_g, counter, grid, block, smem, st)
   DG_SWITCH_N(n, C_)
 #undef C_
   return cudaErrorInvalidValue;

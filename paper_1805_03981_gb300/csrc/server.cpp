@@ -1,5 +1,8 @@
 // Served form: continuous batching of wave solves on one GPU.
 //
+// States are held at the Gauss points while admitted (DG_BASIS_G batches;
+// one change of basis on admission and one on completion).
+//
 // Two threads.  The admission thread takes queued requests in arrival order
 // while they fit the HBM budget (a request that does not fit lets later,
 // smaller ones in: first-fit backfill) and the active-DoF cap, and sets each
@@ -136,6 +139,12 @@ int admit(dg_server* s, const std::shared_ptr<Req>& r, cudaStream_t st) {
     r->err = "upload of the initial state failed";
     return DG_ECUDA;
   }
+  // the state stays at the Gauss points while admitted (one change of basis
+  // on admission, one on completion, however the steps are split in rounds)
+  if ((rc = dg_change_basis(r->ctx, r->U, 1, (uintptr_t)st))) {
+    r->err = dg_last_error(r->ctx);
+    return rc;
+  }
   // the inputs are on the device now
   std::vector<double>().swap(r->nodes);
   std::vector<double>().swap(r->rho);
@@ -184,7 +193,11 @@ void dg_server::admit_loop() {
     std::lock_guard<std::mutex> lk(mu);
     r->t_admit = now_s();
     if (rc || r->nsteps == 0) {
-      if (!rc) cudaMemcpy(r->U_out, r->U, r->state_bytes, cudaMemcpyDeviceToHost);
+      if (!rc) {
+        dg_change_basis(r->ctx, r->U, 0, (uintptr_t)st);
+        cudaStreamSynchronize(st);
+        cudaMemcpy(r->U_out, r->U, r->state_bytes, cudaMemcpyDeviceToHost);
+      }
       release(this, r);
       used -= r->est_bytes;
       admitted_dof -= dof_of(*r);
@@ -250,7 +263,8 @@ void dg_server::run() {
           dts.push_back(r->dt);
         }
         if (dg_batch_create(ctxs.data(), us.data(), dts.data(), (int32_t)ctxs.size(), (uintptr_t)st,
-                            &g.batch) != DG_OK) {
+                            &g.batch) != DG_OK ||
+            dg_batch_set_basis(g.batch, DG_BASIS_G, 0) != DG_OK) {
           std::lock_guard<std::mutex> lk(mu);  // fail the group's solves
           for (auto& r : g.members) {
             r->status = DG_ECUDA;
@@ -295,7 +309,8 @@ void dg_server::run() {
     if (finished.empty()) continue;
     for (auto& r : finished)
       if (r->status == DG_EAGAIN &&
-          cudaMemcpyAsync(r->U_out, r->U, r->state_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+          (dg_change_basis(r->ctx, r->U, 0, (uintptr_t)st) != DG_OK ||
+           cudaMemcpyAsync(r->U_out, r->U, r->state_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)) {
         cudaGetLastError();
         r->status = DG_ECUDA;
       }

@@ -81,3 +81,38 @@ def test_tune_sets_a_valid_tiling():
     assert ms[-1] == -1.0                          # 40 x 25 threads > 1024: impossible
     assert all(m > 0 for m in ms[:-1])
     assert s.tiling()[0] == [1, 2, 3, 5][int(np.argmin(ms[:-1]))]
+
+
+@pytest.mark.parametrize("prec", [dgw.DG_FP64, dgw.DG_FP32])
+@pytest.mark.parametrize("method", ["ader", "lsrk"])
+def test_batch_gauss_basis_bitwise_equals_alone(prec, method):
+    """Gauss-basis batches (general and affine solves mixed) give each solve
+    exactly the state of its own Gauss-basis stepping."""
+    torch = _cuda()
+    cfgs, solvers = _mix(7, 6, prec)
+    for k in (3, 5):                                    # affine, constant coefficients
+        c = synth.configs.standing_wave(N=3, k=k)
+        cfgs.append(c)
+        solvers.append(dgw.Solver(c["mesh"], k, prec, 1.0, c["rho"], c["c"]))
+    assert solvers[-1].is_affine() and not solvers[0].is_affine()
+    steps = 11
+    alone = []
+    for c, s in zip(cfgs, solvers):
+        s.set_basis(dgw.BASIS_G)
+        U = s.to_device(c["U0"])
+        if method == "ader":
+            s.step_ader(U, c["dt"], steps, 2)
+        else:
+            s.step_lsrk(U, c["dt"], steps)
+        alone.append(U)
+    states = [s.to_device(c["U0"]) for c, s in zip(cfgs, solvers)]
+    b = dgw.Batch(solvers, states, [c["dt"] for c in cfgs])
+    b.set_basis(dgw.BASIS_G, convert_each_call=True)
+    if method == "ader":
+        b.step_ader(steps, 2)
+    else:
+        b.step_lsrk(steps)
+    torch.cuda.synchronize()
+    for i, (u, v) in enumerate(zip(states, alone)):
+        assert torch.equal(u, v), (i, (u - v).abs().max().item())
+    b.close()

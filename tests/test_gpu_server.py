@@ -67,6 +67,7 @@ def test_alone_equals_mix_equals_solver(prec):
     assert st["completed"] == 1 + 1 + len(others) and st["peak_active"] >= 3
     srv.close()
     s = dgw.Solver(target["mesh"], target["k"], prec, 1.0, target["rho"], target["c"])
+    s.set_basis(dgw.BASIS_G)            # the server keeps admitted states at the Gauss points
     U = s.to_device(target["U0"])
     s.step_ader(U, target["dt"], target["nsteps"], 2)
     torch.cuda.synchronize()
