@@ -474,7 +474,7 @@ def main():
     import torch
     import torch.distributed as dist
     import paper_1805_03981_gb300 as dgw
-    from paper_1805_03981_gb300 import opcount
+    from paper_1805_03981_gb300 import opcount, traffic
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -574,7 +574,12 @@ def main():
                     "unit": "GB/s", "peak_source": "measured" if hbm else "fallback"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
-    roof["traffic"] = None
+    # DRAM bytes per launch from the ncu table, when it was taken on these
+    # sources and this launch configuration (else null)
+    roof["traffic"] = traffic.lookup(args.workload, args.prec, N, k, args.basis, tiling, dom)
+    roof["traffic_source"] = ("profiles/dram_traffic.txt (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+                              if roof["traffic"] is not None else
+                              "none recorded for these sources and this launch configuration")
     roof["per_launch_ms"] = avg_s * 1e3
     roof["algorithmic_flops_per_launch"] = flops
     roof["algorithmic_bytes_per_launch"] = byts
