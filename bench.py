@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--basis", default="g", choices=["g", "gl"],
                     help="state inside the steppers: g = Gauss-point values (default), gl = the paper's storage")
     ap.add_argument("--workload", default="curved_pulse",
-                    choices=["curved_pulse", "plane_wave", "batched", "served"])
+                    choices=["curved_pulse", "plane_wave", "batched", "served", "reduction"])
     ap.add_argument("--lam", type=float, default=20.0, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="served: arrival window, seconds")
     ap.add_argument("--nrange", default="8,24", help="served: elements per axis, min,max")
@@ -277,6 +277,47 @@ def generate_instances(seeds, workers=None):
     workers = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_gen_one, seeds, chunksize=4))
+
+
+def reduction_bench(args, dgw, torch):
+    """Degree reduction in the predictor every 0, 1, 2 or 3 derivatives
+    (Sec. 3.3, Fig. reduc-comp) for k = 1..7 on the curved-pulse recipe at
+    about 28M DoF per k: the op-count model of the predictor relative to no
+    reduction, next to its measured device time per launch relative to no
+    reduction (ADER steps in the chosen storage basis and precision)."""
+    from paper_1805_03981_gb300 import opcount
+    prec = dgw.DG_FP64 if args.prec == "fp64" else dgw.DG_FP32
+    rows = []
+    for k in range(1, 8):
+        n = k + 1
+        N = max(4, round((28.3e6 / (4 * n ** 3)) ** (1.0 / 3.0)))
+        cfg = workload(N, k)
+        s = dgw.Solver(cfg["mesh"], k, prec, cfg["alpha"], cfg["rho"], cfg["c"])
+        s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
+        base = None
+        for red in (0, 1, 2, 3):
+            U = s.to_device(cfg["U0"])
+            s.step_ader(U, cfg["dt"], args.warmup, red)
+            torch.cuda.synchronize()
+            s.profile(True)
+            s.profile_read(reset=True)
+            s.step_ader(U, cfg["dt"], args.steps, red)
+            torch.cuda.synchronize()
+            ms, nl = s.profile_read(reset=True)["tck"]
+            s.profile(False)
+            per = ms / max(nl, 1)
+            flops = opcount.tck_flops(n, red, args.basis, s.is_affine()) * N ** 3
+            if red == 0:
+                base = (per, flops)
+            rows.append({"k": k, "N": N, "reduce_every": red, "tck_ms_per_launch": per,
+                         "time_rel_to_none": per / base[0], "model_flops_rel_to_none": flops / base[1],
+                         "tflops": flops / (per * 1e-3) / 1e12})
+        s.close()
+    out = {"reduction": {"workload": "curved_pulse recipe at ~28M DoF per k, ADER predictor, reduce_every 0/1/2/3, "
+                                     + args.prec.upper() + ", state basis " + args.basis,
+                         "steps": args.steps, "rows": rows}}
+    print(json.dumps(out))
+    return 0
 
 
 def batched_bench(args, dgw, torch):
@@ -496,6 +537,8 @@ def main():
         return batched_bench(args, dgw, torch)
     if args.workload == "served":
         return served_bench(args, dgw, torch)
+    if args.workload == "reduction":
+        return reduction_bench(args, dgw, torch)
     N, k = args.size, args.k
     cfg = workload(N, k, args.workload)
     if args.accuracy:

@@ -141,9 +141,14 @@ int dg_step_lsrk(dg_ctx* ctx, void* U, double dt, int32_t nsteps, uintptr_t stre
  * nsteps of ADER (Sec. 2.3, Eq. (6)): Ubar = Taylor-Cauchy-Kowalevski
  * predictor with the element-local basis change GL -> G (Sec. 3.2,
  * Algorithm 2) and degree reduction every reduce_every-th derivative
- * (Sec. 3.3, Algorithm 3; 2 = the paper's choice, 0 = none), then
- * U <- U - M^-1 K Ubar. Sum over j = 0..k+1. reduce_every must be 0 or 2;
- * other values return DG_EUNSUPPORTED.
+ * (Sec. 3.3, Algorithm 3; 2 = the paper's choice, 0 = none, 1 and 3 = the
+ * other variants of Fig. reduc-comp), then U <- U - M^-1 K Ubar. Sum over
+ * j = 0..k+1. Other values of reduce_every return DG_EUNSUPPORTED.
+ * Reductions by 1 or 3 visit Gauss sets that the set-up does not store by
+ * default (it stores n, n-2, ...): on a mesh that is curved or has
+ * variable coefficients, the first such call synchronises the stream,
+ * allocates the predictor data of every set n, n-1, ..., 2 and recomputes
+ * the geometry (an extra 11 sum_m m^3 values per element at most).
  */
 int dg_step_ader(dg_ctx* ctx, void* U, double dt, int32_t nsteps,
                  int32_t reduce_every, uintptr_t stream);
@@ -183,7 +188,8 @@ int dg_change_basis(dg_ctx* ctx, void* U, int to_g, uintptr_t stream);
 
 /*
  * The predictor alone: Ubar (device, GL basis) = sum_j dt^{j+1}/(j+1)! T_j of
- * Eq. (6) for the state U. U and Ubar must not overlap.
+ * Eq. (6) for the state U. U and Ubar must not overlap. reduce_every as for
+ * dg_step_ader (0, 1, 2 or 3).
  */
 int dg_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int32_t reduce_every,
            uintptr_t stream);
@@ -291,6 +297,7 @@ int dg_tune(dg_ctx* ctx, int kind, const int32_t* cand, int32_t ncand, int32_t r
 typedef struct dg_batch dg_batch;
 int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double* dt, int32_t n,
                     uintptr_t stream, dg_batch** out);
+/* reduce_every 0 or 2 here; 1 and 3 return DG_EUNSUPPORTED (use dg_step_ader per solve). */
 int dg_batch_step_ader(dg_batch* b, int32_t nsteps, int32_t reduce_every, uintptr_t stream);
 int dg_batch_step_lsrk(dg_batch* b, int32_t nsteps, uintptr_t stream);
 /*
@@ -342,7 +349,7 @@ typedef struct {
   double dt;
   int32_t nsteps;
   int32_t method;      /* 0 = LSRK(5,4), 1 = ADER */
-  int32_t reduce_every;
+  int32_t reduce_every; /* 0 or 2 (the server steps requests in batches) */
 } dg_request;
 typedef struct {
   double t_submit, t_admit, t_done; /* seconds, one monotonic clock */

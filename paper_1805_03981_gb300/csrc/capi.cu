@@ -49,6 +49,8 @@ int init_device(int dev, std::string* err) {
     register_f64_hi(&g_kt);
     register_f32_lo(&g_kt);
     register_f32_hi(&g_kt);
+    register_tck_odd_f64(&g_kt);
+    register_tck_odd_f32(&g_kt);
     g_kt_ready = true;
   }
   if (dev < 0 || dev >= 64) {
@@ -56,9 +58,10 @@ int init_device(int dev, std::string* err) {
     return DG_EINVAL;
   }
   if (!(g_dev_ready >> dev & 1ull)) {
-    int (*up[6])(const double*, const float*) = {upload_f64_lo, upload_f64_hi, upload_f32_lo,
-                                                  upload_f32_hi, upload_batch_f64, upload_batch_f32};
-    for (int i = 0; i < 6; ++i) {
+    int (*up[8])(const double*, const float*) = {upload_f64_lo,     upload_f64_hi,    upload_f32_lo,
+                                                  upload_f32_hi,     upload_batch_f64, upload_batch_f32,
+                                                  upload_tck_odd_f64, upload_tck_odd_f32};
+    for (int i = 0; i < 8; ++i) {
       const int e = up[i](g_tab.tab, g_tab_f);
       if (e) {
         cudaGetLastError();
@@ -97,6 +100,7 @@ struct dg_ctx {
   bool geo_affine = false;  // every element is an affine image of the cube
   bool affine = false;      // ... and has constant coefficients: compact kernels
   int tstride = 0;
+  int tstep = 2;  // predictor geometry at Gauss sets n, n - tstep, ... (1 once a step reduces by 1 or 3)
   void* U2 = nullptr;    // LSRK intermediate stage states
   void* U3 = nullptr;
   void* dU = nullptr;    // LSRK register
@@ -146,6 +150,15 @@ struct dg_ctx {
     dev_bytes += bytes;
     *p = static_cast<T*>(v);
     return DG_OK;
+  }
+  void release(void* p, size_t bytes) {
+    for (size_t i = 0; i < allocs.size(); ++i)
+      if (allocs[i] == p) {
+        cudaFree(p);
+        allocs.erase(allocs.begin() + i);
+        dev_bytes -= bytes;
+        return;
+      }
   }
   cudaEvent_t take_event() {
     if (!event_pool.empty()) {
@@ -337,6 +350,7 @@ int run_setup(dg_ctx* ctx, cudaStream_t st) {
   P.geoK = ctx->affine ? ctx->geoK : nullptr;
   P.geoKT = ctx->affine ? ctx->geoKT : nullptr;
   P.tstride = ctx->tstride;
+  P.tstep = ctx->tstep;
   P.prec = ctx->prec;
   P.bad = ctx->bad;
   DG_CK(cudaMemsetAsync(ctx->bad, 0, sizeof(int), st), "memset");
@@ -395,16 +409,50 @@ int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaS
   p.Ubar = Ubar;
   p.geoT = ctx->geoT;
   p.geoT_stride = ctx->tstride;
+  p.geo_step = ctx->tstep;
   p.E = ctx->E;
   double fact = 1.0;
   for (int j = 0; j <= ctx->n; ++j) {  // dt^{j+1} / (j+1)!
     fact *= (j + 1);
     p.coef[j] = std::pow(dt, j + 1) / fact;
   }
+  const bool odd = red == 1 || red == 3;
+  int epb = ctx->epb_tck;
+  if (odd) {  // more accumulator levels: fewer elements may fit a block
+    const int per = g_kt.smem[ctx->prec][ctx->n](1, red);
+    const int thr = g_kt.tck_odd_maxthr[ctx->prec][ctx->n]();
+    const int n2 = ctx->n * ctx->n;
+    while (epb > 1 && (epb * per > 200 * 1024 || epb * n2 > thr)) --epb;
+  }
   dg_ctx::Span span(ctx, DG_KIND_TCK, st);
-  DG_CK(g_kt.tck[ctx->prec][ctx->n](p, red, ctx->epb_tck, st), "predictor kernel launch");
+  DG_CK((odd ? g_kt.tck_odd : g_kt.tck)[ctx->prec][ctx->n](p, red, epb, st), "predictor kernel launch");
   span.done();
   ctx->launches++;
+  return DG_OK;
+}
+
+// Reduction every 1 or 3 derivatives visits Gauss sets that the default
+// predictor geometry (sets n, n-2, ...) lacks: on first use, rebuild it at
+// every set n, n-1, ..., 2 (curved or variable-coefficient meshes only; the
+// compact affine data serves every set).
+int ensure_levels(dg_ctx* ctx, int red, cudaStream_t st) {
+  if ((red != 1 && red != 3) || ctx->tstep == 1 || ctx->affine) return DG_OK;
+  const size_t old_bytes = (size_t)ctx->rsize * ctx->tstride * ctx->E;
+  void* fresh = nullptr;
+  const int stride1 = tck_geo_stride(ctx->n, 1);
+  int rc = ctx->alloc(&fresh, (size_t)ctx->rsize * stride1 * ctx->E, "predictor geometry (every Gauss set)");
+  if (rc) return rc;
+  DG_CK(cudaStreamSynchronize(st), "predictor geometry rebuild");
+  ctx->release(ctx->geoT, old_bytes);
+  ctx->geoT = fresh;
+  ctx->tstep = 1;
+  ctx->tstride = stride1;
+  return run_setup(ctx, st);
+}
+
+int check_red(dg_ctx* ctx, int red) {
+  if (red < 0 || red > 3)
+    return ctx->fail(DG_EUNSUPPORTED, "reduce_every must be 0, 1, 2 or 3 (got %d)", red);
   return DG_OK;
 }
 
@@ -592,7 +640,7 @@ int dg_mesh_setup_coef(const dg_mesh_desc* m, int k, int prec, double alpha, con
     delete ctx;
     return code;
   };
-  ctx->tstride = tck_geo_stride(n);
+  ctx->tstride = tck_geo_stride(n, ctx->tstep);
   const size_t rs = ctx->rsize;
   if ((rc = ctx->alloc(&ctx->nbr, sizeof(int32_t) * 6 * E, "nbr")) ||
       (rc = ctx->alloc(&ctx->nbr_face, 6 * (size_t)E, "nbr_face")) ||
@@ -706,9 +754,9 @@ int dg_step_ader(dg_ctx* ctx, void* U, double dt, int32_t nsteps, int32_t red, u
   if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0)
     return ctx->fail(DG_EINVAL, "need dt > 0 and nsteps >= 0");
-  if (red != 0 && red != 2)
-    return ctx->fail(DG_EUNSUPPORTED, "reduce_every must be 0 or 2 in this build");
+  if ((rc = check_red(ctx, red))) return rc;
   DeviceGuard g(ctx->dev);
+  if ((rc = ensure_levels(ctx, red, S(stream)))) return rc;
   return ader_steps(ctx, U, dt, nsteps, red, S(stream));
 }
 
@@ -716,10 +764,10 @@ int dg_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int32_t red, uintp
   if (!ctx) return DG_EINVAL;
   int rc;
   if ((rc = check_state_ptr(ctx, U, "U")) || (rc = check_state_ptr(ctx, Ubar, "Ubar"))) return rc;
-  if (red != 0 && red != 2)
-    return ctx->fail(DG_EUNSUPPORTED, "reduce_every must be 0 or 2 in this build");
+  if ((rc = check_red(ctx, red))) return rc;
   if (!std::isfinite(dt)) return ctx->fail(DG_EINVAL, "dt not finite");
   DeviceGuard g(ctx->dev);
+  if ((rc = ensure_levels(ctx, red, S(stream)))) return rc;
   return launch_tck(ctx, U, Ubar, dt, red, S(stream));
 }
 
@@ -786,10 +834,10 @@ int dg_solve_host(dg_ctx* ctx, int method, const void* Uh, void* Uout, double dt
   if (!Uh || !Uout) return ctx->fail(DG_EINVAL, "NULL host buffer");
   if (method != 0 && method != 1) return ctx->fail(DG_EINVAL, "method must be 0 (LSRK) or 1 (ADER)");
   if (!(dt > 0.0) || nsteps < 0) return ctx->fail(DG_EINVAL, "need dt > 0 and nsteps >= 0");
-  if (method == 1 && red != 0 && red != 2)
-    return ctx->fail(DG_EUNSUPPORTED, "reduce_every must be 0 or 2 in this build");
-  DeviceGuard g(ctx->dev);
   int rc;
+  if (method == 1 && (rc = check_red(ctx, red))) return rc;
+  DeviceGuard g(ctx->dev);
+  if (method == 1 && (rc = ensure_levels(ctx, red, S(stream)))) return rc;
   if ((rc = ensure(ctx, &ctx->Uh, "host-solve state"))) return rc;
   cudaStream_t st = S(stream);
   const size_t b = ctx->state_bytes();
@@ -1254,6 +1302,7 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     I.tck.Ubar = c->Ubar;
     I.tck.geoT = c->geoT;
     I.tck.geoT_stride = c->tstride;
+    I.tck.geo_step = c->tstep;
     I.tck.E = c->E;
     I.tck.aff = c->affine ? 1 : 0;
     I.tck.geoKT = c->geoKT;
@@ -1417,7 +1466,8 @@ extern "C" int dg_batch_convert(dg_batch* b, int to_g, uintptr_t stream) {
 
 extern "C" int dg_batch_step_ader(dg_batch* b, int32_t nsteps, int32_t red, uintptr_t stream) {
   if (!b || nsteps < 0) return DG_EINVAL;
-  if (red != 0 && red != 2) return b->fail(DG_EUNSUPPORTED, "reduce_every must be 0 or 2 in this build");
+  if (red != 0 && red != 2)
+    return b->fail(DG_EUNSUPPORTED, "batches take reduce_every 0 or 2 (1 and 3: dg_step_ader per solve)");
   return batch_steps(b, 1, red, nsteps, stream);
 }
 

@@ -31,6 +31,7 @@ struct SetupParams {
   void* geoK;   // compact affine operator data, or nullptr
   void* geoKT;  // compact affine predictor data, or nullptr
   int tstride;
+  int tstep;  // predictor geometry at Gauss sets m = n, n - tstep, ... (1 or 2)
   int prec;  // 0 double, 1 float
   int* bad;  // set to 1 if det J <= 0 anywhere
 };
@@ -43,13 +44,16 @@ typedef cudaError_t (*EnergyFn)(const EnergyParams& p, int epb, cudaStream_t st)
 typedef cudaError_t (*BasisFn)(void* U, int E, int to_g, int epb, cudaStream_t st);
 typedef int (*SmemFn)(int which, int red);  // bytes per element
 typedef int (*MaxThrFn)(int which);          // largest launchable block
+typedef int (*MaxThr0Fn)();
 
 struct KernelTable {
   OpFn op[2][DG_NMAX + 1];
   OpFn opg[2][DG_NMAX + 1];   // operator on Gauss-basis states
   OpFn opga[2][DG_NMAX + 1];  // same, affine elements with constant coefficients
   BasisFn basis[2][DG_NMAX + 1];
-  TckFn tck[2][DG_NMAX + 1];
+  TckFn tck[2][DG_NMAX + 1];      // reduction every 0 or 2 derivatives
+  TckFn tck_odd[2][DG_NMAX + 1];  // reduction every 1 or 3 derivatives
+  MaxThr0Fn tck_odd_maxthr[2][DG_NMAX + 1];
   EnergyFn energy[2][DG_NMAX + 1];
   SmemFn smem[2][DG_NMAX + 1];
   MaxThrFn maxthr[2][DG_NMAX + 1];
@@ -65,6 +69,10 @@ int upload_f64_lo(const double* d, const float* f);
 int upload_f64_hi(const double* d, const float* f);
 int upload_f32_lo(const double* d, const float* f);
 int upload_f32_hi(const double* d, const float* f);
+void register_tck_odd_f64(KernelTable* t);
+void register_tck_odd_f32(KernelTable* t);
+int upload_tck_odd_f64(const double* d, const float* f);
+int upload_tck_odd_f32(const double* d, const float* f);
 
 struct BatchItem;
 struct BatchInst;

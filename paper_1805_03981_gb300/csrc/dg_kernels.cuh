@@ -135,36 +135,59 @@ __host__ __device__ constexpr int line_stride() {
 
 // Contract an X x Y x Z tile (4 fields, field stride FS_IN) along DIR with
 // the RO x RI matrix at OFF (RI = extent along DIR), writing the result tile
-// (extent RO along DIR, field stride FS_OUT) to dst.  Threads 0..nthr-1 of
-// the element share the lines.  dst may equal src only if RO == RI.
+// (extent RO along DIR, field stride FS_OUT) to dst.  contract_line does one
+// line l of the tile.  dst may equal src only if RO == RI.
+template <typename Real, int DIR, int X, int Y, int Z, int RO, int OFF, int FS_IN, int FS_OUT,
+          bool ADD = false>
+__device__ __forceinline__ void contract_line(const Real* src, Real* dst, int l, Real scale = Real(1)) {
+  constexpr int RI = DIR == 0 ? X : (DIR == 1 ? Y : Z);
+  constexpr int A = DIR == 0 ? Y : X;  // extent of the first line coordinate
+  constexpr int OX = DIR == 0 ? RO : X, OY = DIR == 1 ? RO : Y;
+  const int a = l % A, b = l / A;
+  const int bi = line_base<DIR, X, Y>(a, b);
+  const int bo = line_base<DIR, OX, OY>(a, b);
+  constexpr int si = line_stride<DIR, X, Y>();
+  constexpr int so = line_stride<DIR, OX, OY>();
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    Real in[RI], out[RO];
+#pragma unroll
+    for (int s = 0; s < RI; ++s) in[s] = src[f * FS_IN + bi + si * s];
+    mv<Real, OFF, RO, RI>(in, out);
+#pragma unroll
+    for (int s = 0; s < RO; ++s) {
+      if (ADD)
+        dst[f * FS_OUT + bo + so * s] += scale * out[s];
+      else
+        dst[f * FS_OUT + bo + so * s] = out[s];
+    }
+  }
+}
+
+// The whole tile of one element: threads 0..nthr-1 of the element share the lines.
 template <typename Real, int DIR, int X, int Y, int Z, int RO, int OFF, int FS_IN, int FS_OUT,
           bool ADD = false>
 __device__ __forceinline__ void contract_tile(const Real* src, Real* dst, int t, int nthr,
                                               Real scale = Real(1)) {
-  constexpr int RI = DIR == 0 ? X : (DIR == 1 ? Y : Z);
-  constexpr int A = DIR == 0 ? Y : X;  // extent of the first line coordinate
-  constexpr int B = DIR == 2 ? Y : Z;  // extent of the second
-  constexpr int OX = DIR == 0 ? RO : X, OY = DIR == 1 ? RO : Y;
-  for (int l = t; l < A * B; l += nthr) {
-    const int a = l % A, b = l / A;
-    const int bi = line_base<DIR, X, Y>(a, b);
-    const int bo = line_base<DIR, OX, OY>(a, b);
-    constexpr int si = line_stride<DIR, X, Y>();
-    constexpr int so = line_stride<DIR, OX, OY>();
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      Real in[RI], out[RO];
-#pragma unroll
-      for (int s = 0; s < RI; ++s) in[s] = src[f * FS_IN + bi + si * s];
-      mv<Real, OFF, RO, RI>(in, out);
-#pragma unroll
-      for (int s = 0; s < RO; ++s) {
-        if (ADD)
-          dst[f * FS_OUT + bo + so * s] += scale * out[s];
-        else
-          dst[f * FS_OUT + bo + so * s] = out[s];
-      }
-    }
+  constexpr int A = DIR == 0 ? Y : X;
+  constexpr int B = DIR == 2 ? Y : Z;  // extent of the second line coordinate
+  for (int l = t; l < A * B; l += nthr)
+    contract_line<Real, DIR, X, Y, Z, RO, OFF, FS_IN, FS_OUT, ADD>(src, dst, l, scale);
+}
+
+// The tiles of ne elements (element stride es in src and dst): the lines of
+// all of them are spread over threads T = 0..nthr-1 of the block, so that a
+// small tile keeps whole warps busy instead of a few lanes of every warp.
+template <typename Real, int DIR, int X, int Y, int Z, int RO, int OFF, int FS_IN, int FS_OUT,
+          bool ADD = false>
+__device__ __forceinline__ void contract_tile_b(const Real* src0, Real* dst0, int es, int ne, int T,
+                                                int nthr) {
+  constexpr int A = DIR == 0 ? Y : X;
+  constexpr int B = DIR == 2 ? Y : Z;
+  for (int L = T; L < ne * A * B; L += nthr) {
+    const int le = L / (A * B);
+    contract_line<Real, DIR, X, Y, Z, RO, OFF, FS_IN, FS_OUT, ADD>(src0 + le * es, dst0 + le * es,
+                                                                    L - le * (A * B));
   }
 }
 
@@ -1048,17 +1071,19 @@ struct TckParams {
   int E;
   int gmode;  // 1: U and Ubar hold Gauss-point values (no basis change)
   int aff;    // 1: affine elements with constant coefficients (geoKT)
+  int geo_step;  // geoT holds the Gauss sets m = n, n - geo_step, ... >= 2 (1 or 2)
   const void* geoKT;  // [E][DG_AFF_TCK]: J^-1 (9), -rho c^2, -1/rho
 };
 
-// m-point levels visited with reduction every second derivative: N, N-2, ...
+// m-point levels visited with reduction every RED-th derivative (RED = 0:
+// none): N, N-RED, ... >= 1
 template <int N, int RED>
 __host__ __device__ constexpr int tck_level_count() {
-  return RED == 0 ? 1 : (N + 1) / 2;
+  return RED == 0 ? 1 : (N - 1) / RED + 1;
 }
 template <int N, int RED>
 __host__ __device__ constexpr int tck_level_m(int l) {
-  return RED == 0 ? N : N - 2 * l;
+  return RED == 0 ? N : N - RED * l;
 }
 // accumulator offset of level l (Reals, 4 fields each)
 template <int N, int RED>
@@ -1071,27 +1096,31 @@ template <int N, int RED>
 __host__ __device__ constexpr int tck_smem_per_elem() {
   return 8 * N * N * N + tck_acc_off<N, RED>(tck_level_count<N, RED>());
 }
-// per-element geometry of the predictor: levels m = N, N-2, ... >= 2,
+// per-element geometry of the predictor: Gauss sets m = n, n-s, n-2s, ... >= 2
+// (s = 2 serves reduction every 0 or 2 derivatives, s = 1 every 1, 2 or 3),
 // each [3 d][3 i][m^3] line-major J^-1_{d i}, then [2][m^3] (-rho c^2, -1/rho)
-__host__ __device__ constexpr int tck_geo_level_off(int n, int l) {
-  return l == 0 ? 0 : tck_geo_level_off(n, l - 1) + 11 * (n - 2 * (l - 1)) * (n - 2 * (l - 1)) *
-                                                         (n - 2 * (l - 1));
-}
-__host__ __device__ constexpr int tck_geo_levels(int n) { return n / 2; }  // m >= 2
-__host__ __device__ constexpr int tck_geo_stride(int n) {
-  return tck_geo_level_off(n, tck_geo_levels(n));
+__host__ __device__ constexpr int tck_geo_stride(int n, int s) {
+  return n < 2 ? 0 : 11 * n * n * n + tck_geo_stride(n - s, s);
 }
 
 // One derivative T_j = -S T_{j-1} at an M^3 Gauss set (Alg. 2 "evaluate the
-// gradient, set values"): src holds T_{j-1} (4 x M^3, field stride FS),
-// dst receives T_j.  g points at this level's geometry block.
+// gradient, set values") for the ne elements of a block: src0 holds element
+// 0's T_{j-1} (4 x M^3, field stride FS), dst0 receives T_j, es is the
+// element stride in shared memory; g0 points at element 0's geometry of this
+// set, gs is the per-element geometry stride.  The ne M^2 lines of a
+// direction are spread over all threads of the block.
 template <int M, typename Real, int FS>
-__device__ __forceinline__ void tck_derivative(const Real* src, Real* dst, const Real* __restrict__ g,
-                                               int t, int nthr) {
+__device__ __forceinline__ void tck_derivative(const Real* src0, Real* dst0, int es,
+                                               const Real* __restrict__ g0, long long gs, int ne, int T,
+                                               int nthr) {
   constexpr int M2 = M * M, M3 = M2 * M;
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
-    for (int l = t; l < M2; l += nthr) {
+    for (int L = T; L < ne * M2; L += nthr) {
+      const int le = L / M2, l = L - le * M2;
+      const Real* src = src0 + le * es;
+      Real* dst = dst0 + le * es;
+      const Real* g = g0 + le * gs;
       const int a = l % M, b = l / M;
       const int base = dir == 0 ? M * a + M2 * b : (dir == 1 ? a + M2 * b : a + M * b);
       const int st = dir == 0 ? 1 : (dir == 1 ? M : M2);
@@ -1144,14 +1173,18 @@ __device__ __forceinline__ void tck_derivative(const Real* src, Real* dst, const
 // one derivative of p per direction (two contractions per direction instead
 // of four).  g: the element's DG_AFF_TCK values.
 template <int M, typename Real, int FS>
-__device__ __forceinline__ void tck_derivative_aff(const Real* src, Real* dst, const Real* __restrict__ g,
-                                                   int t, int nthr) {
+__device__ __forceinline__ void tck_derivative_aff(const Real* src0, Real* dst0, int es,
+                                                   const Real* __restrict__ g0, int ne, int T, int nthr) {
   constexpr int M2 = M * M;
-  const Real cp = __ldg(g + 9), cv = __ldg(g + 10);
 #pragma unroll
   for (int dir = 0; dir < 3; ++dir) {
-    const Real j0 = __ldg(g + dir * 3), j1 = __ldg(g + dir * 3 + 1), j2 = __ldg(g + dir * 3 + 2);
-    for (int l = t; l < M2; l += nthr) {
+    for (int L = T; L < ne * M2; L += nthr) {
+      const int le = L / M2, l = L - le * M2;
+      const Real* src = src0 + le * es;
+      Real* dst = dst0 + le * es;
+      const Real* g = g0 + le * DG_AFF_TCK;
+      const Real cp = __ldg(g + 9), cv = __ldg(g + 10);
+      const Real j0 = __ldg(g + dir * 3), j1 = __ldg(g + dir * 3 + 1), j2 = __ldg(g + dir * 3 + 2);
       const int a = l % M, b = l / M;
       const int base = dir == 0 ? M * a + M2 * b : (dir == 1 ? a + M2 * b : a + M * b);
       const int st = dir == 0 ? 1 : (dir == 1 ? M : M2);
@@ -1194,69 +1227,80 @@ __device__ __forceinline__ void tck_derivative_aff(const Real* src, Real* dst, c
   }
 }
 
-// Reference L2 projection M^3 -> (M-2)^3 (Alg. 3): three contractions,
-// src (M^3, field stride FS) -> tmp -> src ... result in dst.
-template <int M, typename Real, int FS>
-__device__ __forceinline__ void tck_project(Real* src, Real* tmp, int t, int nthr) {
-  constexpr int R = M - 2;
-  contract_tile<Real, 0, M, M, M, R, OFF_P(M), FS, FS>(src, tmp, t, nthr);
+// Reference L2 projection M^3 -> (M-RR)^3 (Sec. 3.3, Alg. 3 for RR = 2):
+// three contractions, src (M^3, field stride FS) -> tmp -> src; the result
+// is left in tmp.
+template <int M, int RR, typename Real, int FS>
+__device__ __forceinline__ void tck_project(Real* src0, Real* tmp0, int es, int ne, int T, int nthr) {
+  constexpr int R = M - RR;
+  contract_tile_b<Real, 0, M, M, M, R, OFF_PR(M, RR), FS, FS>(src0, tmp0, es, ne, T, nthr);
   __syncthreads();
-  contract_tile<Real, 1, R, M, M, R, OFF_P(M), FS, FS>(tmp, src, t, nthr);
+  contract_tile_b<Real, 1, R, M, M, R, OFF_PR(M, RR), FS, FS>(tmp0, src0, es, ne, T, nthr);
   __syncthreads();
-  contract_tile<Real, 2, R, R, M, R, OFF_P(M), FS, FS>(src, tmp, t, nthr);
-  __syncthreads();
-}
-
-// acc_big += IU(M+2 <- M) applied to acc_small in all three directions
-template <int M, typename Real, int FS>
-__device__ __forceinline__ void tck_fold(const Real* small, Real* big, Real* t1, Real* t2, int t,
-                                         int nthr) {
-  constexpr int B = M + 2;
-  contract_tile<Real, 0, M, M, M, B, OFF_IU(B), M * M * M, FS>(small, t1, t, nthr);
-  __syncthreads();
-  contract_tile<Real, 1, B, M, M, B, OFF_IU(B), FS, FS>(t1, t2, t, nthr);
-  __syncthreads();
-  contract_tile<Real, 2, B, B, M, B, OFF_IU(B), FS, B * B * B, true>(t2, big, t, nthr);
+  contract_tile_b<Real, 2, R, R, M, R, OFF_PR(M, RR), FS, FS>(src0, tmp0, es, ne, T, nthr);
   __syncthreads();
 }
 
-template <int N, typename Real, int RED>
-__device__ __forceinline__ void tck_accumulate(Real* acc, const Real* T, int m3, Real c, int t,
-                                               int nthr, int fs) {
-  for (int i = t; i < 4 * m3; i += nthr) {
-    const int fl = i / m3, q = i - fl * m3;
-    acc[i] = fma(c, T[fl * fs + q], acc[i]);
+// acc_big += I(M+RR <- M) applied to acc_small in all three directions
+template <int M, int RR, typename Real, int FS>
+__device__ __forceinline__ void tck_fold(const Real* small0, Real* big0, Real* t10, Real* t20, int es,
+                                         int ne, int T, int nthr) {
+  constexpr int B = M + RR;
+  contract_tile_b<Real, 0, M, M, M, B, OFF_IR(B, RR), M * M * M, FS>(small0, t10, es, ne, T, nthr);
+  __syncthreads();
+  contract_tile_b<Real, 1, B, M, M, B, OFF_IR(B, RR), FS, FS>(t10, t20, es, ne, T, nthr);
+  __syncthreads();
+  contract_tile_b<Real, 2, B, B, M, B, OFF_IR(B, RR), FS, B * B * B, true>(t20, big0, es, ne, T, nthr);
+  __syncthreads();
+}
+
+// acc += c T over the ne elements of a block (element stride es; T has
+// field stride fs, acc field stride m3), spread over the block's threads.
+template <typename Real>
+__device__ __forceinline__ void tck_accumulate(Real* acc0, const Real* T0, int es, int m3, Real c,
+                                               int fs, int ne, int tid, int nthr) {
+  const int per = 4 * m3;
+  for (int i = tid; i < ne * per; i += nthr) {
+    const int le = i / per, r = i - le * per;
+    const int fl = r / m3, q = r - fl * m3;
+    Real* acc = acc0 + le * es;
+    acc[r] = fma(c, T0[le * es + fl * fs + q], acc[r]);
   }
 }
 
 // One block's share of the predictor: elements e0 .. e0+ne-1 of a block
-// laid out for epb elements.  Threads of element slots >= epb (a block sized
-// for another degree) take no lines and touch no shared memory, but still
-// reach every barrier.
+// laid out for epb elements.  The basis changes at the full point set give
+// each element's N^2 threads one line each; threads of element slots >= epb
+// (a block sized for another degree) take none of those lines.  From the
+// first derivative on, the lines, points and accumulator entries of all ne
+// elements are spread over every thread of the block, so that the reduced
+// sets (m^2 < N^2 lines per element) still fill whole warps.
 template <int N, typename Real, int RED>
 __device__ __forceinline__ void tck_block(const TckParams& p, const int e0, const int ne, const int epb,
                                           Real* sm) {
   constexpr int N2 = N * N, N3 = N2 * N;
   constexpr int SE = tck_smem_per_elem<N, RED>();
   constexpr int NL = tck_level_count<N, RED>();
-  const int le0 = threadIdx.x / N2;
+  constexpr int ACC = 8 * N3;  // accumulators after the two T buffers
+  const int T = threadIdx.x, NT = blockDim.x;
+  const int le0 = T / N2;
   const bool own = le0 < epb;
   const int le = own ? le0 : 0;
-  const int t = own ? (int)threadIdx.x - le0 * N2 : (1 << 28);  // no line for non-owners
-  const int e = e0 + le;
-  const bool act = le0 < ne;
+  const int t = own ? T - le0 * N2 : (1 << 28);  // no line for non-owners
   Real* s0 = sm + le * SE;  // T buffers (field stride N3)
-  Real* s1 = s0 + 4 * N3;
-  Real* acc = s1 + 4 * N3;  // per-level accumulators (field stride m^3)
   const Real* __restrict__ U = static_cast<const Real*>(p.U);
-  const Real* geo = static_cast<const Real*>(p.geoT) + (size_t)(act ? e : 0) * p.geoT_stride;
-  const Real* geoK = p.aff ? static_cast<const Real*>(p.geoKT) + (size_t)(act ? e : 0) * DG_AFF_TCK : nullptr;
+  const Real* geo0 = static_cast<const Real*>(p.geoT) + (size_t)e0 * p.geoT_stride;
+  const Real* geoK0 = p.aff ? static_cast<const Real*>(p.geoKT) + (size_t)e0 * DG_AFF_TCK : nullptr;
 
-  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+  for (int i = T; i < ne * 4 * N3; i += NT) {
     const int l = i / (4 * N3);
     sm[l * SE + (i - l * 4 * N3)] = U[(size_t)e0 * 4 * N3 + i];
   }
-  for (int i = t; i < tck_acc_off<N, RED>(NL); i += N2) acc[i] = Real(0);
+  constexpr int NACC = tck_acc_off<N, RED>(NL);
+  for (int i = T; i < ne * NACC; i += NT) {
+    const int l = i / NACC;
+    sm[l * SE + ACC + (i - l * NACC)] = Real(0);
+  }
   __syncthreads();
   // GL -> G (Sec. 3.2: the basis change is done per element on the fly)
   if (!p.gmode) {
@@ -1267,43 +1311,45 @@ __device__ __forceinline__ void tck_block(const TckParams& p, const int e0, cons
     contract_tile<Real, 1, N, N, N, N, OFF_V(N), N3, N3>(s0, s0, t, N2);
     __syncthreads();
   }
-  tck_accumulate<N, Real, RED>(acc, s0, N3, (Real)p.coef[0], t, N2, N3);
+  tck_accumulate<Real>(sm + ACC, sm, SE, N3, (Real)p.coef[0], N3, ne, T, NT);
 
-  // Taylor terms j = 1 .. k+1 (k + 1 = N)
-  Real* cur = s0;
-  Real* nxt = s1;
-  int m = N, lvl = 0;
+  // Taylor terms j = 1 .. k+1 (k + 1 = N); cur / nxt: element 0's buffers
+  Real* cur = sm;
+  Real* nxt = sm + 4 * N3;
+  int m = N, goff = 0, aoff = 0;  // goff: this set's geometry; aoff: its accumulator
 #pragma unroll 1
   for (int j = 1; j <= N; ++j) {
-    const Real* g = geo + tck_geo_level_off(N, lvl);
     // derivative at the current m (T_{j-1} in cur, field stride N3)
     switch (m) {
-#define DG_TCK_DERIV(MM)                                                         \
-  case MM:                                                                       \
-    if constexpr (MM <= N) {                                                     \
-      if (p.aff)                                                                 \
-        tck_derivative_aff<MM, Real, N3>(cur, nxt, geoK, t, N2);                 \
-      else                                                                       \
-        tck_derivative<MM, Real, N3>(cur, nxt, g, t, N2);                        \
-    }                                                                            \
+#define DG_TCK_DERIV(MM)                                                                  \
+  case MM:                                                                                \
+    if constexpr (MM <= N) {                                                              \
+      if (p.aff)                                                                          \
+        tck_derivative_aff<MM, Real, N3>(cur, nxt, SE, geoK0, ne, T, NT);                 \
+      else                                                                                \
+        tck_derivative<MM, Real, N3>(cur, nxt, SE, geo0 + goff, p.geoT_stride, ne, T, NT); \
+    }                                                                                     \
     break;
       DG_TCK_DERIV(2) DG_TCK_DERIV(3) DG_TCK_DERIV(4) DG_TCK_DERIV(5) DG_TCK_DERIV(6)
       DG_TCK_DERIV(7) DG_TCK_DERIV(8)
 #undef DG_TCK_DERIV
       default:  // m == 1: the derivative of a constant vanishes
-        for (int i = t; i < 4 * N3; i += N2) nxt[i] = Real(0);
+        for (int i = T; i < ne * 4 * N3; i += NT) {
+          const int l = i / (4 * N3);
+          nxt[l * SE + (i - l * 4 * N3)] = Real(0);
+        }
         __syncthreads();
         break;
     }
-    if (RED == 2 && (j % 2) == 0) {
-      if (m - 2 < 1) break;  // projected to degree < 0: T_j = 0, stop
+    if (RED > 0 && (j % RED) == 0) {
+      if (m - RED < 1) break;  // projected to degree < 0: T_j = 0, stop
       switch (m) {
-#define DG_TCK_PROJ(MM)                                                  \
-  case MM:                                                               \
-    if constexpr (MM <= N && MM >= 3) tck_project<MM, Real, N3>(nxt, cur, t, N2); \
+#define DG_TCK_PROJ(MM)                                                                              \
+  case MM:                                                                                           \
+    if constexpr (RED > 0 && MM <= N && MM - RED >= 1) tck_project<MM, RED, Real, N3>(nxt, cur, SE, ne, T, NT); \
     break;
-        DG_TCK_PROJ(3) DG_TCK_PROJ(4) DG_TCK_PROJ(5) DG_TCK_PROJ(6) DG_TCK_PROJ(7)
-        DG_TCK_PROJ(8)
+        DG_TCK_PROJ(2) DG_TCK_PROJ(3) DG_TCK_PROJ(4) DG_TCK_PROJ(5) DG_TCK_PROJ(6)
+        DG_TCK_PROJ(7) DG_TCK_PROJ(8)
 #undef DG_TCK_PROJ
         default:
           break;
@@ -1312,37 +1358,33 @@ __device__ __forceinline__ void tck_block(const TckParams& p, const int e0, cons
       Real* tmp = cur;
       cur = nxt;
       nxt = tmp;
-      m -= 2;
-      ++lvl;
+      // the stored Gauss sets between m and m - RED (step geo_step) precede the next one
+      const int gs = p.geo_step > 1 ? 2 : 1;
+      for (int mm = m; mm > m - RED; mm -= gs) goff += 11 * mm * mm * mm;
+      aoff += 4 * m * m * m;
+      m -= RED;
     }
     // T_j is in nxt at m points
-    {
-      int off = 0, mm = N;
-      for (int l = 0; l < lvl; ++l) {
-        off += 4 * mm * mm * mm;
-        mm -= 2;
-      }
-      tck_accumulate<N, Real, RED>(acc + off, nxt, m * m * m, (Real)p.coef[j], t, N2, N3);
-    }
+    tck_accumulate<Real>(sm + ACC + aoff, nxt, SE, m * m * m, (Real)p.coef[j], N3, ne, T, NT);
     __syncthreads();
     Real* tmp = cur;
     cur = nxt;
     nxt = tmp;
   }
-  // fold the levels from the smallest up: acc(m+2) += I(m -> m+2) acc(m)
-  if (RED == 2) {
+  // fold the levels from the smallest up: acc(m+RED) += I(m -> m+RED) acc(m)
+  if (RED > 0) {
 #pragma unroll
     for (int l = NL - 1; l >= 1; --l) {
       const int ms = tck_level_m<N, RED>(l);
-      Real* small = acc + tck_acc_off<N, RED>(l);
-      Real* big = acc + tck_acc_off<N, RED>(l - 1);
+      Real* small = sm + ACC + tck_acc_off<N, RED>(l);
+      Real* big = sm + ACC + tck_acc_off<N, RED>(l - 1);
       switch (ms) {
-#define DG_TCK_FOLD(MM)                                                   \
-  case MM:                                                                \
-    if constexpr (MM + 2 <= N) tck_fold<MM, Real, N3>(small, big, s0, s1, t, N2); \
+#define DG_TCK_FOLD(MM)                                                                                   \
+  case MM:                                                                                                \
+    if constexpr (RED > 0 && MM + RED <= N) tck_fold<MM, RED, Real, N3>(small, big, sm, sm + 4 * N3, SE, ne, T, NT); \
     break;
         DG_TCK_FOLD(1) DG_TCK_FOLD(2) DG_TCK_FOLD(3) DG_TCK_FOLD(4) DG_TCK_FOLD(5)
-        DG_TCK_FOLD(6)
+        DG_TCK_FOLD(6) DG_TCK_FOLD(7)
 #undef DG_TCK_FOLD
         default:
           break;
@@ -1353,19 +1395,21 @@ __device__ __forceinline__ void tck_block(const TckParams& p, const int e0, cons
   Real* __restrict__ out = static_cast<Real*>(p.Ubar);
   if (p.gmode) {
     __syncthreads();
-    for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+    for (int i = T; i < ne * 4 * N3; i += NT) {
       const int l = i / (4 * N3);
-      out[(size_t)e0 * 4 * N3 + i] = sm[l * SE + 8 * N3 + (i - l * 4 * N3)];  // level-n accumulator
+      out[(size_t)e0 * 4 * N3 + i] = sm[l * SE + ACC + (i - l * 4 * N3)];  // level-n accumulator
     }
     return;
   }
+  Real* acc = s0 + ACC;
+  Real* s1 = s0 + 4 * N3;
   contract_tile<Real, 2, N, N, N, N, OFF_VI(N), N3, N3>(acc, s0, t, N2);
   __syncthreads();
   contract_tile<Real, 0, N, N, N, N, OFF_VI(N), N3, N3>(s0, s1, t, N2);
   __syncthreads();
   contract_tile<Real, 1, N, N, N, N, OFF_VI(N), N3, N3>(s1, s0, t, N2);
   __syncthreads();
-  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
+  for (int i = T; i < ne * 4 * N3; i += NT) {
     const int l = i / (4 * N3);
     out[(size_t)e0 * 4 * N3 + i] = sm[l * SE + (i - l * 4 * N3)];
   }

@@ -62,18 +62,29 @@ cudaError_t launch_basis(void* U, int E, int to_g, int epb, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int N, typename Real>
-cudaError_t launch_tck(const TckParams& p, int red, int epb, cudaStream_t st) {
+template <int N, typename Real, int RED>
+cudaError_t launch_tck_red(const TckParams& p, int epb, cudaStream_t st) {
   const int threads = epb * N * N;
   const int blocks = (p.E + epb - 1) / epb;
-  if (red == 2) {
-    const size_t smem = (size_t)epb * tck_smem_per_elem<N, 2>() * sizeof(Real);
-    tck_kernel<N, Real, 2><<<blocks, threads, smem, st>>>(p);
-  } else {
-    const size_t smem = (size_t)epb * tck_smem_per_elem<N, 0>() * sizeof(Real);
-    tck_kernel<N, Real, 0><<<blocks, threads, smem, st>>>(p);
-  }
+  const size_t smem = (size_t)epb * tck_smem_per_elem<N, RED>() * sizeof(Real);
+  tck_kernel<N, Real, RED><<<blocks, threads, smem, st>>>(p);
   return cudaGetLastError();
+}
+
+// Reduction every 0 or 2 derivatives; 1 and 3 live in their own units
+// (kern_tck_odd_*.cu, launch_tck_odd).
+template <int N, typename Real>
+cudaError_t launch_tck(const TckParams& p, int red, int epb, cudaStream_t st) {
+  if (red == 2) return launch_tck_red<N, Real, 2>(p, epb, st);
+  if (red == 0) return launch_tck_red<N, Real, 0>(p, epb, st);
+  return cudaErrorInvalidValue;
+}
+
+template <int N, typename Real>
+cudaError_t launch_tck_odd(const TckParams& p, int red, int epb, cudaStream_t st) {
+  if (red == 1) return launch_tck_red<N, Real, 1>(p, epb, st);
+  if (red == 3) return launch_tck_red<N, Real, 3>(p, epb, st);
+  return cudaErrorInvalidValue;
 }
 
 template <int N, typename Real>
@@ -92,8 +103,13 @@ int smem_bytes(int which, int red) {
     return max(max(op_smem_per_elem<N>(), opg_smem_per_elem<N, Real>()),
                opga_smem_per_elem<N>(sizeof(Real) == 4)) *
            (int)sizeof(Real);
-  if (which == 1)
-    return (red == 2 ? tck_smem_per_elem<N, 2>() : tck_smem_per_elem<N, 0>()) * (int)sizeof(Real);
+  if (which == 1) {
+    const int per = red == 1 ? tck_smem_per_elem<N, 1>()
+                  : red == 2 ? tck_smem_per_elem<N, 2>()
+                  : red == 3 ? tck_smem_per_elem<N, 3>()
+                             : tck_smem_per_elem<N, 0>();
+    return per * (int)sizeof(Real);
+  }
   return 4 * N * N * N * (int)sizeof(Real);
 }
 
@@ -156,6 +172,26 @@ int max_threads(int which) {
   if (which == 1)
     return min(kernel_max_threads(tck_kernel<N, Real, 0>), kernel_max_threads(tck_kernel<N, Real, 2>));
   return min(kernel_max_threads(energy_kernel<N, Real>), kernel_max_threads(basis_kernel<N, Real>));
+}
+
+// Largest block of the predictor with reduction every 1 or 3 derivatives.
+template <int N, typename Real>
+int tck_odd_max_threads() {
+  return min(kernel_max_threads(tck_kernel<N, Real, 1>), kernel_max_threads(tck_kernel<N, Real, 3>));
+}
+
+template <int N, typename Real>
+cudaError_t tck_odd_allow_smem() {
+  cudaError_t e;
+  if ((e = allow_smem(tck_kernel<N, Real, 1>)) != cudaSuccess) return e;
+  return allow_smem(tck_kernel<N, Real, 3>);
+}
+
+template <int N, typename Real>
+void register_tck_odd_one(KernelTable* t) {
+  const int pi = sizeof(Real) == 8 ? 0 : 1;
+  t->tck_odd[pi][N] = &launch_tck_odd<N, Real>;
+  t->tck_odd_maxthr[pi][N] = &tck_odd_max_threads<N, Real>;
 }
 
 template <int N, typename Real>

@@ -1,0 +1,28 @@
+// Predictor kernels with reduction every 1 or 3 derivatives, double, n = 2..8
+// (the variants of Sec. 3.3 that Fig. reduc-comp compares).
+#include "kern_inst.cuh"
+
+namespace dg {
+void register_tck_odd_f64(KernelTable* t) {
+  register_tck_odd_one<2, double>(t);
+  register_tck_odd_one<3, double>(t);
+  register_tck_odd_one<4, double>(t);
+  register_tck_odd_one<5, double>(t);
+  register_tck_odd_one<6, double>(t);
+  register_tck_odd_one<7, double>(t);
+  register_tck_odd_one<8, double>(t);
+}
+int upload_tck_odd_f64(const double* d, const float* f) {
+  cudaError_t e;
+  if ((e = cudaMemcpyToSymbol(c_tab_d, d, sizeof(double) * DG_TAB_LEN)) != cudaSuccess) return (int)e;
+  if ((e = cudaMemcpyToSymbol(c_tab_f, f, sizeof(float) * DG_TAB_LEN)) != cudaSuccess) return (int)e;
+  if ((e = tck_odd_allow_smem<2, double>()) != cudaSuccess) return (int)e;
+  if ((e = tck_odd_allow_smem<3, double>()) != cudaSuccess) return (int)e;
+  if ((e = tck_odd_allow_smem<4, double>()) != cudaSuccess) return (int)e;
+  if ((e = tck_odd_allow_smem<5, double>()) != cudaSuccess) return (int)e;
+  if ((e = tck_odd_allow_smem<6, double>()) != cudaSuccess) return (int)e;
+  if ((e = tck_odd_allow_smem<7, double>()) != cudaSuccess) return (int)e;
+  if ((e = tck_odd_allow_smem<8, double>()) != cudaSuccess) return (int)e;
+  return 0;
+}
+}  // namespace dg

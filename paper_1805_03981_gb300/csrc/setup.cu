@@ -11,7 +11,8 @@
 //   (per-element strides geo_stride_A/M/F of tables.h: padded to 8 values)
 //                                            Z-/(Z-+Z+), alpha Z- Z+/((Z-+Z+)|nw|),
 //                                            alpha |nw|/(Z-+Z+)
-//   geoT per level m = n, n-2, ... >= 2: [3 d][3 i][m^3] J^-1_{d i} line-major,
+//   geoT per Gauss set m = n, n-s, ... >= 2 (s = P.tstep, 1 or 2):
+//                                        [3 d][3 i][m^3] J^-1_{d i} line-major,
 //                                        [m^3] -rho c^2, [m^3] -1/rho
 // with J_{i j} = d x_i / d xi_j, Nanson's formula for the face normal and
 // Z = rho c (Sec. 2.4).
@@ -112,7 +113,8 @@ __global__ void setup_kernel(const SetupParams P) {
   const double* cc = P.c + (size_t)e * n3;
   const int ncell = n3, nface = 6 * n2;
   int ntck = 0;
-  for (int m = n; m >= 2; m -= 2) ntck += m * m * m;
+  const int ts = P.tstep > 1 ? 2 : 1;
+  for (int m = n; m >= 2; m -= ts) ntck += m * m * m;
   const int nitems = ncell + nface + ntck;
   for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
     double J[3][3], A[3][3], xi[3];
@@ -174,7 +176,7 @@ __global__ void setup_kernel(const SetupParams P) {
       while (k >= m * m * m) {
         k -= m * m * m;
         off += 11 * m * m * m;
-        m -= 2;
+        m -= ts;
       }
       const int m2 = m * m, m3 = m2 * m;
       const int x = k % m, y = (k / m) % m, z = k / m2;

@@ -132,11 +132,12 @@ int build_tables(HostTables* t) {
       t->tab[OFF_W(c) + a] = wg[a];
       t->tab[OFF_IW(c) + a] = 1.0 / wg[a];
     }
-    if (c > 2) {
-      const int r = c - 2;
+    for (int red = 1; red <= 3; ++red) {
+      if (c <= red) continue;
+      const int r = c - red;
       gauss(r, xr.data(), wr.data());
-      double* P = t->tab + OFF_P(c);
-      double* IU = t->tab + OFF_IU(c);
+      double* P = t->tab + OFF_PR(c, red);
+      double* IU = t->tab + OFF_IR(c, red);
       for (int a = 0; a < r; ++a)
         for (int b = 0; b < c; ++b)
           P[a * c + b] = wg[b] * lagrange(xr.data(), r, a, xg[b]) / wr[a];

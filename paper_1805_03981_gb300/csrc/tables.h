@@ -9,12 +9,14 @@
 //   D  [c][c]      collocation derivative on the Gauss points:
 //                  D[q][a] = (l^G_a)'(x^G_q)                    (Sec. 3.2, Alg. 2)
 //   LF [2][c]      l^G_a(-1), l^G_a(+1): Gauss-basis face traces
-//   P  [c-2][c]    reference-element L2 projection Gauss(c) -> Gauss(c-2):
-//                  P[a][b] = w^c_b l^{c-2}_a(x^c_b) / w^{c-2}_a  (Sec. 3.3)
-//   IU [c][c-2]    prolongation Gauss(c-2) -> Gauss(c):
-//                  IU[q][b] = l^{c-2}_b(x^c_q)
+//   for each reduction r = 1, 2, 3 with c > r:
+//     P_r [c-r][c] reference-element L2 projection Gauss(c) -> Gauss(c-r):
+//                  P_r[a][b] = w^c_b l^{c-r}_a(x^c_b) / w^{c-r}_a  (Sec. 3.3)
+//     I_r [c][c-r] prolongation Gauss(c-r) -> Gauss(c):
+//                  I_r[q][b] = l^{c-r}_b(x^c_q)
 //   W  [c]         Gauss weights; IW [c] their inverses
-// The projection and prolongation blocks are empty for c <= 2.
+// The projection by r is exact because the c-point rule integrates the
+// product of degrees c-1 and c-r-1.
 #pragma once
 
 #define DG_NMAX 8
@@ -25,8 +27,9 @@
 #define DG_HD
 #endif
 
+DG_HD constexpr int dg_red_len(int c, int r) { return c > r ? 2 * c * (c - r) : 0; }
 DG_HD constexpr int dg_tab_block(int c) {
-  return 3 * c * c + 2 * c + (c > 2 ? 2 * c * (c - 2) : 0) + 2 * c;
+  return 3 * c * c + 2 * c + dg_red_len(c, 1) + dg_red_len(c, 2) + dg_red_len(c, 3) + 2 * c;
 }
 DG_HD constexpr int dg_tab_base(int c) {
   return c <= 1 ? 0 : dg_tab_base(c - 1) + dg_tab_block(c - 1);
@@ -35,9 +38,16 @@ DG_HD constexpr int OFF_V(int c) { return dg_tab_base(c); }
 DG_HD constexpr int OFF_VI(int c) { return dg_tab_base(c) + c * c; }
 DG_HD constexpr int OFF_D(int c) { return dg_tab_base(c) + 2 * c * c; }
 DG_HD constexpr int OFF_LF(int c) { return dg_tab_base(c) + 3 * c * c; }
-DG_HD constexpr int OFF_P(int c) { return dg_tab_base(c) + 3 * c * c + 2 * c; }
-DG_HD constexpr int OFF_IU(int c) { return OFF_P(c) + (c > 2 ? c * (c - 2) : 0); }
-DG_HD constexpr int OFF_W(int c) { return OFF_IU(c) + (c > 2 ? c * (c - 2) : 0); }
+// projection by r points (r = 1, 2, 3) from count c, and the prolongation
+// from count c - r back to count c
+DG_HD constexpr int OFF_PR(int c, int r) {
+  return dg_tab_base(c) + 3 * c * c + 2 * c + (r > 1 ? dg_red_len(c, 1) : 0) +
+         (r > 2 ? dg_red_len(c, 2) : 0);
+}
+DG_HD constexpr int OFF_IR(int c, int r) { return OFF_PR(c, r) + (c > r ? c * (c - r) : 0); }
+DG_HD constexpr int OFF_W(int c) {
+  return dg_tab_base(c) + 3 * c * c + 2 * c + dg_red_len(c, 1) + dg_red_len(c, 2) + dg_red_len(c, 3);
+}
 DG_HD constexpr int OFF_IW(int c) { return OFF_W(c) + c; }
 
 // Compact per-element data of affine elements with element-wise constant

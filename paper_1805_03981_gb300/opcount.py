@@ -60,8 +60,8 @@ def tck_levels(n, red):
         if m <= 0:
             break
         seq.append(m)
-        if red == 2 and j % 2 == 0:
-            m -= 2
+        if red and j % red == 0:
+            m -= red
     return seq
 
 
@@ -78,10 +78,10 @@ def tck_flops(n, red=2, basis="gl", affine=False):
         if m > 1:
             m3 = m ** 3
             f += deriv_contr * contraction(m3, m) + deriv_pt * m3   # derivatives + chain rule
-        if red == 2 and j % 2 == 0:
-            if m - 2 < 1:
+        if red and j % red == 0:
+            if m - red < 1:
                 break
-            r = m - 2
+            r = m - red
             f += 4 * (contraction(r * m * m, m) + contraction(r * r * m, m) + contraction(r ** 3, m))
             m = r
             levels.append(m)
@@ -99,7 +99,8 @@ def geometry_reals(n, curved=True):
 
 
 def tck_geometry_reals(n, red=2):
-    lv = [n] if red == 0 else [m for m in range(n, 1, -2)]
+    """Predictor geometry values read per element: the Gauss sets visited."""
+    lv = [n] if red == 0 else [m for m in range(n, 1, -red)]
     return 11 * sum(m ** 3 for m in lv)
 
 

@@ -64,7 +64,8 @@ def _sym_minus_S(fields, Ainv, rho, c, xi):
     return [sp.expand(-rho * c ** 2 * div)] + [sp.expand(-gp[i] / rho) for i in range(3)]
 
 
-@pytest.mark.parametrize("k,reduce_every", [(2, 0), (3, 0), (3, 2), (4, 2), (5, 2)])
+@pytest.mark.parametrize("k,reduce_every", [(2, 0), (3, 0), (3, 2), (4, 2), (5, 2),
+                                            (3, 1), (4, 1), (4, 3), (5, 3)])
 def test_tck_terms_match_symbolic(k, reduce_every):
     n, n3 = k + 1, (k + 1) ** 3
     A = np.array([[0.31, 0.05, -0.02], [0.03, 0.27, 0.04], [0.06, -0.01, 0.22]])
@@ -91,6 +92,7 @@ def test_tck_terms_match_symbolic(k, reduce_every):
     Ubar, terms = o.tck(U, dt, reduce_every, return_terms=True)
     cur = flds
     ubar_ex = [dt * f for f in flds]
+    scale = np.abs(U).max()
     for j, (m, T) in enumerate(terms):
         if j == 0:
             continue
@@ -100,7 +102,8 @@ def test_tck_terms_match_symbolic(k, reduce_every):
             break
         Pm = tensor_points(gauss_1d(m)[0])
         ex = np.stack([ev(f, Pm) for f in cur])
-        scale = max(np.abs(ex).max(), 1e-30)
+        # a term that vanishes exactly is held to the size of the terms before it
+        scale = max(np.abs(ex).max(), scale)
         assert np.abs(T[0] - ex).max() / scale < 1e-11, (j, m)
         ubar_ex = [u + dt ** (j + 1) / math.factorial(j + 1) * f for u, f in zip(ubar_ex, cur)]
     ex = np.stack([ev(f, pts) for f in ubar_ex])
@@ -108,6 +111,32 @@ def test_tck_terms_match_symbolic(k, reduce_every):
     if reduce_every == 2:
         # with reduction the (k+1)-th term vanishes identically (Algorithm 3)
         assert terms[-1][0] in (0, 1) or len(terms) <= k + 2
+
+
+@pytest.mark.parametrize("m,r", [(2, 1), (3, 1), (5, 1), (8, 1), (3, 2), (4, 2), (6, 2),
+                                 (4, 3), (6, 3), (8, 3)])
+def test_projection_is_legendre_truncation(m, r):
+    """The reference-element L2 projection from m to m - r Gauss points
+    (Sec. 3.3) keeps the tensor Legendre modes of degree < m - r in every
+    direction and drops the others: Legendre polynomials are L2-orthogonal
+    on [-1, 1], and the m-point rule integrates every product involved."""
+    from numpy.polynomial import legendre as leg
+    k = m - 1 if m > 1 else 1
+    A = np.diag([0.5, 0.5, 0.5])
+    o = oracle.Oracle(single_element_mesh(A), k, np.ones((1, (k + 1) ** 3)), np.ones((1, (k + 1) ** 3)))
+    rng = np.random.default_rng(100 * m + r)
+    C = rng.normal(size=(4, m, m, m))             # C[f, i, j, l]: mode P_i(x) P_j(y) P_l(z)
+
+    def values(C, npts):
+        x = gauss_1d(npts)[0]
+        V = leg.legvander(x, C.shape[1] - 1)      # V[a, i] = P_i(x_a)
+        # node index a + npts b + npts^2 c (first axis fastest)
+        return np.einsum("fijl,ai,bj,cl->fcba", C, V, V, V).reshape(4, -1)
+
+    T = values(C, m)[None]
+    got = o._project(T, m, r)[0]
+    want = values(C[:, :m - r, :m - r, :m - r], m - r)
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
 
 
 def _errors(method, N, k, cr, t_end, reduce_every=2):
