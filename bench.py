@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--basis", default="g", choices=["g", "gl"],
                     help="state inside the steppers: g = Gauss-point values (default), gl = the paper's storage")
     ap.add_argument("--workload", default="curved_pulse",
-                    choices=["curved_pulse", "plane_wave", "batched", "served", "reduction"])
+                    choices=["curved_pulse", "plane_wave", "batched", "served", "reduction",
+                             "time_to_accuracy"])
     ap.add_argument("--lam", type=float, default=20.0, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="served: arrival window, seconds")
     ap.add_argument("--nrange", default="8,24", help="served: elements per axis, min,max")
@@ -77,6 +78,8 @@ def parse():
                          "and report the relative l2 differences and errors against the exact plane wave")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--kset", default="1,4,7", help="time_to_accuracy: degrees")
+    ap.add_argument("--t-end", type=float, default=1.0, help="time_to_accuracy: end time")
     return ap.parse_args()
 
 
@@ -277,6 +280,82 @@ def generate_instances(seeds, workers=None):
     workers = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_gen_one, seeds, chunksize=4))
+
+
+def _l2_pressure_error(U, xnodes, exact, t, k):
+    """Relative continuous L2 error of the pressure against exact(x, t) on a
+    mesh of equal affine elements (constant det J cancels in the ratio):
+    GL nodal values and node positions are interpolated to (k+3)-point Gauss
+    points per direction (tensor Lagrange interpolation)."""
+    from numpy.polynomial import legendre as leg
+    n, m = k + 1, k + 3
+    xq, wq = leg.leggauss(m)
+    xgl = np.concatenate(([-1.0], np.sort(np.real(leg.legroots(leg.legder([0] * (n - 1) + [1])))), [1.0])) \
+        if n > 2 else np.array([-1.0, 1.0])
+    L = np.ones((m, n))
+    for a in range(n):
+        for b in range(n):
+            if b != a:
+                L[:, a] *= (xq - xgl[b]) / (xgl[a] - xgl[b])
+    E = U.shape[0]
+    p = U[:, 0].reshape(E, n, n, n)                       # [e][z][y][x]
+    ph = np.einsum("qa,rb,sc,ecba->esrq", L, L, L, p).reshape(E, -1)
+    X = xnodes.reshape(E, n, n, n, 3)
+    Xq = np.einsum("qa,rb,sc,ecbai->esrqi", L, L, L, X).reshape(E, -1, 3)
+    w = np.einsum("a,b,c->cba", wq, wq, wq).reshape(-1)
+    pe = exact(Xq, t)[..., 0]
+    return float(np.sqrt(np.sum(w * (ph - pe) ** 2) / np.sum(w * pe ** 2)))
+
+
+def time_to_accuracy_bench(args, dgw, torch):
+    """Accuracy against GPU time (Sec. 4.5, Fig. solv-acc-RK-vs-ADER, in 3D):
+    the standing wave on periodic Cartesian meshes of growing size, degrees
+    k = 1, 4, 7, LSRK(5,4) and ADER (order k+1, reduction every 2nd
+    derivative), at Cr = 0.1 and at 0.9 times each method's critical Courant
+    number (measured on the GPU first), to t_end = 1; relative L2 pressure
+    error at t_end against the device time of the solve."""
+    import synth
+    from paper_1805_03981_gb300 import crit_courant
+    prec = dgw.DG_FP64 if args.prec == "fp64" else dgw.DG_FP32
+    sizes = {1: (4, 8, 16, 32, 64), 2: (4, 8, 16, 32), 3: (4, 8, 16, 24, 32), 4: (2, 4, 8, 16, 24),
+             5: (2, 4, 8, 16, 20), 6: (2, 4, 8, 12, 16), 7: (2, 4, 8, 12, 16)}
+    t_end = args.t_end
+    rows, crit = [], {}
+    for k in (int(x) for x in args.kset.split(",")):
+        for method in ("lsrk", "ader"):
+            crit[(k, method)] = crit_courant.critical(k, method)
+        for N in sizes[k]:
+            cfg = synth.configs.standing_wave(N=N, k=k)
+            s = dgw.Solver(cfg["mesh"], k, prec, cfg["alpha"], cfg["rho"], cfg["c"])
+            s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
+            dof = 4 * (k + 1) ** 3 * N ** 3
+            for method in ("lsrk", "ader"):
+                for label, cr in (("0.1", 0.1), ("0.9crit", 0.9 * crit[(k, method)])):
+                    dt_max = synth.configs.dt_from_courant(cr, cfg["mesh"]["h"], 1.0, k)
+                    steps = int(np.ceil(t_end / dt_max))
+                    dt = t_end / steps
+                    U = s.to_device(cfg["U0"])
+                    torch.cuda.synchronize()
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record()
+                    if method == "lsrk":
+                        s.step_lsrk(U, dt, steps)
+                    else:
+                        s.step_ader(U, dt, steps, 2)
+                    ev1.record()
+                    torch.cuda.synchronize()
+                    sec = ev0.elapsed_time(ev1) * 1e-3
+                    err = _l2_pressure_error(U.double().cpu().numpy(), cfg["xnodes"], cfg["exact"], t_end, k)
+                    rows.append({"k": k, "N": N, "dof": dof, "method": method, "cr": label,
+                                 "cr_value": cr, "steps": steps, "gpu_seconds": sec, "l2_p": err,
+                                 "dofs_per_s": dof * steps / sec})
+            s.close()
+    out = {"time_to_accuracy": {
+        "workload": "standing wave p = cos 2pi x cos 2pi y cos 2pi z cos wt on periodic Cartesian N^3 meshes, "
+                    "rho = c = 1, upwind, t_end = %g, %s, state basis %s" % (t_end, args.prec.upper(), args.basis),
+        "crit_courant": {"%d/%s" % kk: v for kk, v in crit.items()}, "rows": rows}}
+    print(json.dumps(out))
+    return 0
 
 
 def reduction_bench(args, dgw, torch):
@@ -539,6 +618,8 @@ def main():
         return served_bench(args, dgw, torch)
     if args.workload == "reduction":
         return reduction_bench(args, dgw, torch)
+    if args.workload == "time_to_accuracy":
+        return time_to_accuracy_bench(args, dgw, torch)
     N, k = args.size, args.k
     cfg = workload(N, k, args.workload)
     if args.accuracy:

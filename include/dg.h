@@ -316,6 +316,48 @@ const char* dg_batch_last_error(const dg_batch* b);
 void dg_batch_destroy(dg_batch* b);
 
 /*
+ * Partitioned solve (the data-parallel split of one solve, Sec. 4.6: the
+ * operator needs the neighbours' data across a face, the predictor none).
+ * A part is a context set up on its owned elements followed by ghost
+ * elements: copies of the neighbours of owned elements that other parts own.
+ * Ghosts keep their faces towards elements present in the part and have
+ * walls elsewhere; they are never stepped.
+ *
+ * dg_set_owned: only the first n_owned elements of ctx are stepped (default
+ * all); operator, predictor, basis changes, energy and norms then cover those
+ * elements alone. 1 <= n_owned <= element count, else DG_EINVAL.
+ *
+ * dg_part_create: ctxs[P], U[P] (device states of the parts, [E_i][4][n^3],
+ * 16-byte aligned, caller-owned, must outlive the object), n_ghost[P] with
+ * n_owned_i + n_ghost[i] == E_i. ghost_src_part / ghost_src_elem list, part
+ * after part and in each part's ghost order, the owning part (!= the ghost's
+ * own part) and its owned element index of every ghost. Parts must share
+ * degree, precision, device and storage basis (dg_set_basis). Copies the map
+ * to the device (a small allocation), so create once and step many times.
+ * Errors: DG_EINVAL (message in dg_last_error(NULL)), DG_ENOMEM.
+ *
+ * dg_part_step_lsrk / dg_part_step_ader: as dg_step_lsrk / dg_step_ader for
+ * the whole mesh. Before every operator application the ghost tiles of its
+ * input (the stage input for LSRK, the predictor for ADER) are copied from
+ * their owners by one gather kernel on the stream: five exchanges per LSRK
+ * step, one per ADER step. Every owned element then computes exactly what it
+ * computes in the unpartitioned solve, so the owned states are bitwise equal
+ * to those of one context on the whole mesh that runs the same kernels (the
+ * same storage basis, and every part affine or not as the whole mesh is).
+ * dg_part_exchange copies the ghosts of the states U themselves.
+ */
+int dg_set_owned(dg_ctx* ctx, int32_t n_owned);
+typedef struct dg_part dg_part;
+int dg_part_create(dg_ctx* const* ctxs, void* const* U, int32_t P, const int32_t* n_ghost,
+                   const int32_t* ghost_src_part, const int32_t* ghost_src_elem, dg_part** out);
+int dg_part_step_lsrk(dg_part* t, double dt, int32_t nsteps, uintptr_t stream);
+int dg_part_step_ader(dg_part* t, double dt, int32_t nsteps, int32_t reduce_every, uintptr_t stream);
+int dg_part_exchange(dg_part* t, uintptr_t stream);
+int dg_part_info(const dg_part* t, int32_t* n_parts, int32_t* n_ghost_total, uint64_t* exchanges);
+const char* dg_part_last_error(const dg_part* t);
+void dg_part_destroy(dg_part* t);
+
+/*
  * Served form: continuous batching of solves on one GPU. An admission thread
  * takes queued requests in arrival order while they fit the HBM budget (a
  * request that does not fit lets later, smaller ones in) and sets them up on

@@ -18,6 +18,8 @@ EXPORTED_SYMBOLS = [
     "dg_server_create", "dg_submit", "dg_poll", "dg_server_stats", "dg_server_destroy",
     "dg_request_bytes", "dg_mesh_setup_coef", "dg_set_basis", "dg_get_basis", "dg_check_device",
     "dg_is_affine", "dg_change_basis", "dg_batch_set_basis", "dg_batch_convert",
+    "dg_set_owned", "dg_part_create", "dg_part_step_lsrk", "dg_part_step_ader", "dg_part_exchange",
+    "dg_part_info", "dg_part_last_error", "dg_part_destroy",
 ]
 BASIS_GL, BASIS_G = 0, 1
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
@@ -125,6 +127,15 @@ def load_library():
         "dg_get_basis": (C.c_int, [vp]),
         "dg_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
         "dg_last_error": (C.c_char_p, [vp]),
+        "dg_set_owned": (C.c_int, [vp, C.c_int32]),
+        "dg_part_create": (C.c_int, [C.POINTER(vp), C.POINTER(vp), C.c_int32, C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(vp)]),
+        "dg_part_step_lsrk": (C.c_int, [vp, C.c_double, C.c_int32, st]),
+        "dg_part_step_ader": (C.c_int, [vp, C.c_double, C.c_int32, C.c_int32, st]),
+        "dg_part_exchange": (C.c_int, [vp, st]),
+        "dg_part_info": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]),
+        "dg_part_last_error": (C.c_char_p, [vp]),
+        "dg_part_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -286,6 +297,10 @@ class Solver:
 
     def is_affine(self):
         return bool(self.lib.dg_is_affine(self.ctx))
+
+    def set_owned(self, n_owned):
+        """Step only the first n_owned elements (the rest are ghosts of a part)."""
+        self._check(self.lib.dg_set_owned(self.ctx, int(n_owned)))
 
     def set_basis(self, basis):
         """BASIS_GL (paper's storage, default) or BASIS_G (Gauss values inside the steppers)."""

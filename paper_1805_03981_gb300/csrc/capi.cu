@@ -80,6 +80,7 @@ int init_device(int dev, std::string* err) {
 struct dg_ctx {
   int dev = 0;
   int E = 0, k = 0, n = 0, q = 0, prec = 0;
+  int Erun = 0;  // elements stepped: the first Erun (the rest are ghosts of a partition)
   double alpha = 1.0;
   size_t rsize = 8;
   int32_t* nbr = nullptr;
@@ -124,6 +125,7 @@ struct dg_ctx {
   std::string err;
 
   size_t state_elems() const { return (size_t)E * 4 * n * n * n; }
+  size_t run_elems() const { return (size_t)Erun * 4 * n * n * n; }
   size_t state_bytes() const { return state_elems() * rsize; }
 
   int fail(int code, const char* fmt, ...) {
@@ -374,7 +376,7 @@ OpParams op_params(const dg_ctx* ctx) {
   p.geoF = ctx->geoF;
   p.geoK = ctx->geoK;
   p.err = ctx->bad;
-  p.E = ctx->E;
+  p.E = ctx->Erun;
   return p;
 }
 
@@ -392,7 +394,7 @@ int launch_op(dg_ctx* ctx, const OpParams& p, int epi, cudaStream_t st, bool gba
 // In-place change of basis of a whole state (GL <-> G).
 int change_basis(dg_ctx* ctx, void* U, int to_g, cudaStream_t st) {
   dg_ctx::Span span(ctx, DG_KIND_OTHER, st);
-  DG_CK(g_kt.basis[ctx->prec][ctx->n](U, ctx->E, to_g, ctx->epb_en, st), "basis kernel launch");
+  DG_CK(g_kt.basis[ctx->prec][ctx->n](U, ctx->Erun, to_g, ctx->epb_en, st), "basis kernel launch");
   span.done();
   ctx->launches++;
   return DG_OK;
@@ -410,7 +412,7 @@ int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaS
   p.geoT = ctx->geoT;
   p.geoT_stride = ctx->tstride;
   p.geo_step = ctx->tstep;
-  p.E = ctx->E;
+  p.E = ctx->Erun;
   double fact = 1.0;
   for (int j = 0; j <= ctx->n; ++j) {  // dt^{j+1} / (j+1)!
     fact *= (j + 1);
@@ -627,6 +629,7 @@ int dg_mesh_setup_coef(const dg_mesh_desc* m, int k, int prec, double alpha, con
   if (!ctx) return DG_ENOMEM;
   ctx->dev = dev;
   ctx->E = m->n_elem;
+  ctx->Erun = m->n_elem;
   ctx->k = k;
   ctx->n = k + 1;
   ctx->q = m->geom_degree;
@@ -776,13 +779,13 @@ int dg_energy(dg_ctx* ctx, const void* U, double* out, uintptr_t stream) {
   int rc;
   if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
   DeviceGuard g(ctx->dev);
-  const int blocks = (ctx->E + ctx->epb_en - 1) / ctx->epb_en;
+  const int blocks = (ctx->Erun + ctx->epb_en - 1) / ctx->epb_en;
   if ((rc = ensure_partial(ctx, blocks))) return rc;
   EnergyParams p;
   p.U = U;
   p.geoM = ctx->geoM;
   p.partial = ctx->partial;
-  p.E = ctx->E;
+  p.E = ctx->Erun;
   cudaStream_t st = S(stream);
   DG_CK(g_kt.energy[ctx->prec][ctx->n](p, ctx->epb_en, st), "energy kernel launch");
   ctx->launches++;
@@ -805,7 +808,7 @@ int dg_norms(dg_ctx* ctx, const void* A, const void* B, double* aa, double* dd, 
   const int blocks = 1024;
   if ((rc = ensure_partial(ctx, 2 * blocks))) return rc;
   cudaStream_t st = S(stream);
-  const size_t cnt = ctx->state_elems();
+  const size_t cnt = ctx->run_elems();
   if (ctx->prec == DG_FP64)
     sumsq_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(A),
                                                  static_cast<const double*>(B), cnt, ctx->partial);
@@ -969,7 +972,7 @@ extern "C" int dg_energy_noalloc(dg_ctx* ctx, const void* U, double* out, uintpt
   int rc;
   if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
   if (!out) return ctx->fail(DG_EINVAL, "out is NULL");
-  const int blocks = (ctx->E + ctx->epb_en - 1) / ctx->epb_en;
+  const int blocks = (ctx->Erun + ctx->epb_en - 1) / ctx->epb_en;
   if (blocks > kNoallocMaxPartials)
     return ctx->fail(DG_EINVAL,
                      "dg_energy_noalloc: this mesh needs %d partial sums but the fixed buffer "
@@ -998,7 +1001,7 @@ extern "C" int dg_energy_noalloc(dg_ctx* ctx, const void* U, double* out, uintpt
   p.U = U;
   p.geoM = ctx->geoM;
   p.partial = part;
-  p.E = ctx->E;
+  p.E = ctx->Erun;
   cudaStream_t st = S(stream);
   DG_CK(g_kt.energy[ctx->prec][ctx->n](p, ctx->epb_en, st), "energy kernel launch");
   noalloc_sum_kernel<<<1, 256, 0, st>>>(part, blocks, out);
@@ -1303,7 +1306,7 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     I.tck.geoT = c->geoT;
     I.tck.geoT_stride = c->tstride;
     I.tck.geo_step = c->tstep;
-    I.tck.E = c->E;
+    I.tck.E = c->Erun;
     I.tck.aff = c->affine ? 1 : 0;
     I.tck.geoKT = c->geoKT;
     double fact = 1.0;
@@ -1315,8 +1318,8 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     const int eo = std::max(1, std::min(c->epb_op, maxthr(nn, 0) / n2));
     const int et = std::max(1, std::min(c->epb_tck, maxthr(nn, 1) / n2));
     // items are cut below, once each group's launch shape is known
-    hop[gk].push_back({i, 0, c->E, nn, eo});
-    htck[gk].push_back({i, 0, c->E, nn, et});
+    hop[gk].push_back({i, 0, c->Erun, nn, eo});
+    htck[gk].push_back({i, 0, c->Erun, nn, et});
     BatchGroup& g = byn[gk];
     g.n = nn;
     g.aff = c->affine ? 1 : 0;
@@ -1496,3 +1499,256 @@ extern "C" int dg_batch_info(const dg_batch* b, int32_t* n_inst, int32_t* n_item
 extern "C" const char* dg_batch_last_error(const dg_batch* b) { return b ? b->err.c_str() : ""; }
 
 extern "C" void dg_batch_destroy(dg_batch* b) { delete b; }
+
+// ---------------------------------------------------------------------------
+// Partitioned solve: one mesh split into parts, each a context whose first
+// n_owned elements are stepped and whose remaining elements are ghost copies
+// of neighbours owned by other parts.  Before every operator application the
+// ghost tiles of its input are refreshed from their owners (five exchanges
+// per LSRK step, one per ADER step: the predictor is element-local, Sec. 4.6).
+// All parts live on this device; the exchange is one gather kernel.
+// ---------------------------------------------------------------------------
+extern "C" int dg_set_owned(dg_ctx* ctx, int32_t n_owned) {
+  if (!ctx) return DG_EINVAL;
+  if (n_owned < 1 || n_owned > ctx->E)
+    return ctx->fail(DG_EINVAL, "n_owned %d outside [1, %d]", n_owned, ctx->E);
+  ctx->Erun = n_owned;
+  return DG_OK;
+}
+
+namespace {
+
+constexpr int DG_PART_MAX = 64;
+struct PartPtrs {
+  void* p[DG_PART_MAX];
+};
+
+// Block g copies ghost tile g: dst part / element <- src part / element,
+// `words` 16-byte words per tile.
+__global__ void ghost_copy_kernel(PartPtrs bufs, const int32_t* __restrict__ map, int words) {
+  const int g = blockIdx.x;
+  const int dp = map[4 * g], de = map[4 * g + 1], sp = map[4 * g + 2], se = map[4 * g + 3];
+  const int4* src = static_cast<const int4*>(bufs.p[sp]) + (size_t)se * words;
+  int4* dst = static_cast<int4*>(bufs.p[dp]) + (size_t)de * words;
+  for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+}
+
+}  // namespace
+
+struct dg_part {
+  int dev = 0, P = 0, nghost = 0, words = 0;
+  std::vector<dg_ctx*> c;
+  std::vector<void*> U;
+  int32_t* map = nullptr;  // [nghost][4]: dst part, dst element, src part, src element
+  uint64_t launches = 0;
+  std::string err;
+  int fail(int code, const char* msg) {
+    err = msg;
+    return code;
+  }
+  ~dg_part() {
+    if (map) {
+      int cur = 0;
+      cudaGetDevice(&cur);
+      cudaSetDevice(dev);
+      cudaFree(map);
+      cudaSetDevice(cur);
+    }
+  }
+};
+
+namespace {
+
+int part_exchange(dg_part* t, void* const* bufs, cudaStream_t st) {
+  if (!t->nghost) return DG_OK;
+  PartPtrs pp;
+  std::memset(&pp, 0, sizeof(pp));
+  for (int i = 0; i < t->P; ++i) pp.p[i] = bufs[i];
+  ghost_copy_kernel<<<t->nghost, 128, 0, st>>>(pp, t->map, t->words);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return t->fail(DG_ECUDA, cudaGetErrorString(e));
+  t->launches++;
+  return DG_OK;
+}
+
+int part_lsrk(dg_part* t, double dt, int nsteps, cudaStream_t st) {
+  int rc;
+  const int P = t->P;
+  for (int i = 0; i < P; ++i) {
+    dg_ctx* c = t->c[i];
+    if ((rc = ensure(c, &c->U2, "LSRK state")) || (rc = ensure(c, &c->U3, "LSRK state")) ||
+        (rc = ensure(c, &c->dU, "LSRK register")))
+      return t->fail(rc, c->err.c_str());
+  }
+  const bool g = t->c[0]->basis == DG_BASIS_G && nsteps > 0;
+  if (g)
+    for (int i = 0; i < P; ++i)
+      if ((rc = change_basis(t->c[i], t->U[i], 1, st))) return t->fail(rc, t->c[i]->err.c_str());
+  std::vector<void*> in(P);
+  for (int s = 0; s < nsteps; ++s)
+    for (int st5 = 0; st5 < 5; ++st5) {
+      for (int i = 0; i < P; ++i) {
+        dg_ctx* c = t->c[i];
+        void* const chain[6] = {t->U[i], c->U2, c->U3, c->U2, c->U3, t->U[i]};
+        in[i] = chain[st5];
+      }
+      if ((rc = part_exchange(t, in.data(), st))) return rc;
+      for (int i = 0; i < P; ++i) {
+        dg_ctx* c = t->c[i];
+        void* const chain[6] = {t->U[i], c->U2, c->U3, c->U2, c->U3, t->U[i]};
+        OpParams p = op_params(c);
+        p.U = chain[st5];
+        p.Uadd = chain[st5];
+        p.out = chain[st5 + 1];
+        p.dU = c->dU;
+        p.cA = kLsrkA[st5];
+        p.cB = kLsrkB[st5];
+        p.dt = dt;
+        p.first = st5 == 0;
+        if ((rc = launch_op(c, p, EPI_LSRK, st, g))) return t->fail(rc, c->err.c_str());
+      }
+    }
+  if (g)
+    for (int i = 0; i < P; ++i)
+      if ((rc = change_basis(t->c[i], t->U[i], 0, st))) return t->fail(rc, t->c[i]->err.c_str());
+  return DG_OK;
+}
+
+int part_ader(dg_part* t, double dt, int nsteps, int red, cudaStream_t st) {
+  int rc;
+  const int P = t->P;
+  for (int i = 0; i < P; ++i) {
+    dg_ctx* c = t->c[i];
+    if ((rc = ensure(c, &c->Ubar, "ADER predictor")) || (rc = ensure_levels(c, red, st)))
+      return t->fail(rc, c->err.c_str());
+  }
+  const bool g = t->c[0]->basis == DG_BASIS_G && nsteps > 0;
+  if (g)
+    for (int i = 0; i < P; ++i)
+      if ((rc = change_basis(t->c[i], t->U[i], 1, st))) return t->fail(rc, t->c[i]->err.c_str());
+  std::vector<void*> bar(P);
+  for (int i = 0; i < P; ++i) bar[i] = t->c[i]->Ubar;
+  for (int s = 0; s < nsteps; ++s) {
+    for (int i = 0; i < P; ++i)
+      if ((rc = launch_tck(t->c[i], t->U[i], t->c[i]->Ubar, dt, red, st, g))) return t->fail(rc, t->c[i]->err.c_str());
+    if ((rc = part_exchange(t, bar.data(), st))) return rc;
+    for (int i = 0; i < P; ++i) {
+      dg_ctx* c = t->c[i];
+      OpParams p = op_params(c);
+      p.U = c->Ubar;
+      p.Uadd = t->U[i];
+      p.out = t->U[i];
+      if ((rc = launch_op(c, p, EPI_ADD, st, g))) return t->fail(rc, c->err.c_str());
+    }
+  }
+  if (g)
+    for (int i = 0; i < P; ++i)
+      if ((rc = change_basis(t->c[i], t->U[i], 0, st))) return t->fail(rc, t->c[i]->err.c_str());
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" int dg_part_create(dg_ctx* const* ctxs, void* const* U, int32_t P, const int32_t* n_ghost,
+                              const int32_t* ghost_src_part, const int32_t* ghost_src_elem, dg_part** out) {
+  if (!out) return DG_EINVAL;
+  *out = nullptr;
+  std::string& e = g_setup_err;
+  if (!ctxs || !U || !n_ghost || P < 1 || P > DG_PART_MAX) {
+    e = "need 1..64 parts with contexts, states and ghost counts";
+    return DG_EINVAL;
+  }
+  dg_ctx* c0 = ctxs[0];
+  if (!c0) return DG_EINVAL;
+  int total = 0;
+  for (int i = 0; i < P; ++i) {
+    dg_ctx* c = ctxs[i];
+    if (!c || c->n != c0->n || c->prec != c0->prec || c->dev != c0->dev || c->basis != c0->basis) {
+      e = "parts must share degree, precision, device and storage basis";
+      return DG_EINVAL;
+    }
+    if (n_ghost[i] < 0 || c->Erun + n_ghost[i] != c->E) {
+      e = "part " + std::to_string(i) + ": n_owned + n_ghost must equal its element count";
+      return DG_EINVAL;
+    }
+    int rc;
+    if ((rc = check_state_ptr(c, U[i], "U"))) {
+      e = c->err;
+      return rc;
+    }
+    total += n_ghost[i];
+  }
+  if (total > 0 && (!ghost_src_part || !ghost_src_elem)) {
+    e = "ghost sources missing";
+    return DG_EINVAL;
+  }
+  std::vector<int32_t> map(4 * (size_t)total);
+  int g = 0;
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < n_ghost[i]; ++j, ++g) {
+      const int sp = ghost_src_part[g], se = ghost_src_elem[g];
+      if (sp < 0 || sp >= P || sp == i || se < 0 || se >= ctxs[sp]->Erun) {
+        e = "ghost " + std::to_string(g) + ": source is not an owned element of another part";
+        return DG_EINVAL;
+      }
+      map[4 * g] = i;
+      map[4 * g + 1] = ctxs[i]->Erun + j;
+      map[4 * g + 2] = sp;
+      map[4 * g + 3] = se;
+    }
+  DeviceGuard dgd(c0->dev);
+  dg_part* t = new (std::nothrow) dg_part();
+  if (!t) return DG_ENOMEM;
+  t->dev = c0->dev;
+  t->P = P;
+  t->nghost = total;
+  t->words = (int)(4 * (size_t)c0->n * c0->n * c0->n * c0->rsize / 16);
+  t->c.assign(ctxs, ctxs + P);
+  t->U.assign(U, U + P);
+  if (total) {
+    cudaError_t ce = cudaMalloc(&t->map, sizeof(int32_t) * map.size());
+    if (ce == cudaSuccess)
+      ce = cudaMemcpy(t->map, map.data(), sizeof(int32_t) * map.size(), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      e = std::string("ghost map: ") + cudaGetErrorString(ce);
+      delete t;
+      return DG_ENOMEM;
+    }
+  }
+  *out = t;
+  return DG_OK;
+}
+
+extern "C" int dg_part_exchange(dg_part* t, uintptr_t stream) {
+  if (!t) return DG_EINVAL;
+  DeviceGuard g(t->dev);
+  return part_exchange(t, t->U.data(), S(stream));
+}
+
+extern "C" int dg_part_step_lsrk(dg_part* t, double dt, int32_t nsteps, uintptr_t stream) {
+  if (!t) return DG_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return t->fail(DG_EINVAL, "need dt > 0 and nsteps >= 0");
+  DeviceGuard g(t->dev);
+  return part_lsrk(t, dt, nsteps, S(stream));
+}
+
+extern "C" int dg_part_step_ader(dg_part* t, double dt, int32_t nsteps, int32_t red, uintptr_t stream) {
+  if (!t) return DG_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return t->fail(DG_EINVAL, "need dt > 0 and nsteps >= 0");
+  if (red < 0 || red > 3) return t->fail(DG_EUNSUPPORTED, "reduce_every must be 0, 1, 2 or 3");
+  DeviceGuard g(t->dev);
+  return part_ader(t, dt, nsteps, red, S(stream));
+}
+
+extern "C" int dg_part_info(const dg_part* t, int32_t* n_parts, int32_t* n_ghost_total, uint64_t* exchanges) {
+  if (!t) return DG_EINVAL;
+  if (n_parts) *n_parts = t->P;
+  if (n_ghost_total) *n_ghost_total = t->nghost;
+  if (exchanges) *exchanges = t->launches;
+  return DG_OK;
+}
+
+extern "C" const char* dg_part_last_error(const dg_part* t) { return t ? t->err.c_str() : ""; }
+
+extern "C" void dg_part_destroy(dg_part* t) { delete t; }
