@@ -295,11 +295,13 @@ class Oracle:
         P = np.linalg.solve(mass, (Wm[:, None] * psi_r).T)
         return np.einsum("ab,evb->eva", P, T)
 
-    def tck(self, U, dt, reduce_every=2, return_terms=False):
+    def tck(self, U, dt, reduce_every=2, return_terms=False, first=None):
         """Taylor-Cauchy-Kowalevski predictor Ubar (GL basis) of Eq. (6):
         sum_{j=0}^{k+1} dt^{j+1}/(j+1)! T_j, T_j = -S T_{j-1} by collocation
         at the current Gauss set, the set shrunk by ``reduce_every`` points
-        after every ``reduce_every``-th derivative (0 = never)."""
+        after every ``reduce_every``-th derivative (0 = never).  ``first``
+        (GL basis) replaces T_1 = -S U, as HDG-ADER does with the DG
+        derivative (Eq. hdg-ader)."""
         U = np.asarray(U, float)
         n = self.n
         T = np.einsum("qa,eva->evq", self.Phi, U)              # values in G
@@ -310,13 +312,16 @@ class Oracle:
             if m <= 0:
                 break
             t = self._tck_level(m)
-            gp = np.einsum("dqb,eb->edq", t["D"], T[:, 0])
-            gv = np.einsum("dqb,eib->eidq", t["D"], T[:, 1:])
-            dp = np.einsum("eqdi,edq->eiq", t["Jinv"], gp)
-            divv = np.einsum("eqdi,eidq->eq", t["Jinv"], gv)
-            Tn = np.empty((self.E, 4, m ** 3))
-            Tn[:, 1:] = -dp / t["rho"][:, None, :]
-            Tn[:, 0] = -t["rho"] * t["c"] ** 2 * divv
+            if j == 1 and first is not None:
+                Tn = np.einsum("qa,eva->evq", self.Phi, np.asarray(first, float))
+            else:
+                gp = np.einsum("dqb,eb->edq", t["D"], T[:, 0])
+                gv = np.einsum("dqb,eib->eidq", t["D"], T[:, 1:])
+                dp = np.einsum("eqdi,edq->eiq", t["Jinv"], gp)
+                divv = np.einsum("eqdi,eidq->eq", t["Jinv"], gv)
+                Tn = np.empty((self.E, 4, m ** 3))
+                Tn[:, 1:] = -dp / t["rho"][:, None, :]
+                Tn[:, 0] = -t["rho"] * t["c"] ** 2 * divv
             if reduce_every > 0 and j % reduce_every == 0:
                 if m - reduce_every >= 1:
                     Tn = self._project(Tn, m, reduce_every)
@@ -333,6 +338,17 @@ class Oracle:
         if return_terms:
             return Ubar_gl, terms
         return Ubar_gl
+
+    def hdg_ader(self, U, dt, nsteps, reduce_every=2):
+        """nsteps of HDG-ADER (Eq. hdg-ader): with W = -M^-1 K U the DG
+        derivative, U <- U + dt W - M^-1 K sum_{j=1}^{k+1} dt^{j+1}/(j+1)!
+        (-S)^{j-1} W.  Since -M^-1 K is linear this is U + R(Ubar) with the
+        predictor's T_1 replaced by W."""
+        U = np.array(U, float, copy=True)
+        for _ in range(nsteps):
+            W = self.apply(U)
+            U = U + self.apply(self.tck(U, dt, reduce_every, first=W))
+        return U
 
     def ader(self, U, dt, nsteps, reduce_every=2, callback=None):
         """nsteps of ADER: U <- U + R(Ubar), Eq. (6)."""

@@ -144,3 +144,15 @@ def paper_kernel_calls(k, d=3):
     """(cell, face) tensor-kernel calls of M^-1, K and TCK (Table kernel-calls)."""
     return {"mass": (2 * d, 0), "stiffness": (d * d + 4 * d, 4 * (d * d - d)),
             "tck": (2 * d + d * (k - 1), 0)}
+
+
+def paper_scheme_ops(k, d=3, stages=5):
+    """Operations per element and step of the paper's model (Sec. 4.1):
+    C_RK = s (C_M + C_K) and C_ADER = 2 C_M + C_K + C_TCK, where a cell
+    kernel call costs C_tensorial(d) and a face kernel call C_tensorial(d-1)
+    (Table kernel-calls)."""
+    C, F = c_tensorial(k, d), c_tensorial(k, d - 1)
+    calls = paper_kernel_calls(k, d)
+    cost = {name: cf[0] * C + cf[1] * F for name, cf in calls.items()}
+    return {"rk": stages * (cost["mass"] + cost["stiffness"]),
+            "ader": 2 * cost["mass"] + cost["stiffness"] + cost["tck"], **cost}

@@ -1,5 +1,5 @@
 """The GPU schemes' critical Courant numbers (found by simulation, as the
-paper's Sec. 4.6 does) agree with the oracle's Bloch-wave analysis and with
+paper's Sec. 4.7 does) agree with the oracle's Bloch-wave analysis and with
 the paper's Table crit-Cr (3D, k = 1)."""
 import pytest
 

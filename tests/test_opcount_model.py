@@ -1,0 +1,30 @@
+"""The paper's operation-count model (Sec. 4.1) as restated in opcount.py,
+checked against what the paper states about it."""
+from paper_1805_03981_gb300 import opcount
+
+
+def test_c_tensorial_even_odd_halves_the_plain_product():
+    # the even-odd decomposition cuts a 1D matrix-vector product of (k+1)^2
+    # multiply-adds (2 (k+1)^2 operations) to about one half
+    for k in range(3, 13):
+        plain = 2 * (k + 1) ** 2
+        assert 0.45 < opcount.c_tensorial(k, 1) / plain < 0.75, k
+    # one kernel on a delta-dimensional domain runs over (k+1)^(delta-1) lines
+    for k in range(1, 13):
+        assert opcount.c_tensorial(k, 3) == opcount.c_tensorial(k, 1) * (k + 1) ** 2
+
+
+def test_ader_fewer_operations_than_five_stage_rk():
+    # "ADER involves fewer arithmetic operations for all considered
+    # polynomial degrees k in {1..12} for both d = 2, 3" (Sec. 4.1)
+    for d in (2, 3):
+        for k in range(1, 13):
+            ops = opcount.paper_scheme_ops(k, d)
+            assert ops["ader"] < ops["rk"], (d, k)
+
+
+def test_predictor_share_grows_with_degree():
+    # the predictor carries the extra dependency on k: its share of an ADER
+    # step grows with the degree
+    shares = [opcount.paper_scheme_ops(k)["tck"] / opcount.paper_scheme_ops(k)["ader"] for k in range(1, 13)]
+    assert all(b > a for a, b in zip(shares, shares[1:]))

@@ -1,5 +1,5 @@
 """Pin against the paper's printed critical Courant numbers (Table crit-Cr,
-Sec. 4.6, 3D Cartesian mesh), stored in tests/golden/crit_courant_3d.txt.
+Sec. 4.7, 3D Cartesian mesh), stored in tests/golden/crit_courant_3d.txt.
 
 ADER (Eq. (6) with Algorithm 3) is compared at 15%.  The paper's LSRK4(5) is
 a different 2R scheme from the 2N scheme built here, so LSRK is held to the

@@ -7,7 +7,7 @@
   coefficients every Taylor term T_j equals (-S)^j u computed symbolically;
   with degree reduction this holds for total-degree data.
 * Full schemes: convergence to the analytic standing wave at rate k+1 in
-  space (LSRK at a small step) and in space-time (ADER, Sec. 4.6).
+  space (LSRK at a small step) and in space-time (ADER, Sec. 4.7).
 * Energy: upwind decays monotonically step by step.
 """
 import math
