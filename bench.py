@@ -310,8 +310,8 @@ def _l2_pressure_error(U, xnodes, exact, t, k):
 def time_to_accuracy_bench(args, dgw, torch):
     """Accuracy against GPU time (Sec. 4.5, Fig. solv-acc-RK-vs-ADER, in 3D):
     the standing wave on periodic Cartesian meshes of growing size, degrees
-    k = 1, 4, 7, LSRK(5,4) and ADER (order k+1, reduction every 2nd
-    derivative), at Cr = 0.1 and at 0.9 times each method's critical Courant
+    k = 1, 4, 7, LSRK(5,4), ADER and HDG-ADER (order k+1, reduction every
+    2nd derivative), at Cr = 0.1 and at 0.9 times each method's critical Courant
     number (measured on the GPU first), to t_end = 1; relative L2 pressure
     error at t_end against the device time of the solve."""
     import synth
@@ -322,14 +322,14 @@ def time_to_accuracy_bench(args, dgw, torch):
     t_end = args.t_end
     rows, crit = [], {}
     for k in (int(x) for x in args.kset.split(",")):
-        for method in ("lsrk", "ader"):
+        for method in ("lsrk", "ader", "hdg_ader"):
             crit[(k, method)] = crit_courant.critical(k, method)
         for N in sizes[k]:
             cfg = synth.configs.standing_wave(N=N, k=k)
             s = dgw.Solver(cfg["mesh"], k, prec, cfg["alpha"], cfg["rho"], cfg["c"])
             s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
             dof = 4 * (k + 1) ** 3 * N ** 3
-            for method in ("lsrk", "ader"):
+            for method in ("lsrk", "ader", "hdg_ader"):
                 for label, cr in (("0.1", 0.1), ("0.9crit", 0.9 * crit[(k, method)])):
                     dt_max = synth.configs.dt_from_courant(cr, cfg["mesh"]["h"], 1.0, k)
                     steps = int(np.ceil(t_end / dt_max))
@@ -340,6 +340,8 @@ def time_to_accuracy_bench(args, dgw, torch):
                     ev0.record()
                     if method == "lsrk":
                         s.step_lsrk(U, dt, steps)
+                    elif method == "hdg_ader":
+                        s.step_hdg_ader(U, dt, steps, 2)
                     else:
                         s.step_ader(U, dt, steps, 2)
                     ev1.record()

@@ -154,6 +154,18 @@ int dg_step_ader(dg_ctx* ctx, void* U, double dt, int32_t nsteps,
                  int32_t reduce_every, uintptr_t stream);
 
 /*
+ * nsteps of HDG-ADER (Sec. 2.4, Eq. hdg-ader): every step first evaluates the
+ * DG derivative W = -M^-1 K U (one more operator application), which takes
+ * the place of the predictor's first Taylor term -S U; then
+ * U <- U - M^-1 K Ubar as in dg_step_ader. The HDG flux with tau = 1/(rho c)
+ * is the upwind flux of this build (flux_alpha = 1) where rho c is continuous.
+ * The superconvergent postprocessing the paper refers to is not part of it.
+ * Arguments, errors and the storage basis as for dg_step_ader.
+ */
+int dg_step_hdg_ader(dg_ctx* ctx, void* U, double dt, int32_t nsteps,
+                     int32_t reduce_every, uintptr_t stream);
+
+/*
  * Representation of the state inside dg_step_lsrk and dg_step_ader (the
  * state passed in and out is always GL nodal values):
  *  DG_BASIS_GL  the paper's scheme: GL storage, so that a face needs only the
@@ -316,7 +328,7 @@ const char* dg_batch_last_error(const dg_batch* b);
 void dg_batch_destroy(dg_batch* b);
 
 /*
- * Partitioned solve (the data-parallel split of one solve, Sec. 4.6: the
+ * Partitioned solve (the data-parallel split of one solve, Sec. 4.1, 4.8: the
  * operator needs the neighbours' data across a face, the predictor none).
  * A part is a context set up on its owned elements followed by ghost
  * elements: copies of the neighbours of owned elements that other parts own.
@@ -352,6 +364,8 @@ int dg_part_create(dg_ctx* const* ctxs, void* const* U, int32_t P, const int32_t
                    const int32_t* ghost_src_part, const int32_t* ghost_src_elem, dg_part** out);
 int dg_part_step_lsrk(dg_part* t, double dt, int32_t nsteps, uintptr_t stream);
 int dg_part_step_ader(dg_part* t, double dt, int32_t nsteps, int32_t reduce_every, uintptr_t stream);
+/* HDG-ADER on the parts: two exchanges per step (the state, then the predictor). */
+int dg_part_step_hdg_ader(dg_part* t, double dt, int32_t nsteps, int32_t reduce_every, uintptr_t stream);
 int dg_part_exchange(dg_part* t, uintptr_t stream);
 int dg_part_info(const dg_part* t, int32_t* n_parts, int32_t* n_ghost_total, uint64_t* exchanges);
 const char* dg_part_last_error(const dg_part* t);

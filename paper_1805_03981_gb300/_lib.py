@@ -19,7 +19,7 @@ EXPORTED_SYMBOLS = [
     "dg_request_bytes", "dg_mesh_setup_coef", "dg_set_basis", "dg_get_basis", "dg_check_device",
     "dg_is_affine", "dg_change_basis", "dg_batch_set_basis", "dg_batch_convert",
     "dg_set_owned", "dg_part_create", "dg_part_step_lsrk", "dg_part_step_ader", "dg_part_exchange",
-    "dg_part_info", "dg_part_last_error", "dg_part_destroy",
+    "dg_part_info", "dg_part_last_error", "dg_part_destroy", "dg_step_hdg_ader", "dg_part_step_hdg_ader",
 ]
 BASIS_GL, BASIS_G = 0, 1
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
@@ -128,6 +128,8 @@ def load_library():
         "dg_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
         "dg_last_error": (C.c_char_p, [vp]),
         "dg_set_owned": (C.c_int, [vp, C.c_int32]),
+        "dg_step_hdg_ader": (C.c_int, [vp, vp, C.c_double, C.c_int32, C.c_int32, st]),
+        "dg_part_step_hdg_ader": (C.c_int, [vp, C.c_double, C.c_int32, C.c_int32, st]),
         "dg_part_create": (C.c_int, [C.POINTER(vp), C.POINTER(vp), C.c_int32, C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(vp)]),
         "dg_part_step_lsrk": (C.c_int, [vp, C.c_double, C.c_int32, st]),
@@ -241,6 +243,12 @@ class Solver:
     def step_ader(self, U, dt, nsteps, reduce_every=2, stream=None):
         self._check(self.lib.dg_step_ader(self.ctx, self._state(U), float(dt), int(nsteps),
                                           int(reduce_every), _stream(stream)))
+        return U
+
+    def step_hdg_ader(self, U, dt, nsteps, reduce_every=2, stream=None):
+        """HDG-ADER steps (Eq. hdg-ader), U updated in place."""
+        self._check(self.lib.dg_step_hdg_ader(self.ctx, self._state(U), float(dt), int(nsteps),
+                                              int(reduce_every), _stream(stream)))
         return U
 
     def tck(self, U, dt, reduce_every=2, out=None, stream=None):

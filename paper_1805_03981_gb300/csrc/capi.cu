@@ -106,6 +106,7 @@ struct dg_ctx {
   void* U3 = nullptr;
   void* dU = nullptr;    // LSRK register
   void* Ubar = nullptr;  // ADER predictor
+  void* Wd = nullptr;    // HDG-ADER: the DG derivative of the state
   void* Uh = nullptr;    // state for dg_solve_host
   double* partial = nullptr;
   int partial_cap = 0;
@@ -401,9 +402,10 @@ int change_basis(dg_ctx* ctx, void* U, int to_g, cudaStream_t st) {
 }
 
 int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaStream_t st,
-               bool gbasis = false) {
+               bool gbasis = false, const void* W = nullptr) {
   TckParams p;
   std::memset(&p, 0, sizeof(p));
+  p.W = W;
   p.gmode = gbasis ? 1 : 0;
   p.aff = ctx->affine ? 1 : 0;
   p.geoKT = ctx->geoKT;
@@ -505,14 +507,23 @@ int lsrk_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st) {
   return DG_OK;
 }
 
-int ader_steps(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_t st) {
+// hdg: HDG-ADER (Eq. hdg-ader): each step first evaluates the DG derivative
+// W = -M^-1 K U, which takes the place of the predictor's first term -S U.
+int ader_steps(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_t st, bool hdg = false) {
   int rc;
   if ((rc = ensure(ctx, &ctx->Ubar, "ADER predictor"))) return rc;
+  if (hdg && (rc = ensure(ctx, &ctx->Wd, "HDG-ADER derivative"))) return rc;
   OpParams p = op_params(ctx);
   const bool g = ctx->basis == DG_BASIS_G && nsteps > 0;
   if (g && (rc = change_basis(ctx, U, 1, st))) return rc;
   for (int s = 0; s < nsteps; ++s) {
-    if ((rc = launch_tck(ctx, U, ctx->Ubar, dt, red, st, g))) return rc;
+    if (hdg) {
+      OpParams q = op_params(ctx);
+      q.U = U;
+      q.out = ctx->Wd;
+      if ((rc = launch_op(ctx, q, EPI_WRITE, st, g))) return rc;
+    }
+    if ((rc = launch_tck(ctx, U, ctx->Ubar, dt, red, st, g, hdg ? ctx->Wd : nullptr))) return rc;
     p.U = ctx->Ubar;
     p.Uadd = U;
     p.out = U;
@@ -761,6 +772,18 @@ int dg_step_ader(dg_ctx* ctx, void* U, double dt, int32_t nsteps, int32_t red, u
   DeviceGuard g(ctx->dev);
   if ((rc = ensure_levels(ctx, red, S(stream)))) return rc;
   return ader_steps(ctx, U, dt, nsteps, red, S(stream));
+}
+
+int dg_step_hdg_ader(dg_ctx* ctx, void* U, double dt, int32_t nsteps, int32_t red, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  int rc;
+  if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0)
+    return ctx->fail(DG_EINVAL, "need dt > 0 and nsteps >= 0");
+  if ((rc = check_red(ctx, red))) return rc;
+  DeviceGuard g(ctx->dev);
+  if ((rc = ensure_levels(ctx, red, S(stream)))) return rc;
+  return ader_steps(ctx, U, dt, nsteps, red, S(stream), true);
 }
 
 int dg_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int32_t red, uintptr_t stream) {
@@ -1505,7 +1528,7 @@ extern "C" void dg_batch_destroy(dg_batch* b) { delete b; }
 // n_owned elements are stepped and whose remaining elements are ghost copies
 // of neighbours owned by other parts.  Before every operator application the
 // ghost tiles of its input are refreshed from their owners (five exchanges
-// per LSRK step, one per ADER step: the predictor is element-local, Sec. 4.6).
+// per LSRK step, one per ADER step: the predictor is element-local, Sec. 4.1, 4.8).
 // All parts live on this device; the exchange is one gather kernel.
 // ---------------------------------------------------------------------------
 extern "C" int dg_set_owned(dg_ctx* ctx, int32_t n_owned) {
@@ -1614,12 +1637,13 @@ int part_lsrk(dg_part* t, double dt, int nsteps, cudaStream_t st) {
   return DG_OK;
 }
 
-int part_ader(dg_part* t, double dt, int nsteps, int red, cudaStream_t st) {
+int part_ader(dg_part* t, double dt, int nsteps, int red, cudaStream_t st, bool hdg = false) {
   int rc;
   const int P = t->P;
   for (int i = 0; i < P; ++i) {
     dg_ctx* c = t->c[i];
-    if ((rc = ensure(c, &c->Ubar, "ADER predictor")) || (rc = ensure_levels(c, red, st)))
+    if ((rc = ensure(c, &c->Ubar, "ADER predictor")) || (rc = ensure_levels(c, red, st)) ||
+        (hdg && (rc = ensure(c, &c->Wd, "HDG-ADER derivative"))))
       return t->fail(rc, c->err.c_str());
   }
   const bool g = t->c[0]->basis == DG_BASIS_G && nsteps > 0;
@@ -1629,8 +1653,19 @@ int part_ader(dg_part* t, double dt, int nsteps, int red, cudaStream_t st) {
   std::vector<void*> bar(P);
   for (int i = 0; i < P; ++i) bar[i] = t->c[i]->Ubar;
   for (int s = 0; s < nsteps; ++s) {
+    if (hdg) {  // the DG derivative needs the state's ghosts
+      if ((rc = part_exchange(t, t->U.data(), st))) return rc;
+      for (int i = 0; i < P; ++i) {
+        dg_ctx* c = t->c[i];
+        OpParams q = op_params(c);
+        q.U = t->U[i];
+        q.out = c->Wd;
+        if ((rc = launch_op(c, q, EPI_WRITE, st, g))) return t->fail(rc, c->err.c_str());
+      }
+    }
     for (int i = 0; i < P; ++i)
-      if ((rc = launch_tck(t->c[i], t->U[i], t->c[i]->Ubar, dt, red, st, g))) return t->fail(rc, t->c[i]->err.c_str());
+      if ((rc = launch_tck(t->c[i], t->U[i], t->c[i]->Ubar, dt, red, st, g, hdg ? t->c[i]->Wd : nullptr)))
+        return t->fail(rc, t->c[i]->err.c_str());
     if ((rc = part_exchange(t, bar.data(), st))) return rc;
     for (int i = 0; i < P; ++i) {
       dg_ctx* c = t->c[i];
@@ -1739,6 +1774,14 @@ extern "C" int dg_part_step_ader(dg_part* t, double dt, int32_t nsteps, int32_t 
   if (red < 0 || red > 3) return t->fail(DG_EUNSUPPORTED, "reduce_every must be 0, 1, 2 or 3");
   DeviceGuard g(t->dev);
   return part_ader(t, dt, nsteps, red, S(stream));
+}
+
+extern "C" int dg_part_step_hdg_ader(dg_part* t, double dt, int32_t nsteps, int32_t red, uintptr_t stream) {
+  if (!t) return DG_EINVAL;
+  if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return t->fail(DG_EINVAL, "need dt > 0 and nsteps >= 0");
+  if (red < 0 || red > 3) return t->fail(DG_EUNSUPPORTED, "reduce_every must be 0, 1, 2 or 3");
+  DeviceGuard g(t->dev);
+  return part_ader(t, dt, nsteps, red, S(stream), true);
 }
 
 extern "C" int dg_part_info(const dg_part* t, int32_t* n_parts, int32_t* n_ghost_total, uint64_t* exchanges) {

@@ -1073,6 +1073,7 @@ struct TckParams {
   int aff;    // 1: affine elements with constant coefficients (geoKT)
   int geo_step;  // geoT holds the Gauss sets m = n, n - geo_step, ... >= 2 (1 or 2)
   const void* geoKT;  // [E][DG_AFF_TCK]: J^-1 (9), -rho c^2, -1/rho
+  const void* W;      // HDG-ADER: T_1 = W (the DG derivative, same basis as U) instead of -S U; else null
 };
 
 // m-point levels visited with reduction every RED-th derivative (RED = 0:
@@ -1319,6 +1320,23 @@ __device__ __forceinline__ void tck_block(const TckParams& p, const int e0, cons
   int m = N, goff = 0, aoff = 0;  // goff: this set's geometry; aoff: its accumulator
 #pragma unroll 1
   for (int j = 1; j <= N; ++j) {
+    if (j == 1 && p.W) {  // HDG-ADER (Eq. hdg-ader): the DG derivative in place of -S U
+      const Real* __restrict__ Wg = static_cast<const Real*>(p.W);
+      for (int i = T; i < ne * 4 * N3; i += NT) {
+        const int l = i / (4 * N3);
+        nxt[l * SE + (i - l * 4 * N3)] = Wg[(size_t)e0 * 4 * N3 + i];
+      }
+      __syncthreads();
+      if (!p.gmode) {
+        Real* w = nxt + le * SE;
+        contract_tile<Real, 2, N, N, N, N, OFF_V(N), N3, N3>(w, w, t, N2);
+        __syncthreads();
+        contract_tile<Real, 0, N, N, N, N, OFF_V(N), N3, N3>(w, w, t, N2);
+        __syncthreads();
+        contract_tile<Real, 1, N, N, N, N, OFF_V(N), N3, N3>(w, w, t, N2);
+        __syncthreads();
+      }
+    } else {
     // derivative at the current m (T_{j-1} in cur, field stride N3)
     switch (m) {
 #define DG_TCK_DERIV(MM)                                                                  \
@@ -1340,6 +1358,7 @@ __device__ __forceinline__ void tck_block(const TckParams& p, const int e0, cons
         }
         __syncthreads();
         break;
+    }
     }
     if (RED > 0 && (j % RED) == 0) {
       if (m - RED < 1) break;  // projected to degree < 0: T_j = 0, stop

@@ -5,7 +5,7 @@ that neighbour an owned element across a face and belong to another part.
 The operator of an owned element reads its neighbours' states across every
 face (Sec. 2.4), so before each operator application the ghosts of its input
 are refreshed from their owners; the ADER predictor is element-local, so an
-ADER step needs one such exchange and an LSRK step five (Sec. 4.6).
+ADER step needs one such exchange and an LSRK step five (Sec. 4.1, 4.8).
 
 ``split`` is host logic only (numpy): the parts' local meshes and the
 exchange plan.  ``Partitioned`` runs all parts on this device through the
@@ -142,6 +142,10 @@ class Partitioned:
     def step_ader(self, dt, nsteps, reduce_every=2, stream=None):
         self._check(self.lib.dg_part_step_ader(self.t, float(dt), int(nsteps), int(reduce_every),
                                                _lib._stream(stream)))
+
+    def step_hdg_ader(self, dt, nsteps, reduce_every=2, stream=None):
+        self._check(self.lib.dg_part_step_hdg_ader(self.t, float(dt), int(nsteps), int(reduce_every),
+                                                   _lib._stream(stream)))
 
     def exchange(self, stream=None):
         self._check(self.lib.dg_part_exchange(self.t, _lib._stream(stream)))
