@@ -17,3 +17,4 @@ Parity status per function is stated in each module's header.
 from .basis import (gauss_1d, gauss_lobatto_1d, lagrange_1d,  # noqa: F401
                     lagrange_deriv_1d, tensor_points)
 from .dg import Oracle, LSRK54_A, LSRK54_B  # noqa: F401
+from .dg2d import Oracle2D  # noqa: F401
