@@ -585,31 +585,30 @@ __device__ __forceinline__ void opg_block(const OpParams& p, const int e0, const
         r[fl][s] = sr[fl * N3 + base + N2 * s];
       }
     cell_face_dir<N, Real, 2, true>(u, r, gA, gF, snb, t, fmask);
+    // the residual of this z-line is final: the epilogue runs here, on the
+    // line's points (contiguous across the warp), with no shared-memory pass
+    Real* __restrict__ out = static_cast<Real*>(p.out);
+    const Real* __restrict__ Uadd = static_cast<const Real*>(p.Uadd);
+    Real* __restrict__ dU = static_cast<Real*>(p.dU);
+    const Real cA = (Real)p.cA, cB = (Real)p.cB, dt = (Real)p.dt;
+    const size_t g0 = (size_t)e * 4 * N3 + base;
 #pragma unroll
     for (int s = 0; s < N; ++s) {
       const Real mp = __ldg(gM + base + N2 * s), mvv = __ldg(gM + N3 + base + N2 * s);
-      sr[base + N2 * s] = r[0][s] * mp;
 #pragma unroll
-      for (int fl = 1; fl < 4; ++fl) sr[fl * N3 + base + N2 * s] = r[fl][s] * mvv;
-    }
-  }
-  __syncthreads();
-  Real* __restrict__ out = static_cast<Real*>(p.out);
-  const Real* __restrict__ Uadd = static_cast<const Real*>(p.Uadd);
-  Real* __restrict__ dU = static_cast<Real*>(p.dU);
-  const Real cA = (Real)p.cA, cB = (Real)p.cB, dt = (Real)p.dt;
-  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
-    const int l = i / (4 * N3);
-    const Real R = sm[l * SE + 4 * N3 + (i - l * 4 * N3)];
-    const size_t g = (size_t)e0 * 4 * N3 + i;
-    if (EPI == EPI_WRITE) {
-      out[g] = R;
-    } else if (EPI == EPI_ADD) {
-      out[g] = Uadd[g] + R;
-    } else {
-      const Real d = p.first ? dt * R : fma(cA, dU[g], dt * R);
-      dU[g] = d;
-      out[g] = fma(cB, d, Uadd[g]);
+      for (int fl = 0; fl < 4; ++fl) {
+        const Real R = r[fl][s] * (fl == 0 ? mp : mvv);
+        const size_t g = g0 + fl * N3 + N2 * s;
+        if (EPI == EPI_WRITE) {
+          out[g] = R;
+        } else if (EPI == EPI_ADD) {
+          out[g] = Uadd[g] + R;
+        } else {
+          const Real d = p.first ? dt * R : fma(cA, dU[g], dt * R);
+          dU[g] = d;
+          out[g] = fma(cB, d, Uadd[g]);
+        }
+      }
     }
   }
 }
@@ -741,33 +740,35 @@ __device__ __forceinline__ void opgs_block(const OpParams& p, const int e0, cons
         r[fl][s] = sr[fl * N3 + base + N2 * s];
       }
     cell_face_dir<N, Real, 2, true, true>(u, r, gA, gF, snb, t, fmask);
+    // the residual of this z-line is final: the epilogue runs here, on the
+    // line's points (contiguous across the warp), with no shared-memory pass
+    Real* __restrict__ out = static_cast<Real*>(p.out);
+    Real* __restrict__ dU = static_cast<Real*>(p.dU);
+    const Real cA = (Real)p.cA, cB = (Real)p.cB, dt = (Real)p.dt;
+    const Real* sx = sxA + le * 4 * N3;
+    const size_t g0 = (size_t)e * 4 * N3 + base;
 #pragma unroll
     for (int s = 0; s < N; ++s) {
       const Real mp = gM[base + N2 * s], mvv = gM[N3 + base + N2 * s];
-      sr[base + N2 * s] = r[0][s] * mp;
 #pragma unroll
-      for (int fl = 1; fl < 4; ++fl) sr[fl * N3 + base + N2 * s] = r[fl][s] * mvv;
+      for (int fl = 0; fl < 4; ++fl) {
+        const Real R = r[fl][s] * (fl == 0 ? mp : mvv);
+        const int i = fl * N3 + base + N2 * s;
+        const size_t g = g0 + fl * N3 + N2 * s;
+        if (EPI == EPI_WRITE) {
+          out[g] = R;
+        } else if (EPI == EPI_ADD) {
+          out[g] = sx[i] + R;
+        } else {  // LSRK: the stage input is the staged state
+          const Real d = p.first ? dt * R : fma(cA, sx[i], dt * R);
+          dU[g] = d;
+          out[g] = fma(cB, d, su[i]);
+        }
+      }
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) mbar_inval(&bar);
-  if (!ok) return;
-  Real* __restrict__ out = static_cast<Real*>(p.out);
-  Real* __restrict__ dU = static_cast<Real*>(p.dU);
-  const Real cA = (Real)p.cA, cB = (Real)p.cB, dt = (Real)p.dt;
-  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
-    const Real R = srA[i];
-    const size_t g = (size_t)e0 * 4 * N3 + i;
-    if (EPI == EPI_WRITE) {
-      out[g] = R;
-    } else if (EPI == EPI_ADD) {
-      out[g] = sxA[i] + R;
-    } else {  // LSRK: the stage input is the staged state
-      const Real d = p.first ? dt * R : fma(cA, sxA[i], dt * R);
-      dU[g] = d;
-      out[g] = fma(cB, d, suA[i]);
-    }
-  }
 }
 
 template <int N, typename Real, int EPI>
@@ -985,36 +986,39 @@ __device__ __forceinline__ void opga_block(const OpParams& p, const int e0, cons
       }
     cell_face_dir_aff<N, Real, 2, true, STAGE>(u, r, gK, wab, iwab, snb, t, fmask);
     const Real mpab = geo_ld<Real, STAGE>(gK + 9) * iwab, mvab = geo_ld<Real, STAGE>(gK + 10) * iwab;
+    // the residual of this z-line is final: the epilogue runs here, on the
+    // line's points (across the warp the lines' points are contiguous in
+    // memory), without a round trip through shared memory
+    Real* __restrict__ out = static_cast<Real*>(p.out);
+    Real* __restrict__ dU = static_cast<Real*>(p.dU);
+    const Real* __restrict__ Uadd = static_cast<const Real*>(p.Uadd);
+    const Real cA = (Real)p.cA, cB = (Real)p.cB, dt = (Real)p.dt;
+    const Real* sx = sxA + le * 4 * N3;
+    const size_t g0 = (size_t)e * 4 * N3 + base;
 #pragma unroll
     for (int s = 0; s < N; ++s) {
       const Real iw = tab<Real>(OFF_IW(N) + s);
       const Real mp = mpab * iw, mvv = mvab * iw;
-      sr[base + N2 * s] = r[0][s] * mp;
 #pragma unroll
-      for (int fl = 1; fl < 4; ++fl) sr[fl * N3 + base + N2 * s] = r[fl][s] * mvv;
+      for (int fl = 0; fl < 4; ++fl) {
+        const Real R = r[fl][s] * (fl == 0 ? mp : mvv);
+        const int i = fl * N3 + base + N2 * s;
+        const size_t g = g0 + fl * N3 + N2 * s;
+        if (EPI == EPI_WRITE) {
+          out[g] = R;
+        } else if (EPI == EPI_ADD) {
+          out[g] = (STAGE ? sx[i] : Uadd[g]) + R;
+        } else {
+          const Real d = p.first ? dt * R : fma(cA, STAGE ? sx[i] : dU[g], dt * R);
+          dU[g] = d;
+          out[g] = fma(cB, d, su[i]);
+        }
+      }
     }
   }
-  __syncthreads();
   if constexpr (STAGE) {
+    __syncthreads();
     if (threadIdx.x == 0) mbar_inval(&bar);
-  }
-  if (!ok) return;
-  Real* __restrict__ out = static_cast<Real*>(p.out);
-  Real* __restrict__ dU = static_cast<Real*>(p.dU);
-  const Real* __restrict__ Uadd = static_cast<const Real*>(p.Uadd);
-  const Real cA = (Real)p.cA, cB = (Real)p.cB, dt = (Real)p.dt;
-  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) {
-    const Real R = srA[i];
-    const size_t g = (size_t)e0 * 4 * N3 + i;
-    if (EPI == EPI_WRITE) {
-      out[g] = R;
-    } else if (EPI == EPI_ADD) {
-      out[g] = (STAGE ? sxA[i] : Uadd[g]) + R;
-    } else {
-      const Real d = p.first ? dt * R : fma(cA, STAGE ? sxA[i] : dU[g], dt * R);
-      dU[g] = d;
-      out[g] = fma(cB, d, suA[i]);
-    }
   }
 }
 

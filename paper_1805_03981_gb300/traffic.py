@@ -5,7 +5,7 @@ The traffic of a launch is ``dram__bytes_read.sum + dram__bytes_write.sum``
 ``profiles/dram_traffic.txt``; each row names the workload, the precision,
 the size, the degree, the storage basis, the kernel kind and that kernel's
 elements per block it was taken on, and the table carries a SHA-256 digest of
-the CUDA sources and build script it was taken with.  ``lookup`` returns a
+the kernel sources and build script it was taken with (DIGEST_FILES).  ``lookup`` returns a
 figure only when the digest of the sources as they are now equals the
 table's and a row matches the launch configuration exactly: once a kernel
 changes, its old counters no longer describe it.
@@ -35,12 +35,21 @@ NKEY = 7
 _EPI_KIND = {0: "operator", 1: "lsrk_stage", 2: "ader_update"}
 
 
+# The sources that determine the code of the recorded kernels (the 3D operator
+# and predictor launched one solve at a time) and their per-element data: the
+# kernel bodies, their instantiation units, the 1D tables, the geometry set-up
+# and the build flags.  The launch configuration that matters is part of each
+# row (elements per block).
+DIGEST_FILES = ("dg_kernels.cuh", "kern_inst.cuh", "kern_f64_lo.cu", "kern_f64_hi.cu", "kern_f32_lo.cu",
+                "kern_f32_hi.cu", "kern_tck_odd_f64.cu", "kern_tck_odd_f32.cu", "tables.h", "tables.cpp",
+                "setup.cu")
+
+
 def sources_digest():
-    """SHA-256 over every file of csrc/ (sorted by name) and build.py."""
+    """SHA-256 over the kernel-determining sources (DIGEST_FILES) and build.py."""
     h = hashlib.sha256()
     csrc = os.path.join(PKG, "csrc")
-    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc)
-                   if f.endswith((".cu", ".cuh", ".h", ".cpp")))
+    files = [os.path.join(csrc, f) for f in DIGEST_FILES]
     files.append(os.path.join(PKG, "build.py"))
     for path in files:
         h.update(os.path.basename(path).encode())
