@@ -63,7 +63,7 @@ def parse():
                     help="state inside the steppers: g = Gauss-point values (default), gl = the paper's storage")
     ap.add_argument("--workload", default="curved_pulse",
                     choices=["curved_pulse", "plane_wave", "batched", "served", "reduction",
-                             "time_to_accuracy"])
+                             "time_to_accuracy", "time_to_accuracy_2d"])
     ap.add_argument("--lam", type=float, default=20.0, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="served: arrival window, seconds")
     ap.add_argument("--nrange", default="8,24", help="served: elements per axis, min,max")
@@ -360,6 +360,72 @@ def time_to_accuracy_bench(args, dgw, torch):
     return 0
 
 
+def _l2_pressure_error_2d(U, xnodes, exact, t, k):
+    """The 2D counterpart of _l2_pressure_error (equal affine elements)."""
+    from numpy.polynomial import legendre as leg
+    n, m = k + 1, k + 3
+    xq, wq = leg.leggauss(m)
+    xgl = np.concatenate(([-1.0], np.sort(np.real(leg.legroots(leg.legder([0] * (n - 1) + [1])))), [1.0])) \
+        if n > 2 else np.array([-1.0, 1.0])
+    L = np.ones((m, n))
+    for a in range(n):
+        for b in range(n):
+            if b != a:
+                L[:, a] *= (xq - xgl[b]) / (xgl[a] - xgl[b])
+    E = U.shape[0]
+    ph = np.einsum("qa,rb,eba->erq", L, L, U[:, 0].reshape(E, n, n)).reshape(E, -1)
+    Xq = np.einsum("qa,rb,ebai->erqi", L, L, xnodes.reshape(E, n, n, 2)).reshape(E, -1, 2)
+    w = np.einsum("a,b->ba", wq, wq).reshape(-1)
+    pe = exact(Xq, t)[..., 0]
+    return float(np.sqrt(np.sum(w * (ph - pe) ** 2) / np.sum(w * pe ** 2)))
+
+
+def time_to_accuracy_2d_bench(args, dgw, torch):
+    """The paper's time-versus-accuracy study in its own 2D setting (Sec. 4.7,
+    Fig. solv-acc-RK-vs-ADER): a seven-mode standing field on the periodic
+    unit square (stand-in for the paper's membrane), rho = c = 1, k = 1, 4,
+    7, LSRK(5,4) and ADER at Cr = 0.1 and at 0.9 of each method's critical
+    Courant number (measured on the GPU in 2D first), to t_end; relative L2
+    pressure error against the device time of the solve."""
+    from synth import mesh2d
+    from paper_1805_03981_gb300 import crit_courant
+    prec = dgw.DG_FP64 if args.prec == "fp64" else dgw.DG_FP32
+    sizes = {1: (8, 16, 32, 64, 128, 256, 512), 4: (4, 8, 16, 32, 64, 128), 7: (4, 8, 16, 32, 64)}
+    t_end = args.t_end
+    rows, crit = [], {}
+    for k in (int(x) for x in args.kset.split(",")):
+        for method in ("lsrk", "ader"):
+            crit[(k, method)] = crit_courant.critical(k, method, dim=2)
+        for N in sizes[k]:
+            cfg = mesh2d.standing_wave_config_2d(N=N, k=k, exact=mesh2d.membrane_modes_2d)
+            s = dgw.Solver2D(cfg["mesh"], k, prec, 1.0, cfg["rho"], cfg["c"])
+            dof = 3 * (k + 1) ** 2 * N * N
+            for method in ("lsrk", "ader"):
+                for label, cr in (("0.1", 0.1), ("0.9crit", 0.9 * crit[(k, method)])):
+                    steps = int(np.ceil(t_end / (cr * cfg["mesh"]["h"] / k ** 1.5)))
+                    dt = t_end / steps
+                    U = s.to_device(cfg["U0"])
+                    torch.cuda.synchronize()
+                    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    ev0.record()
+                    if method == "lsrk":
+                        s.step_lsrk(U, dt, steps)
+                    else:
+                        s.step_ader(U, dt, steps, 2)
+                    ev1.record()
+                    torch.cuda.synchronize()
+                    sec = ev0.elapsed_time(ev1) * 1e-3
+                    err = _l2_pressure_error_2d(U.double().cpu().numpy(), cfg["xnodes"], cfg["exact"], t_end, k)
+                    rows.append({"k": k, "N": N, "dof": dof, "method": method, "cr": label, "cr_value": cr,
+                                 "steps": steps, "gpu_seconds": sec, "l2_p": err, "dofs_per_s": dof * steps / sec})
+            s.close()
+    print(json.dumps({"time_to_accuracy_2d": {
+        "workload": "seven-mode standing field on the periodic unit square (N^2 quadrilaterals), rho = c = 1, "
+                    "upwind, t_end = %g, %s" % (t_end, args.prec.upper()),
+        "crit_courant_2d": {"%d/%s" % kk: v for kk, v in crit.items()}, "rows": rows}}))
+    return 0
+
+
 def reduction_bench(args, dgw, torch):
     """Degree reduction in the predictor every 0, 1, 2 or 3 derivatives
     (Sec. 3.3, Fig. reduc-comp) for k = 1..7 on the curved-pulse recipe at
@@ -622,6 +688,8 @@ def main():
         return reduction_bench(args, dgw, torch)
     if args.workload == "time_to_accuracy":
         return time_to_accuracy_bench(args, dgw, torch)
+    if args.workload == "time_to_accuracy_2d":
+        return time_to_accuracy_2d_bench(args, dgw, torch)
     N, k = args.size, args.k
     cfg = workload(N, k, args.workload)
     if args.accuracy:

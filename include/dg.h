@@ -110,6 +110,36 @@ int dg_mesh_setup_coef(const dg_mesh_desc* mesh, int k, int prec, double flux_al
                        const double* rho, const double* c, uintptr_t stream, dg_ctx** out);
 
 /*
+ * 2D meshes of quadrilaterals (the paper treats d = 2 and d = 3 alike,
+ * Sec. 2; its 2D experiments are in Sec. 4.7). Faces 0: xi = -1, 1: xi = +1,
+ * 2: eta = -1, 3: eta = +1; node (x, y) of an element at x + n y.
+ *   nodes    [E][(q+1)^2][2]  GL geometry nodes
+ *   nbr      [E][4]           neighbour across face f, -1 = wall
+ *   nbr_face [E][4]           the neighbour's face
+ *   orient   [E][4]           1 when the neighbour's face coordinate runs
+ *                             opposite to this element's, else 0; must be
+ *                             reciprocated
+ * rho, c: [E][(k+1)^2] at the GL solution nodes, or both NULL (= 1).
+ * States are [E][3][(k+1)^2] (p, v_x, v_y), GL nodal values, 16-byte
+ * aligned. A 2D context steps with the state in the Gauss basis (dg_set_basis
+ * accepts DG_BASIS_G only) and takes dg_apply_operator, dg_step_lsrk,
+ * dg_step_ader (reduce_every 0 or 2), dg_tck, dg_energy, dg_norms,
+ * dg_solve_host, dg_set_coefficients, dg_change_basis and the query and
+ * profiling calls. Batches, parts, the server, tuning, HDG-ADER and
+ * dg_energy_noalloc return DG_EUNSUPPORTED for it. Errors as dg_mesh_setup.
+ */
+typedef struct {
+  int32_t n_elem;
+  int32_t geom_degree;
+  const double* nodes;
+  const int32_t* nbr;
+  const int8_t* nbr_face;
+  const int8_t* orient;
+} dg_mesh2d_desc;
+int dg_mesh_setup_2d(const dg_mesh2d_desc* mesh, int k, int prec, double flux_alpha, const double* rho,
+                     const double* c, uintptr_t stream, dg_ctx** out);
+
+/*
  * Set the coefficients rho > 0 and c > 0 (Sec. 2, Eq. (1)) as host arrays
  * [E][(k+1)^3] of values at each element's GL solution nodes; each is the
  * degree-k polynomial through those values, and may jump between elements.

@@ -6,6 +6,6 @@ kernels; this package only marshals arrays, pointers and streams.  Importing
 it does not load the library; the first use does, and fails loudly if the
 library is missing.
 """
-from ._lib import (DGError, Solver, Batch, Server, load_library, library_path,  # noqa: F401
+from ._lib import (DGError, Solver, Solver2D, Batch, Server, load_library, library_path,  # noqa: F401
                    DG_FP64, DG_FP32, EXPORTED_SYMBOLS, KIND_LSRK, KIND_ADER, KIND_TCK,
                    BASIS_GL, BASIS_G)

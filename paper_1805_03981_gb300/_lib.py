@@ -20,6 +20,7 @@ EXPORTED_SYMBOLS = [
     "dg_is_affine", "dg_change_basis", "dg_batch_set_basis", "dg_batch_convert",
     "dg_set_owned", "dg_part_create", "dg_part_step_lsrk", "dg_part_step_ader", "dg_part_exchange",
     "dg_part_info", "dg_part_last_error", "dg_part_destroy", "dg_step_hdg_ader", "dg_part_step_hdg_ader",
+    "dg_mesh_setup_2d",
 ]
 BASIS_GL, BASIS_G = 0, 1
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
@@ -33,6 +34,12 @@ class DGError(RuntimeError):
 
 
 class MeshDesc(C.Structure):
+    _fields_ = [("n_elem", C.c_int32), ("geom_degree", C.c_int32),
+                ("nodes", C.POINTER(C.c_double)), ("nbr", C.POINTER(C.c_int32)),
+                ("nbr_face", C.POINTER(C.c_int8)), ("orient", C.POINTER(C.c_int8))]
+
+
+class MeshDesc2D(C.Structure):
     _fields_ = [("n_elem", C.c_int32), ("geom_degree", C.c_int32),
                 ("nodes", C.POINTER(C.c_double)), ("nbr", C.POINTER(C.c_int32)),
                 ("nbr_face", C.POINTER(C.c_int8)), ("orient", C.POINTER(C.c_int8))]
@@ -128,6 +135,8 @@ def load_library():
         "dg_profile_read": (C.c_int, [vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int]),
         "dg_last_error": (C.c_char_p, [vp]),
         "dg_set_owned": (C.c_int, [vp, C.c_int32]),
+        "dg_mesh_setup_2d": (C.c_int, [C.POINTER(MeshDesc2D), C.c_int, C.c_int, C.c_double,
+                                       C.POINTER(C.c_double), C.POINTER(C.c_double), st, C.POINTER(vp)]),
         "dg_step_hdg_ader": (C.c_int, [vp, vp, C.c_double, C.c_int32, C.c_int32, st]),
         "dg_part_step_hdg_ader": (C.c_int, [vp, C.c_double, C.c_int32, C.c_int32, st]),
         "dg_part_create": (C.c_int, [C.POINTER(vp), C.POINTER(vp), C.c_int32, C.POINTER(C.c_int32),
@@ -208,9 +217,14 @@ class Solver:
             pass
 
     # --- state helpers -------------------------------------------------
+    _FIELDS, _DIM = 4, 3
+
+    def _state_shape(self):
+        return (self.E, self._FIELDS, self.n ** self._DIM)
+
     def empty_state(self):
         import torch
-        return torch.empty((self.E, 4, self.n ** 3), dtype=self.dtype, device="cuda")
+        return torch.empty(self._state_shape(), dtype=self.dtype, device="cuda")
 
     def to_device(self, U):
         import torch
@@ -219,8 +233,9 @@ class Solver:
     def _state(self, U):
         import torch
         if not (isinstance(U, torch.Tensor) and U.is_cuda and U.dtype == self.dtype and U.is_contiguous()
-                and U.numel() == self.E * 4 * self.n ** 3):
-            raise DGError(-1, "state must be a contiguous CUDA tensor [E,4,(k+1)^3] of the solver dtype")
+                and U.numel() == int(np.prod(self._state_shape()))):
+            raise DGError(-1, "state must be a contiguous CUDA tensor %s of the solver dtype"
+                          % (list(self._state_shape()),))
         return _ptr(U)
 
     # --- C ABI calls ------------------------------------------------------
@@ -338,6 +353,45 @@ class Solver:
 
     def launch_count(self):
         return int(self.lib.dg_launch_count(self.ctx))
+
+
+class Solver2D(Solver):
+    """A 2D mesh of quadrilaterals (include/dg.h, dg_mesh_setup_2d).
+
+    mesh: dict with ``n_elem``, ``geom_degree``, ``nodes`` [E,(q+1)^2,2],
+    ``nbr``, ``nbr_face``, ``orient`` [E,4] (see ``synth.mesh2d``).  States
+    are torch CUDA tensors [E, 3, (k+1)^2]; the steppers work in the Gauss
+    basis (the only basis a 2D context takes)."""
+
+    _FIELDS, _DIM = 3, 2
+
+    def __init__(self, mesh, k, prec=DG_FP64, alpha=1.0, rho=None, c=None, stream=None):
+        import torch
+        self.lib = load_library()
+        self.k, self.n, self.prec = int(k), int(k) + 1, int(prec)
+        self.E = int(mesh["n_elem"])
+        self.dtype = torch.float64 if self.prec == DG_FP64 else torch.float32
+        self._nodes = np.ascontiguousarray(mesh["nodes"], np.float64)
+        self._nbr = np.ascontiguousarray(mesh["nbr"], np.int32)
+        self._nbf = np.ascontiguousarray(mesh["nbr_face"], np.int8)
+        self._ori = np.ascontiguousarray(mesh["orient"], np.int8)
+        desc = MeshDesc2D(self.E, int(mesh["geom_degree"]),
+                          self._nodes.ctypes.data_as(C.POINTER(C.c_double)),
+                          self._nbr.ctypes.data_as(C.POINTER(C.c_int32)),
+                          self._nbf.ctypes.data_as(C.POINTER(C.c_int8)),
+                          self._ori.ctypes.data_as(C.POINTER(C.c_int8)))
+        rho_p = c_p = None
+        if rho is not None:
+            self._rho = np.ascontiguousarray(rho, np.float64).reshape(-1)
+            self._c = np.ascontiguousarray(c, np.float64).reshape(-1)
+            rho_p = self._rho.ctypes.data_as(C.POINTER(C.c_double))
+            c_p = self._c.ctypes.data_as(C.POINTER(C.c_double))
+        ctx = C.c_void_p()
+        rc = self.lib.dg_mesh_setup_2d(C.byref(desc), self.k, self.prec, float(alpha), rho_p, c_p,
+                                       _stream(stream), C.byref(ctx))
+        if rc != 0:
+            raise DGError(rc, self.lib.dg_last_error(None).decode())
+        self.ctx = ctx
 
 
 class Batch:

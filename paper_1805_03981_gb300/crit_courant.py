@@ -14,9 +14,14 @@ import json
 import numpy as np
 
 
-def _setup(k, N, prec):
+def _setup(k, N, prec, dim=3):
     import synth
     from . import _lib
+    if dim == 2:
+        from synth import mesh2d
+        mesh = mesh2d.square_mesh(N, q=1, periodic=True)
+        ones = np.ones((N * N, (k + 1) ** 2))
+        return _lib.Solver2D(mesh, k, prec, 1.0, ones, ones), mesh2d.random_state_2d(N * N, k, 1234), 1.0 / N
     mesh = synth.cube_mesh(N, q=1, periodic=True)
     n3 = (k + 1) ** 3
     ones = np.ones((N ** 3, n3))
@@ -41,9 +46,9 @@ def stable(s, U0, h, k, cr, method, steps, growth):
     return bool(np.isfinite(e1) and e1 <= e0 * (1.0 + growth))
 
 
-def critical(k, method, N=4, steps=1000, growth=0.01, lo=0.02, hi=1.2, tol=2e-3, prec=None):
+def critical(k, method, N=4, steps=1000, growth=0.01, lo=0.02, hi=1.2, tol=2e-3, prec=None, dim=3):
     from . import _lib
-    s, U0, h = _setup(k, N, _lib.DG_FP64 if prec is None else prec)
+    s, U0, h = _setup(k, N, _lib.DG_FP64 if prec is None else prec, dim)
     if method in ("ader", "hdg_ader"):
         hi = min(hi, 0.6)
     while hi - lo > tol:
@@ -61,11 +66,14 @@ def main():
     ap.add_argument("--k", default="1,4,7")
     ap.add_argument("--N", type=int, default=4)
     ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--dim", type=int, default=3, choices=[2, 3])
     a = ap.parse_args()
     out = {}
+    methods = ("lsrk", "ader", "hdg_ader") if a.dim == 3 else ("lsrk", "ader")
     for k in (int(x) for x in a.k.split(",")):
-        out[k] = {m: critical(k, m, a.N, a.steps) for m in ("lsrk", "ader", "hdg_ader")}
-    print(json.dumps({"crit_courant_3d": out, "mesh": f"{a.N}^3 periodic Cartesian, rho=c=1, upwind",
+        out[k] = {m: critical(k, m, a.N, a.steps, dim=a.dim) for m in methods}
+    print(json.dumps({"crit_courant_%dd" % a.dim: out,
+                      "mesh": f"{a.N}^{a.dim} periodic Cartesian, rho=c=1, upwind",
                       "criterion": f"energy growth <= 1 percent over {a.steps} steps from a seeded random state"}))
 
 

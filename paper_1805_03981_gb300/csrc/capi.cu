@@ -14,7 +14,7 @@
 
 #include "../../include/dg.h"
 #include "dg_internal.h"
-#include "dg_kernels.cuh"
+#include "dg2d.cuh"
 
 using namespace dg;
 
@@ -33,6 +33,7 @@ const double kLsrkB[5] = {1432997174477.0 / 9575080441755.0,
 
 std::mutex g_mu;
 KernelTable g_kt;
+KernelTable2D g_kt2;
 bool g_kt_ready = false;
 HostTables g_tab;
 float g_tab_f[DG_TAB_LEN];
@@ -51,6 +52,7 @@ int init_device(int dev, std::string* err) {
     register_f32_hi(&g_kt);
     register_tck_odd_f64(&g_kt);
     register_tck_odd_f32(&g_kt);
+    register_2d(&g_kt2);
     g_kt_ready = true;
   }
   if (dev < 0 || dev >= 64) {
@@ -58,10 +60,10 @@ int init_device(int dev, std::string* err) {
     return DG_EINVAL;
   }
   if (!(g_dev_ready >> dev & 1ull)) {
-    int (*up[8])(const double*, const float*) = {upload_f64_lo,     upload_f64_hi,    upload_f32_lo,
+    int (*up[9])(const double*, const float*) = {upload_f64_lo,     upload_f64_hi,    upload_f32_lo,
                                                   upload_f32_hi,     upload_batch_f64, upload_batch_f32,
-                                                  upload_tck_odd_f64, upload_tck_odd_f32};
-    for (int i = 0; i < 8; ++i) {
+                                                  upload_tck_odd_f64, upload_tck_odd_f32, upload_2d};
+    for (int i = 0; i < 9; ++i) {
       const int e = up[i](g_tab.tab, g_tab_f);
       if (e) {
         cudaGetLastError();
@@ -81,6 +83,7 @@ struct dg_ctx {
   int dev = 0;
   int E = 0, k = 0, n = 0, q = 0, prec = 0;
   int Erun = 0;  // elements stepped: the first Erun (the rest are ghosts of a partition)
+  int dim = 3;   // 2: quadrilaterals (dg_mesh_setup_2d), state [E][3][n^2], Gauss basis inside the steppers
   double alpha = 1.0;
   size_t rsize = 8;
   int32_t* nbr = nullptr;
@@ -125,8 +128,9 @@ struct dg_ctx {
   std::vector<void*> allocs;
   std::string err;
 
-  size_t state_elems() const { return (size_t)E * 4 * n * n * n; }
-  size_t run_elems() const { return (size_t)Erun * 4 * n * n * n; }
+  int npts() const { return dim == 2 ? n * n : n * n * n; }  // nodes per element
+  size_t state_elems() const { return (size_t)E * (dim + 1) * npts(); }
+  size_t run_elems() const { return (size_t)Erun * (dim + 1) * npts(); }
   size_t state_bytes() const { return state_elems() * rsize; }
 
   int fail(int code, const char* fmt, ...) {
@@ -234,6 +238,15 @@ struct DeviceGuard {
 
 inline cudaStream_t S(uintptr_t s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// the 2D path (defined with dg_mesh_setup_2d below)
+int run_setup2(dg_ctx* ctx, cudaStream_t st);
+int change_basis2(dg_ctx* ctx, void* U, int to_g, cudaStream_t st);
+int lsrk_steps2(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st);
+int ader_steps2(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_t st);
+int apply2(dg_ctx* ctx, const void* U, void* R, cudaStream_t st);
+int tck2_gl(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaStream_t st);
+int energy2(dg_ctx* ctx, const void* U, double* out, cudaStream_t st);
+
 int orient_map(int o, int n, int i, int j, int* ip, int* jp) {
   const int u = (o & 1) ? j : i, v = (o & 1) ? i : j;
   *ip = (o & 2) ? n - 1 - u : u;
@@ -333,6 +346,7 @@ int pick_epb(int n, int bytes_per_elem, int target_threads, int max_threads) {
 }
 
 int run_setup(dg_ctx* ctx, cudaStream_t st) {
+  if (ctx->dim == 2) return run_setup2(ctx, st);
   SetupParams P;
   P.E = ctx->E;
   P.n = ctx->n;
@@ -394,6 +408,7 @@ int launch_op(dg_ctx* ctx, const OpParams& p, int epi, cudaStream_t st, bool gba
 
 // In-place change of basis of a whole state (GL <-> G).
 int change_basis(dg_ctx* ctx, void* U, int to_g, cudaStream_t st) {
+  if (ctx->dim == 2) return change_basis2(ctx, U, to_g, st);
   dg_ctx::Span span(ctx, DG_KIND_OTHER, st);
   DG_CK(g_kt.basis[ctx->prec][ctx->n](U, ctx->Erun, to_g, ctx->epb_en, st), "basis kernel launch");
   span.done();
@@ -440,7 +455,7 @@ int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaS
 // every set n, n-1, ..., 2 (curved or variable-coefficient meshes only; the
 // compact affine data serves every set).
 int ensure_levels(dg_ctx* ctx, int red, cudaStream_t st) {
-  if ((red != 1 && red != 3) || ctx->tstep == 1 || ctx->affine) return DG_OK;
+  if ((red != 1 && red != 3) || ctx->tstep == 1 || ctx->affine || ctx->dim == 2) return DG_OK;
   const size_t old_bytes = (size_t)ctx->rsize * ctx->tstride * ctx->E;
   void* fresh = nullptr;
   const int stride1 = tck_geo_stride(ctx->n, 1);
@@ -457,6 +472,8 @@ int ensure_levels(dg_ctx* ctx, int red, cudaStream_t st) {
 int check_red(dg_ctx* ctx, int red) {
   if (red < 0 || red > 3)
     return ctx->fail(DG_EUNSUPPORTED, "reduce_every must be 0, 1, 2 or 3 (got %d)", red);
+  if (ctx->dim == 2 && red != 0 && red != 2)
+    return ctx->fail(DG_EUNSUPPORTED, "2D meshes take reduce_every 0 or 2");
   return DG_OK;
 }
 
@@ -483,6 +500,7 @@ int check_state_ptr(dg_ctx* ctx, const void* p, const char* what) {
 // (neighbours read face values of the input while it is being written):
 // U -> A -> B -> A -> B -> U, so each step ends in U without a copy.
 int lsrk_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st) {
+  if (ctx->dim == 2) return lsrk_steps2(ctx, U, dt, nsteps, st);
   int rc;
   if ((rc = ensure(ctx, &ctx->U2, "LSRK state"))) return rc;
   if ((rc = ensure(ctx, &ctx->U3, "LSRK state"))) return rc;
@@ -510,6 +528,10 @@ int lsrk_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st) {
 // hdg: HDG-ADER (Eq. hdg-ader): each step first evaluates the DG derivative
 // W = -M^-1 K U, which takes the place of the predictor's first term -S U.
 int ader_steps(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_t st, bool hdg = false) {
+  if (ctx->dim == 2) {
+    if (hdg) return ctx->fail(DG_EUNSUPPORTED, "HDG-ADER is not built for 2D meshes");
+    return ader_steps2(ctx, U, dt, nsteps, red, st);
+  }
   int rc;
   if ((rc = ensure(ctx, &ctx->Ubar, "ADER predictor"))) return rc;
   if (hdg && (rc = ensure(ctx, &ctx->Wd, "HDG-ADER derivative"))) return rc;
@@ -725,7 +747,7 @@ int dg_mesh_setup_coef(const dg_mesh_desc* m, int k, int prec, double alpha, con
 int dg_set_coefficients(dg_ctx* ctx, const double* rho, const double* c, uintptr_t stream) {
   if (!ctx) return DG_EINVAL;
   if (!rho || !c) return ctx->fail(DG_EINVAL, "NULL coefficient array");
-  const size_t cnt = (size_t)ctx->E * ctx->n * ctx->n * ctx->n;
+  const size_t cnt = (size_t)ctx->E * ctx->npts();
   for (size_t i = 0; i < cnt; ++i)
     if (!(rho[i] > 0.0) || !(c[i] > 0.0) || !std::isfinite(rho[i]) || !std::isfinite(c[i]))
       return ctx->fail(DG_EINVAL, "coefficients must be positive and finite (index %zu)", i);
@@ -733,7 +755,7 @@ int dg_set_coefficients(dg_ctx* ctx, const double* rho, const double* c, uintptr
   cudaStream_t st = S(stream);
   DG_CK(cudaMemcpyAsync(ctx->rho, rho, sizeof(double) * cnt, cudaMemcpyHostToDevice, st), "upload rho");
   DG_CK(cudaMemcpyAsync(ctx->c, c, sizeof(double) * cnt, cudaMemcpyHostToDevice, st), "upload c");
-  ctx->affine = ctx->geo_affine && coef_constant(rho, c, ctx->E, ctx->n * ctx->n * ctx->n);
+  ctx->affine = ctx->dim == 3 && ctx->geo_affine && coef_constant(rho, c, ctx->E, ctx->npts());
   return run_setup(ctx, st);
 }
 
@@ -746,6 +768,7 @@ int dg_apply_operator(dg_ctx* ctx, const void* U, void* R, uintptr_t stream) {
   const size_t b = ctx->state_bytes();
   if (u0 < r0 + b && r0 < u0 + b) return ctx->fail(DG_EINVAL, "U and R overlap");
   DeviceGuard g(ctx->dev);
+  if (ctx->dim == 2) return apply2(ctx, U, R, S(stream));
   OpParams p = op_params(ctx);
   p.U = U;
   p.out = R;
@@ -793,6 +816,7 @@ int dg_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int32_t red, uintp
   if ((rc = check_red(ctx, red))) return rc;
   if (!std::isfinite(dt)) return ctx->fail(DG_EINVAL, "dt not finite");
   DeviceGuard g(ctx->dev);
+  if (ctx->dim == 2) return tck2_gl(ctx, U, Ubar, dt, red, S(stream));
   if ((rc = ensure_levels(ctx, red, S(stream)))) return rc;
   return launch_tck(ctx, U, Ubar, dt, red, S(stream));
 }
@@ -802,6 +826,7 @@ int dg_energy(dg_ctx* ctx, const void* U, double* out, uintptr_t stream) {
   int rc;
   if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
   DeviceGuard g(ctx->dev);
+  if (ctx->dim == 2) return energy2(ctx, U, out, S(stream));
   const int blocks = (ctx->Erun + ctx->epb_en - 1) / ctx->epb_en;
   if ((rc = ensure_partial(ctx, blocks))) return rc;
   EnergyParams p;
@@ -879,6 +904,8 @@ int dg_solve_host(dg_ctx* ctx, int method, const void* Uh, void* Uout, double dt
 int dg_set_basis(dg_ctx* ctx, int basis) {
   if (!ctx) return DG_EINVAL;
   if (basis != DG_BASIS_GL && basis != DG_BASIS_G) return ctx->fail(DG_EINVAL, "basis must be DG_BASIS_GL or DG_BASIS_G");
+  if (ctx->dim == 2 && basis != DG_BASIS_G)
+    return ctx->fail(DG_EUNSUPPORTED, "2D meshes step in the Gauss basis only");
   ctx->basis = basis;
   return DG_OK;
 }
@@ -991,6 +1018,7 @@ __global__ void noalloc_sum_kernel(const double* part, int n, double* out) {
 }  // namespace
 
 extern "C" int dg_energy_noalloc(dg_ctx* ctx, const void* U, double* out, uintptr_t stream) {
+  if (ctx && ctx->dim == 2) return ctx->fail(DG_EUNSUPPORTED, "not built for 2D meshes");
   if (!ctx) return DG_EINVAL;
   int rc;
   if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
@@ -1048,6 +1076,7 @@ int epb_ok(const dg_ctx* ctx, int which, int epb) {
 }  // namespace
 
 extern "C" int dg_set_tiling(dg_ctx* ctx, int32_t epb_op, int32_t epb_tck) {
+  if (ctx && ctx->dim == 2) return ctx->fail(DG_EUNSUPPORTED, "not built for 2D meshes");
   if (!ctx) return DG_EINVAL;
   if (epb_op > 0) {
     if (!epb_ok(ctx, 0, epb_op)) return ctx->fail(DG_EINVAL, "elements per block %d not possible", epb_op);
@@ -1069,6 +1098,7 @@ extern "C" int dg_get_tiling(const dg_ctx* ctx, int32_t* epb_op, int32_t* epb_tc
 
 extern "C" int dg_tune(dg_ctx* ctx, int kind, const int32_t* cand, int32_t ncand, int32_t reps,
                        double* ms_out, uintptr_t stream) {
+  if (ctx && ctx->dim == 2) return ctx->fail(DG_EUNSUPPORTED, "not built for 2D meshes");
   if (!ctx || !cand || !ms_out || ncand < 1 || reps < 1) return DG_EINVAL;
   if (kind != DG_KIND_LSRK && kind != DG_KIND_TCK && kind != DG_KIND_ADER)
     return ctx->fail(DG_EINVAL, "kind must be DG_KIND_LSRK, DG_KIND_ADER or DG_KIND_TCK");
@@ -1269,6 +1299,10 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
   }
   const int prec = ctxs[0] ? ctxs[0]->prec : 0, dev = ctxs[0] ? ctxs[0]->dev : 0;
   for (int i = 0; i < n; ++i) {
+    if (ctxs[i] && ctxs[i]->dim == 2) {
+      g_setup_err = "batches are not built for 2D meshes";
+      return DG_EUNSUPPORTED;
+    }
     if (!ctxs[i] || ctxs[i]->prec != prec || ctxs[i]->dev != dev) {
       g_setup_err = "dg_batch_create: contexts must be non-NULL, of one precision and one device";
       return DG_EINVAL;
@@ -1533,6 +1567,7 @@ extern "C" void dg_batch_destroy(dg_batch* b) { delete b; }
 // ---------------------------------------------------------------------------
 extern "C" int dg_set_owned(dg_ctx* ctx, int32_t n_owned) {
   if (!ctx) return DG_EINVAL;
+  if (ctx->dim == 2) return ctx->fail(DG_EUNSUPPORTED, "not built for 2D meshes");
   if (n_owned < 1 || n_owned > ctx->E)
     return ctx->fail(DG_EINVAL, "n_owned %d outside [1, %d]", n_owned, ctx->E);
   ctx->Erun = n_owned;
@@ -1698,6 +1733,10 @@ extern "C" int dg_part_create(dg_ctx* const* ctxs, void* const* U, int32_t P, co
   int total = 0;
   for (int i = 0; i < P; ++i) {
     dg_ctx* c = ctxs[i];
+    if (c && c->dim == 2) {
+      e = "parts are not built for 2D meshes";
+      return DG_EUNSUPPORTED;
+    }
     if (!c || c->n != c0->n || c->prec != c0->prec || c->dev != c0->dev || c->basis != c0->basis) {
       e = "parts must share degree, precision, device and storage basis";
       return DG_EINVAL;
@@ -1795,3 +1834,328 @@ extern "C" int dg_part_info(const dg_part* t, int32_t* n_parts, int32_t* n_ghost
 extern "C" const char* dg_part_last_error(const dg_part* t) { return t ? t->err.c_str() : ""; }
 
 extern "C" void dg_part_destroy(dg_part* t) { delete t; }
+
+// ---------------------------------------------------------------------------
+// The 2D path (quadrilaterals): the same scheme one dimension down, with the
+// state held at the Gauss points inside the steppers.  Contexts created by
+// dg_mesh_setup_2d take dg_apply_operator, dg_step_lsrk, dg_step_ader
+// (reduction 0 or 2), dg_tck, dg_energy, dg_norms, dg_solve_host,
+// dg_set_coefficients and dg_change_basis; the other calls return
+// DG_EUNSUPPORTED for them.
+// ---------------------------------------------------------------------------
+namespace {
+
+int pick_epb2(int n, int bytes_per_elem, int target_threads, int max_threads) {
+  int epb = target_threads / n;
+  if (epb < 1) epb = 1;
+  while (epb > 1 && (epb * bytes_per_elem > 200 * 1024 || epb * n > max_threads)) --epb;
+  return epb;
+}
+
+int validate_mesh2(const dg_mesh2d_desc* m, std::string* err) {
+  char buf[256];
+  const int E = m->n_elem;
+  for (int e = 0; e < E; ++e)
+    for (int f = 0; f < 4; ++f) {
+      const int en = m->nbr[e * 4 + f];
+      if (en < -1 || en >= E) {
+        snprintf(buf, sizeof buf, "nbr[%d][%d] = %d out of range", e, f, en);
+        *err = buf;
+        return DG_EMESH;
+      }
+      if (en < 0) continue;
+      const int fn = m->nbr_face[e * 4 + f], o = m->orient[e * 4 + f];
+      if (fn < 0 || fn >= 4 || (o != 0 && o != 1)) {
+        snprintf(buf, sizeof buf, "nbr_face/orient of (%d,%d) out of range", e, f);
+        *err = buf;
+        return DG_EMESH;
+      }
+      if (m->nbr[en * 4 + fn] != e || m->nbr_face[en * 4 + fn] != f || m->orient[en * 4 + fn] != o) {
+        snprintf(buf, sizeof buf, "face (%d,%d) -> (%d,%d) is not reciprocated", e, f, en, fn);
+        *err = buf;
+        return DG_EMESH;
+      }
+    }
+  return DG_OK;
+}
+
+int run_setup2(dg_ctx* ctx, cudaStream_t st) {
+  Setup2Params P;
+  P.E = ctx->E;
+  P.n = ctx->n;
+  P.q = ctx->q;
+  P.alpha = ctx->alpha;
+  P.nodes = ctx->nodes;
+  P.rho = ctx->rho;
+  P.c = ctx->c;
+  P.nbr = ctx->nbr;
+  P.nbr_face = ctx->nbr_face;
+  P.orient = ctx->orient;
+  P.pts = ctx->pts;
+  P.xq = ctx->xq;
+  P.geoA = ctx->geoA;
+  P.geoM = ctx->geoM;
+  P.geoF = ctx->geoF;
+  P.geoT = ctx->geoT;
+  P.tstride = ctx->tstride;
+  P.tstep = ctx->tstep;
+  P.prec = ctx->prec;
+  P.bad = ctx->bad;
+  DG_CK(cudaMemsetAsync(ctx->bad, 0, sizeof(int), st), "memset");
+  DG_CK(launch_setup2d(P, st), "2D set-up kernel launch");
+  ctx->launches++;
+  int bad = 0;
+  DG_CK(cudaMemcpyAsync(&bad, ctx->bad, sizeof(int), cudaMemcpyDeviceToHost, st), "copy flag");
+  DG_CK(cudaStreamSynchronize(st), "2D set-up kernel");
+  if (bad) return ctx->fail(DG_EMESH, "non-positive Jacobian determinant in the mesh");
+  return DG_OK;
+}
+
+int change_basis2(dg_ctx* ctx, void* U, int to_g, cudaStream_t st) {
+  dg_ctx::Span span(ctx, DG_KIND_OTHER, st);
+  DG_CK(g_kt2.basis[ctx->prec][ctx->n](U, ctx->E, to_g, ctx->epb_en, st), "2D basis kernel launch");
+  span.done();
+  ctx->launches++;
+  return DG_OK;
+}
+
+Op2Params op2_params(const dg_ctx* ctx) {
+  Op2Params p;
+  std::memset(&p, 0, sizeof(p));
+  p.nbr = ctx->nbr;
+  p.nbr_face = ctx->nbr_face;
+  p.orient = ctx->orient;
+  p.geoA = ctx->geoA;
+  p.geoM = ctx->geoM;
+  p.geoF = ctx->geoF;
+  p.E = ctx->E;
+  return p;
+}
+
+int launch_op2(dg_ctx* ctx, const Op2Params& p, int epi, cudaStream_t st) {
+  const int kind = epi == EPI_WRITE ? DG_KIND_OPERATOR : (epi == EPI_LSRK ? DG_KIND_LSRK : DG_KIND_ADER);
+  dg_ctx::Span span(ctx, kind, st);
+  DG_CK(g_kt2.op[ctx->prec][ctx->n](p, epi, ctx->epb_op, st), "2D operator kernel launch");
+  span.done();
+  ctx->launches++;
+  return DG_OK;
+}
+
+int launch_tck2(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaStream_t st) {
+  Tck2Params p;
+  std::memset(&p, 0, sizeof(p));
+  p.U = U;
+  p.Ubar = Ubar;
+  p.geoT = ctx->geoT;
+  p.geoT_stride = ctx->tstride;
+  p.geo_step = ctx->tstep;
+  p.E = ctx->E;
+  double fact = 1.0;
+  for (int j = 0; j <= ctx->n; ++j) {
+    fact *= (j + 1);
+    p.coef[j] = std::pow(dt, j + 1) / fact;
+  }
+  dg_ctx::Span span(ctx, DG_KIND_TCK, st);
+  DG_CK(g_kt2.tck[ctx->prec][ctx->n](p, red, ctx->epb_tck, st), "2D predictor kernel launch");
+  span.done();
+  ctx->launches++;
+  return DG_OK;
+}
+
+int lsrk_steps2(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st) {
+  int rc;
+  if ((rc = ensure(ctx, &ctx->U2, "LSRK state")) || (rc = ensure(ctx, &ctx->U3, "LSRK state")) ||
+      (rc = ensure(ctx, &ctx->dU, "LSRK register")))
+    return rc;
+  if (nsteps == 0) return DG_OK;
+  if ((rc = change_basis2(ctx, U, 1, st))) return rc;
+  void* const chain[6] = {U, ctx->U2, ctx->U3, ctx->U2, ctx->U3, U};
+  Op2Params p = op2_params(ctx);
+  for (int s = 0; s < nsteps; ++s)
+    for (int st5 = 0; st5 < 5; ++st5) {
+      p.U = chain[st5];
+      p.Uadd = chain[st5];
+      p.out = chain[st5 + 1];
+      p.dU = ctx->dU;
+      p.cA = kLsrkA[st5];
+      p.cB = kLsrkB[st5];
+      p.dt = dt;
+      p.first = st5 == 0;
+      if ((rc = launch_op2(ctx, p, EPI_LSRK, st))) return rc;
+    }
+  return change_basis2(ctx, U, 0, st);
+}
+
+int ader_steps2(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_t st) {
+  int rc;
+  if ((rc = ensure(ctx, &ctx->Ubar, "ADER predictor"))) return rc;
+  if (nsteps == 0) return DG_OK;
+  if ((rc = change_basis2(ctx, U, 1, st))) return rc;
+  Op2Params p = op2_params(ctx);
+  for (int s = 0; s < nsteps; ++s) {
+    if ((rc = launch_tck2(ctx, U, ctx->Ubar, dt, red, st))) return rc;
+    p.U = ctx->Ubar;
+    p.Uadd = U;
+    p.out = U;
+    if ((rc = launch_op2(ctx, p, EPI_ADD, st))) return rc;
+  }
+  return change_basis2(ctx, U, 0, st);
+}
+
+// R = -M^-1 K U with GL states in and out (the operator works on Gauss values)
+int apply2(dg_ctx* ctx, const void* U, void* R, cudaStream_t st) {
+  int rc;
+  if ((rc = ensure(ctx, &ctx->U2, "scratch state"))) return rc;
+  DG_CK(cudaMemcpyAsync(ctx->U2, U, ctx->state_bytes(), cudaMemcpyDeviceToDevice, st), "copy");
+  if ((rc = change_basis2(ctx, ctx->U2, 1, st))) return rc;
+  Op2Params p = op2_params(ctx);
+  p.U = ctx->U2;
+  p.out = R;
+  if ((rc = launch_op2(ctx, p, EPI_WRITE, st))) return rc;
+  return change_basis2(ctx, R, 0, st);
+}
+
+int tck2_gl(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaStream_t st) {
+  int rc;
+  if ((rc = ensure(ctx, &ctx->U2, "scratch state"))) return rc;
+  DG_CK(cudaMemcpyAsync(ctx->U2, U, ctx->state_bytes(), cudaMemcpyDeviceToDevice, st), "copy");
+  if ((rc = change_basis2(ctx, ctx->U2, 1, st))) return rc;
+  if ((rc = launch_tck2(ctx, ctx->U2, Ubar, dt, red, st))) return rc;
+  return change_basis2(ctx, Ubar, 0, st);
+}
+
+int energy2(dg_ctx* ctx, const void* U, double* out, cudaStream_t st) {
+  int rc;
+  const int blocks = (ctx->E + ctx->epb_en - 1) / ctx->epb_en;
+  if ((rc = ensure_partial(ctx, blocks))) return rc;
+  Energy2Params p;
+  p.U = U;
+  p.geoM = ctx->geoM;
+  p.partial = ctx->partial;
+  p.E = ctx->E;
+  DG_CK(g_kt2.energy[ctx->prec][ctx->n](p, ctx->epb_en, st), "2D energy kernel launch");
+  ctx->launches++;
+  std::vector<double> h(blocks);
+  DG_CK(cudaMemcpyAsync(h.data(), ctx->partial, sizeof(double) * blocks, cudaMemcpyDeviceToHost, st),
+        "copy partials");
+  DG_CK(cudaStreamSynchronize(st), "energy");
+  double s = 0.0;
+  for (int i = 0; i < blocks; ++i) s += h[i];
+  *out = s;
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" int dg_mesh_setup_2d(const dg_mesh2d_desc* m, int k, int prec, double alpha, const double* rho_h,
+                                const double* c_h, uintptr_t stream, dg_ctx** out) {
+  if (!out) return DG_EINVAL;
+  *out = nullptr;
+  g_setup_err.clear();
+  if (!m || !m->nodes || !m->nbr || !m->nbr_face || !m->orient || m->n_elem < 1) {
+    g_setup_err = "NULL mesh array or n_elem < 1";
+    return DG_EINVAL;
+  }
+  if (k < 1 || k > DG_KMAX) {
+    g_setup_err = "degree k outside [1, DG_KMAX]";
+    return DG_EUNSUPPORTED;
+  }
+  if (m->geom_degree < 1 || m->geom_degree > DG_NMAX) {
+    g_setup_err = "geometry degree outside [1, 8]";
+    return DG_EUNSUPPORTED;
+  }
+  if (prec != DG_FP64 && prec != DG_FP32) {
+    g_setup_err = "precision must be DG_FP64 or DG_FP32";
+    return DG_EINVAL;
+  }
+  if (!(alpha >= 0.0 && alpha <= 1.0)) {
+    g_setup_err = "flux_alpha outside [0, 1]";
+    return DG_EINVAL;
+  }
+  if ((rho_h == nullptr) != (c_h == nullptr)) {
+    g_setup_err = "rho and c must both be given or both be NULL";
+    return DG_EINVAL;
+  }
+  int rc = validate_mesh2(m, &g_setup_err);
+  if (rc) return rc;
+  const int n = k + 1, n2 = n * n, E = m->n_elem, qc = m->geom_degree + 1;
+  if (rho_h)
+    for (size_t i = 0; i < (size_t)n2 * E; ++i)
+      if (!(rho_h[i] > 0.0) || !(c_h[i] > 0.0) || !std::isfinite(rho_h[i]) || !std::isfinite(c_h[i])) {
+        g_setup_err = "coefficients must be positive and finite";
+        return DG_EINVAL;
+      }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    g_setup_err = "no CUDA device";
+    return DG_ECUDA;
+  }
+  if ((rc = init_device(dev, &g_setup_err))) return rc;
+  dg_ctx* ctx = new (std::nothrow) dg_ctx();
+  if (!ctx) return DG_ENOMEM;
+  ctx->dim = 2;
+  ctx->basis = DG_BASIS_G;
+  ctx->dev = dev;
+  ctx->E = ctx->Erun = E;
+  ctx->k = k;
+  ctx->n = n;
+  ctx->q = m->geom_degree;
+  ctx->prec = prec;
+  ctx->alpha = alpha;
+  ctx->rsize = prec == DG_FP64 ? 8 : 4;
+  ctx->tstep = 2;
+  ctx->tstride = geo2_stride_T(n, 2);
+  cudaStream_t st = S(stream);
+  auto bail = [&](int code) {
+    g_setup_err = ctx->err;
+    delete ctx;
+    return code;
+  };
+  const size_t rs = ctx->rsize;
+  if ((rc = ctx->alloc(&ctx->nbr, sizeof(int32_t) * 4 * E, "nbr")) ||
+      (rc = ctx->alloc(&ctx->nbr_face, 4 * (size_t)E, "nbr_face")) ||
+      (rc = ctx->alloc(&ctx->orient, 4 * (size_t)E, "orient")) ||
+      (rc = ctx->alloc(&ctx->nodes, sizeof(double) * 2 * qc * qc * (size_t)E, "nodes")) ||
+      (rc = ctx->alloc(&ctx->rho, sizeof(double) * n2 * (size_t)E, "rho")) ||
+      (rc = ctx->alloc(&ctx->c, sizeof(double) * n2 * (size_t)E, "c")) ||
+      (rc = ctx->alloc(&ctx->pts, sizeof(double) * 3 * DG_PTS_LEN, "points")) ||
+      (rc = ctx->alloc(&ctx->xq, sizeof(double) * (DG_NMAX + 2), "geometry points")) ||
+      (rc = ctx->alloc(&ctx->bad, sizeof(int), "flag")) ||
+      (rc = ctx->alloc(&ctx->geoA, rs * geo2_stride_A(n) * (size_t)E, "cell metric")) ||
+      (rc = ctx->alloc(&ctx->geoM, rs * geo2_stride_M(n) * (size_t)E, "mass diagonal")) ||
+      (rc = ctx->alloc(&ctx->geoF, rs * geo2_stride_F(n) * (size_t)E, "face data")) ||
+      (rc = ctx->alloc(&ctx->geoT, rs * (size_t)ctx->tstride * E, "predictor geometry")))
+    return bail(rc);
+  std::vector<double> hpts(3 * DG_PTS_LEN);
+  std::memcpy(hpts.data(), g_tab.xg, sizeof(double) * DG_PTS_LEN);
+  std::memcpy(hpts.data() + DG_PTS_LEN, g_tab.wg, sizeof(double) * DG_PTS_LEN);
+  std::memcpy(hpts.data() + 2 * DG_PTS_LEN, g_tab.xgl, sizeof(double) * DG_PTS_LEN);
+  std::vector<double> hxq(DG_NMAX + 2, 0.0);
+  gauss_lobatto(qc, hxq.data());
+  std::vector<double> ones(rho_h ? 0 : (size_t)n2 * E, 1.0);
+  const double* rho_src = rho_h ? rho_h : ones.data();
+  const double* c_src = c_h ? c_h : ones.data();
+  cudaError_t ce;
+#define DG_UP(dst, src, bytes)                                                            \
+  if ((ce = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) { \
+    ctx->cuda_fail(ce, "upload");                                                         \
+    return bail(DG_ECUDA);                                                                \
+  }
+  DG_UP(ctx->nbr, m->nbr, sizeof(int32_t) * 4 * E);
+  DG_UP(ctx->nbr_face, m->nbr_face, 4 * (size_t)E);
+  DG_UP(ctx->orient, m->orient, 4 * (size_t)E);
+  DG_UP(ctx->nodes, m->nodes, sizeof(double) * 2 * qc * qc * (size_t)E);
+  DG_UP(ctx->rho, rho_src, sizeof(double) * n2 * (size_t)E);
+  DG_UP(ctx->c, c_src, sizeof(double) * n2 * (size_t)E);
+  DG_UP(ctx->pts, hpts.data(), sizeof(double) * 3 * DG_PTS_LEN);
+  DG_UP(ctx->xq, hxq.data(), sizeof(double) * (DG_NMAX + 2));
+#undef DG_UP
+  const int pi = ctx->prec;
+  ctx->epb_op = pick_epb2(n, g_kt2.smem[pi][n](0), 128, g_kt2.maxthr[pi][n](0));
+  ctx->epb_tck = pick_epb2(n, g_kt2.smem[pi][n](1), 128, g_kt2.maxthr[pi][n](1));
+  ctx->epb_en = pick_epb2(n, g_kt2.smem[pi][n](2), 128, g_kt2.maxthr[pi][n](2));
+  if ((rc = run_setup2(ctx, st))) return bail(rc);
+  *out = ctx;
+  return DG_OK;
+}

@@ -38,6 +38,29 @@ struct SetupParams {
 
 cudaError_t launch_setup(const SetupParams& P, cudaStream_t st);
 
+// 2D (quadrilateral) set-up: as SetupParams with 4 faces and n^2 points.
+struct Setup2Params {
+  int E, n, q;
+  double alpha;
+  const double* nodes;  // [E][(q+1)^2][2]
+  const double* rho;    // [E][n^2]
+  const double* c;      // [E][n^2]
+  const int32_t* nbr;   // [E][4]
+  const int8_t* nbr_face;
+  const int8_t* orient;  // [E][4]: 1 = the neighbour's face coordinate runs opposite
+  const double* pts;
+  const double* xq;
+  void* geoA;
+  void* geoM;
+  void* geoF;
+  void* geoT;
+  int tstride;
+  int tstep;
+  int prec;
+  int* bad;
+};
+cudaError_t launch_setup2d(const Setup2Params& P, cudaStream_t st);
+
 typedef cudaError_t (*OpFn)(const OpParams& p, int epi, int epb, cudaStream_t st);
 typedef cudaError_t (*TckFn)(const TckParams& p, int red, int epb, cudaStream_t st);
 typedef cudaError_t (*EnergyFn)(const EnergyParams& p, int epb, cudaStream_t st);
@@ -58,6 +81,20 @@ struct KernelTable {
   SmemFn smem[2][DG_NMAX + 1];
   MaxThrFn maxthr[2][DG_NMAX + 1];
 };
+
+struct Op2Params;
+struct Tck2Params;
+struct Energy2Params;
+struct KernelTable2D {
+  cudaError_t (*op[2][DG_NMAX + 1])(const Op2Params& p, int epi, int epb, cudaStream_t st);
+  cudaError_t (*tck[2][DG_NMAX + 1])(const Tck2Params& p, int red, int epb, cudaStream_t st);
+  cudaError_t (*basis[2][DG_NMAX + 1])(void* U, int E, int to_g, int epb, cudaStream_t st);
+  cudaError_t (*energy[2][DG_NMAX + 1])(const Energy2Params& p, int epb, cudaStream_t st);
+  int (*smem[2][DG_NMAX + 1])(int which);
+  int (*maxthr[2][DG_NMAX + 1])(int which);
+};
+void register_2d(KernelTable2D* t);
+int upload_2d(const double* d, const float* f);
 
 // Each kernel translation unit registers its instantiations and uploads the
 // constant tables into its own copy (returns 0 or a cudaError_t value).
