@@ -289,6 +289,29 @@ int dg_solve_host(dg_ctx* ctx, int method, const void* U_host, void* U_out_host,
                   double dt, int32_t nsteps, int32_t reduce_every, uintptr_t stream);
 
 /*
+ * Checkpoint and restart of a solve.  The paper's steppers are one-step
+ * methods (Sec. 2.2-2.3: the LSRK stages and the ADER step need only U_n),
+ * so U between two step calls is the whole state of a solve: a restart
+ * from it gives, bit for bit, what the same step calls give without the
+ * checkpoint.  (With DG_BASIS_G a call changes basis on entry and exit, so
+ * two calls of m steps and one call of 2m steps agree to rounding only.)
+ *
+ * dg_get_state copies the device state U (this context's precision and
+ * layout, [E][fields][npts] in the Gauss-Lobatto basis) into the caller's
+ * host array host_out of E*fields*npts doubles (fields = 4 and npts =
+ * (k+1)^3 in 3D; 3 and (k+1)^2 in 2D).  dg_set_state copies such a host
+ * array into the device state U, rounding to nearest when the context is
+ * FP32.  FP32 -> FP64 -> FP32 is exact, so a checkpoint of either precision
+ * restores bit for bit.  For an FP32 context each call takes a temporary
+ * device buffer of 8 bytes per entry from the stream-ordered allocator and
+ * returns it before it returns (DG_ENOMEM if that fails).  Host arrays may
+ * be pageable; both calls synchronise the stream.  A partitioned context
+ * copies its whole local state, ghost slots included.
+ */
+int dg_get_state(dg_ctx* ctx, const void* U, double* host_out, uintptr_t stream);
+int dg_set_state(dg_ctx* ctx, const double* host_in, void* U, uintptr_t stream);
+
+/*
  * Per-kernel timing. While enabled, every kernel launch of the context is
  * bracketed by two CUDA events recorded on the launching stream.
  * dg_profile_read synchronises on those events and returns, per kind, the

@@ -20,7 +20,7 @@ EXPORTED_SYMBOLS = [
     "dg_is_affine", "dg_change_basis", "dg_batch_set_basis", "dg_batch_convert",
     "dg_set_owned", "dg_part_create", "dg_part_step_lsrk", "dg_part_step_ader", "dg_part_exchange",
     "dg_part_info", "dg_part_last_error", "dg_part_destroy", "dg_step_hdg_ader", "dg_part_step_hdg_ader",
-    "dg_mesh_setup_2d",
+    "dg_mesh_setup_2d", "dg_get_state", "dg_set_state",
 ]
 BASIS_GL, BASIS_G = 0, 1
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
@@ -147,6 +147,8 @@ def load_library():
         "dg_part_info": (C.c_int, [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint64)]),
         "dg_part_last_error": (C.c_char_p, [vp]),
         "dg_part_destroy": (None, [vp]),
+        "dg_get_state": (C.c_int, [vp, vp, C.POINTER(C.c_double), st]),
+        "dg_set_state": (C.c_int, [vp, C.POINTER(C.c_double), vp, st]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -181,6 +183,7 @@ class Solver:
         import torch
         self.lib = load_library()
         self.k, self.n, self.prec = int(k), int(k) + 1, int(prec)
+        self.alpha = float(alpha)
         self.E = int(mesh["n_elem"])
         self.dtype = torch.float64 if self.prec == DG_FP64 else torch.float32
         self._nodes = np.ascontiguousarray(mesh["nodes"], np.float64)
@@ -242,6 +245,7 @@ class Solver:
     def set_coefficients(self, rho, c, stream=None):
         rho = np.ascontiguousarray(rho, np.float64).reshape(-1)
         c = np.ascontiguousarray(c, np.float64).reshape(-1)
+        self._coef = (rho.copy(), c.copy())
         self._check(self.lib.dg_set_coefficients(
             self.ctx, rho.ctypes.data_as(C.POINTER(C.c_double)),
             c.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
@@ -294,6 +298,24 @@ class Solver:
         self._check(self.lib.dg_solve_host(self.ctx, int(method), _ptr(U_host), _ptr(U_out_host),
                                            float(dt), int(nsteps), int(reduce_every), _stream(stream)))
         return U_out_host
+
+    def get_state(self, U, stream=None):
+        """The device state U as a new FP64 host array (dg_get_state)."""
+        out = np.empty(self._state_shape(), np.float64)
+        self._check(self.lib.dg_get_state(self.ctx, self._state(U), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                          _stream(stream)))
+        return out
+
+    def set_state(self, host, U=None, stream=None):
+        """Copy an FP64 host array into the device state U (a new one when
+        None) with dg_set_state; returns U."""
+        host = np.ascontiguousarray(host, np.float64)
+        if host.size != int(np.prod(self._state_shape())):
+            raise DGError(-1, "host state must have %d entries" % int(np.prod(self._state_shape())))
+        U = self.empty_state() if U is None else U
+        self._check(self.lib.dg_set_state(self.ctx, host.ctypes.data_as(C.POINTER(C.c_double)),
+                                          self._state(U), _stream(stream)))
+        return U
 
     def info(self):
         E, k, p, b = C.c_int32(), C.c_int32(), C.c_int32(), C.c_size_t()
@@ -369,6 +391,7 @@ class Solver2D(Solver):
         import torch
         self.lib = load_library()
         self.k, self.n, self.prec = int(k), int(k) + 1, int(prec)
+        self.alpha = float(alpha)
         self.E = int(mesh["n_elem"])
         self.dtype = torch.float64 if self.prec == DG_FP64 else torch.float32
         self._nodes = np.ascontiguousarray(mesh["nodes"], np.float64)
@@ -384,6 +407,7 @@ class Solver2D(Solver):
         if rho is not None:
             self._rho = np.ascontiguousarray(rho, np.float64).reshape(-1)
             self._c = np.ascontiguousarray(c, np.float64).reshape(-1)
+            self._coef = (self._rho.copy(), self._c.copy())
             rho_p = self._rho.ctypes.data_as(C.POINTER(C.c_double))
             c_p = self._c.ctypes.data_as(C.POINTER(C.c_double))
         ctx = C.c_void_p()

@@ -555,6 +555,13 @@ int ader_steps(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_
   return DG_OK;
 }
 
+// Element-wise precision change of a state (checkpoint copies).
+template <typename From, typename To>
+__global__ void cast_kernel(const From* __restrict__ in, To* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = static_cast<To>(in[i]);
+}
+
 // Sums of squares with a fixed launch shape and summation order.
 template <typename Real>
 __global__ void sumsq_kernel(const Real* A, const Real* B, size_t n, double* part) {
@@ -899,6 +906,67 @@ int dg_solve_host(dg_ctx* ctx, int method, const void* Uh, void* Uout, double dt
   DG_CK(cudaMemcpyAsync(Uout, ctx->Uh, b, cudaMemcpyDeviceToHost, st), "copy out");
   DG_CK(cudaStreamSynchronize(st), "solve");
   return dg_check_device(ctx, stream);
+}
+
+namespace {
+// One FP64 <-> context-precision copy between a host array and a device
+// state: to_host != 0 reads U into host, else writes host into U.
+int state_copy(dg_ctx* ctx, void* U, double* host, int to_host, cudaStream_t st) {
+  const size_t cnt = ctx->state_elems();
+  if (ctx->prec == DG_FP64) {
+    if (to_host)
+      DG_CK(cudaMemcpyAsync(host, U, cnt * sizeof(double), cudaMemcpyDeviceToHost, st), "copy out");
+    else
+      DG_CK(cudaMemcpyAsync(U, host, cnt * sizeof(double), cudaMemcpyHostToDevice, st), "copy in");
+    DG_CK(cudaStreamSynchronize(st), "state copy");
+    return DG_OK;
+  }
+  void* tmp = nullptr;
+  if (cudaMallocAsync(&tmp, cnt * sizeof(double), st) != cudaSuccess) {
+    cudaGetLastError();
+    return ctx->fail(DG_ENOMEM, "no room for a %zu-byte FP64 staging buffer", cnt * sizeof(double));
+  }
+  const int threads = 256;
+  const int blocks = (int)std::min<size_t>((cnt + threads - 1) / threads, 4096);
+  cudaError_t e = cudaSuccess;
+  if (to_host) {
+    cast_kernel<float, double><<<blocks, threads, 0, st>>>(static_cast<const float*>(U),
+                                                          static_cast<double*>(tmp), cnt);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, tmp, cnt * sizeof(double), cudaMemcpyDeviceToHost, st);
+  } else {
+    e = cudaMemcpyAsync(tmp, host, cnt * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+      cast_kernel<double, float><<<blocks, threads, 0, st>>>(static_cast<const double*>(tmp),
+                                                            static_cast<float*>(U), cnt);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess) ctx->launches++;
+  cudaError_t f = cudaFreeAsync(tmp, st);
+  if (e == cudaSuccess) e = f;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "state copy");
+  return DG_OK;
+}
+}  // namespace
+
+int dg_get_state(dg_ctx* ctx, const void* U, double* host_out, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  if (!host_out) return ctx->fail(DG_EINVAL, "NULL host buffer");
+  int rc;
+  if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
+  DeviceGuard g(ctx->dev);
+  return state_copy(ctx, const_cast<void*>(U), host_out, 1, S(stream));
+}
+
+int dg_set_state(dg_ctx* ctx, const double* host_in, void* U, uintptr_t stream) {
+  if (!ctx) return DG_EINVAL;
+  if (!host_in) return ctx->fail(DG_EINVAL, "NULL host buffer");
+  int rc;
+  if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
+  DeviceGuard g(ctx->dev);
+  return state_copy(ctx, U, const_cast<double*>(host_in), 0, S(stream));
 }
 
 int dg_set_basis(dg_ctx* ctx, int basis) {

@@ -83,4 +83,6 @@ def test_argument_validation(lib):
     assert lib.dg_mesh_setup(C.byref(d), 2, 0, 1.5, 0, C.byref(ctx)) == -1     # alpha
     assert lib.dg_mesh_setup(None, 2, 0, 1.0, 0, C.byref(ctx)) == -1
     assert lib.dg_apply_operator(None, None, None, 0) == -1
+    assert lib.dg_get_state(None, None, None, 0) == -1
+    assert lib.dg_set_state(None, None, None, 0) == -1
     lib.dg_destroy(None)  # NULL-safe
