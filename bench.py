@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--tiling", default="", help="elements per block 'op,tck' instead of autotuning")
     ap.add_argument("--basis", default="g", choices=["g", "gl"],
                     help="state inside the steppers: g = Gauss-point values (default), gl = the paper's storage")
+    ap.add_argument("--pred", default="auto", choices=["auto", "lines", "columns"],
+                    help="predictor kernel for Gauss-point states (dg_set_predictor_kernel)")
     ap.add_argument("--workload", default="curved_pulse",
                     choices=["curved_pulse", "plane_wave", "batched", "served", "reduction",
                              "time_to_accuracy", "time_to_accuracy_2d"])
@@ -696,6 +698,7 @@ def main():
         return accuracy_study(args, cfg, dgw, torch)
     s = dgw.Solver(cfg["mesh"], k, prec, cfg["alpha"], cfg["rho"], cfg["c"])
     s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
+    s.set_predictor_kernel({"auto": dgw.PRED_AUTO, "lines": dgw.PRED_LINES, "columns": dgw.PRED_COLUMNS}[args.pred])
     # autotune the tiling of this workload's kernels (results do not depend on it)
     from paper_1805_03981_gb300 import autotune
     if args.tiling:
@@ -824,6 +827,8 @@ def main():
             "config": {"workload": workload_desc(N, k, args.prec, args.workload), "elements": E, "k": k, "dof": dof,
                        "state_basis_inside_steppers": "Gauss points (G)" if args.basis == "g" else "Gauss-Lobatto (GL)",
                        "tiling_elements_per_block": {"operator": tiling[0], "tck": tiling[1]},
+                       "predictor_kernel": ("lines" if args.pred == "lines" or args.basis == "gl"
+                                            or (args.pred == "auto" and args.prec == "fp64") else "columns"),
                        "affine_compact_kernels": s.is_affine(),
                        "l2": "inputs larger than L2 (state %d MB, %d MB device-resident incl. geometry), no flush"
                        % (state_bytes >> 20, s.device_bytes() >> 20),

@@ -217,6 +217,27 @@ int dg_set_basis(dg_ctx* ctx, int basis);
 int dg_get_basis(const dg_ctx* ctx);
 
 /*
+ * Predictor kernel for Gauss-point states (DG_BASIS_G steppers, dg_tck is
+ * unaffected).  Both compute the Taylor sum of Sec. 2.3 Eq. (6) with the
+ * degree reduction of Sec. 3.3, to rounding:
+ *  DG_PRED_LINES    every derivative, projection and prolongation as
+ *                   contractions of element tiles in shared memory, lines
+ *                   spread over the whole block;
+ *  DG_PRED_COLUMNS  each thread keeps a z-column of the current Taylor term
+ *                   and of the n-point sum in registers; x and y lines pass
+ *                   through shared memory once per derivative;
+ *  DG_PRED_AUTO     the column form in FP32, the line form in FP64 (default;
+ *                   the FP64 pipe is the bound there, and the line form
+ *                   keeps whole warps busy at the reduced Gauss sets).
+ * Takes effect on 3D contexts only.  Errors: DG_EINVAL.
+ */
+#define DG_PRED_AUTO 0
+#define DG_PRED_LINES 1
+#define DG_PRED_COLUMNS 2
+int dg_set_predictor_kernel(dg_ctx* ctx, int kind);
+int dg_get_predictor_kernel(const dg_ctx* ctx);
+
+/*
  * 1 if every element is an affine image of the reference cube and the
  * coefficients are constant within each element (checked at set-up and at
  * dg_set_coefficients), else 0. Such meshes get compact per-element data

@@ -21,8 +21,10 @@ EXPORTED_SYMBOLS = [
     "dg_set_owned", "dg_part_create", "dg_part_step_lsrk", "dg_part_step_ader", "dg_part_exchange",
     "dg_part_info", "dg_part_last_error", "dg_part_destroy", "dg_step_hdg_ader", "dg_part_step_hdg_ader",
     "dg_mesh_setup_2d", "dg_get_state", "dg_set_state",
+    "dg_set_predictor_kernel", "dg_get_predictor_kernel",
 ]
 BASIS_GL, BASIS_G = 0, 1
+PRED_AUTO, PRED_LINES, PRED_COLUMNS = 0, 1, 2
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
 KINDS = ["operator", "lsrk_stage", "ader_update", "tck", "other"]
 
@@ -149,6 +151,8 @@ def load_library():
         "dg_part_destroy": (None, [vp]),
         "dg_get_state": (C.c_int, [vp, vp, C.POINTER(C.c_double), st]),
         "dg_set_state": (C.c_int, [vp, C.POINTER(C.c_double), vp, st]),
+        "dg_set_predictor_kernel": (C.c_int, [vp, C.c_int]),
+        "dg_get_predictor_kernel": (C.c_int, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -350,6 +354,13 @@ class Solver:
     def set_basis(self, basis):
         """BASIS_GL (paper's storage, default) or BASIS_G (Gauss values inside the steppers)."""
         self._check(self.lib.dg_set_basis(self.ctx, int(basis)))
+
+    def set_predictor_kernel(self, kind):
+        """PRED_AUTO, PRED_LINES or PRED_COLUMNS (include/dg.h)."""
+        self._check(self.lib.dg_set_predictor_kernel(self.ctx, int(kind)))
+
+    def predictor_kernel(self):
+        return int(self.lib.dg_get_predictor_kernel(self.ctx))
 
     def basis(self):
         return int(self.lib.dg_get_basis(self.ctx))

@@ -52,6 +52,10 @@ int init_device(int dev, std::string* err) {
     register_f32_hi(&g_kt);
     register_tck_odd_f64(&g_kt);
     register_tck_odd_f32(&g_kt);
+    register_tckc_f64_lo(&g_kt);
+    register_tckc_f64_hi(&g_kt);
+    register_tckc_f32_lo(&g_kt);
+    register_tckc_f32_hi(&g_kt);
     register_2d(&g_kt2);
     g_kt_ready = true;
   }
@@ -60,10 +64,11 @@ int init_device(int dev, std::string* err) {
     return DG_EINVAL;
   }
   if (!(g_dev_ready >> dev & 1ull)) {
-    int (*up[9])(const double*, const float*) = {upload_f64_lo,     upload_f64_hi,    upload_f32_lo,
-                                                  upload_f32_hi,     upload_batch_f64, upload_batch_f32,
-                                                  upload_tck_odd_f64, upload_tck_odd_f32, upload_2d};
-    for (int i = 0; i < 9; ++i) {
+    int (*up[13])(const double*, const float*) = {
+        upload_f64_lo,      upload_f64_hi,      upload_f32_lo,      upload_f32_hi,      upload_batch_f64,
+        upload_batch_f32,   upload_tck_odd_f64, upload_tck_odd_f32, upload_tckc_f64_lo, upload_tckc_f64_hi,
+        upload_tckc_f32_lo, upload_tckc_f32_hi, upload_2d};
+    for (int i = 0; i < 13; ++i) {
       const int e = up[i](g_tab.tab, g_tab_f);
       if (e) {
         cudaGetLastError();
@@ -117,6 +122,7 @@ struct dg_ctx {
   uint64_t launches = 0;
   int epb_op = 1, epb_tck = 1, epb_en = 1;
   int basis = DG_BASIS_GL;  // representation of the state inside the steppers
+  int pred_kernel = DG_PRED_AUTO;  // predictor kernel for Gauss-point states
   // profiling: event pairs recorded around launches while enabled
   bool prof = false;
   struct Rec {
@@ -416,6 +422,15 @@ int change_basis(dg_ctx* ctx, void* U, int to_g, cudaStream_t st) {
   return DG_OK;
 }
 
+// Predictor kernel for Gauss-point states (dg_set_predictor_kernel).  By
+// default FP32 takes the column form, which issues fewer shared-memory and
+// index instructions; FP64 takes the line form, whose block-wide spreading
+// keeps every lane of the FP64 pipe busy at the reduced Gauss sets.
+bool use_columns(const dg_ctx* ctx) {
+  if (ctx->pred_kernel == DG_PRED_LINES || g_kt.tckc[ctx->prec][ctx->n] == nullptr) return false;
+  return ctx->pred_kernel == DG_PRED_COLUMNS || ctx->prec == DG_FP32;
+}
+
 int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaStream_t st,
                bool gbasis = false, const void* W = nullptr) {
   TckParams p;
@@ -436,15 +451,21 @@ int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaS
     p.coef[j] = std::pow(dt, j + 1) / fact;
   }
   const bool odd = red == 1 || red == 3;
+  const bool col = gbasis && use_columns(ctx);
   int epb = ctx->epb_tck;
-  if (odd) {  // more accumulator levels: fewer elements may fit a block
+  const int n2 = ctx->n * ctx->n;
+  if (col) {
+    const int per = g_kt.tckc_smem[ctx->prec][ctx->n](red);
+    const int thr = g_kt.tckc_maxthr[ctx->prec][ctx->n]();
+    while (epb > 1 && (epb * per > 200 * 1024 || epb * n2 > thr)) --epb;
+  } else if (odd) {  // more accumulator levels: fewer elements may fit a block
     const int per = g_kt.smem[ctx->prec][ctx->n](1, red);
     const int thr = g_kt.tck_odd_maxthr[ctx->prec][ctx->n]();
-    const int n2 = ctx->n * ctx->n;
     while (epb > 1 && (epb * per > 200 * 1024 || epb * n2 > thr)) --epb;
   }
   dg_ctx::Span span(ctx, DG_KIND_TCK, st);
-  DG_CK((odd ? g_kt.tck_odd : g_kt.tck)[ctx->prec][ctx->n](p, red, epb, st), "predictor kernel launch");
+  DG_CK((col ? g_kt.tckc : odd ? g_kt.tck_odd : g_kt.tck)[ctx->prec][ctx->n](p, red, epb, st),
+        "predictor kernel launch");
   span.done();
   ctx->launches++;
   return DG_OK;
@@ -980,6 +1001,16 @@ int dg_set_basis(dg_ctx* ctx, int basis) {
 
 int dg_get_basis(const dg_ctx* ctx) { return ctx ? ctx->basis : DG_EINVAL; }
 
+int dg_set_predictor_kernel(dg_ctx* ctx, int kind) {
+  if (!ctx) return DG_EINVAL;
+  if (kind != DG_PRED_AUTO && kind != DG_PRED_LINES && kind != DG_PRED_COLUMNS)
+    return ctx->fail(DG_EINVAL, "predictor kernel must be DG_PRED_AUTO, DG_PRED_LINES or DG_PRED_COLUMNS");
+  ctx->pred_kernel = kind;
+  return DG_OK;
+}
+
+int dg_get_predictor_kernel(const dg_ctx* ctx) { return ctx ? ctx->pred_kernel : DG_EINVAL; }
+
 int dg_is_affine(const dg_ctx* ctx) { return ctx ? (ctx->affine ? 1 : 0) : DG_EINVAL; }
 
 int dg_change_basis(dg_ctx* ctx, void* U, int to_g, uintptr_t stream) {
@@ -1238,8 +1269,8 @@ struct BatchGroup {
   BatchItem* items_op = nullptr;
   BatchItem* items_tck = nullptr;
   int n_op = 0, n_tck = 0;
-  int block_op = 0, block_tck = 0, grid_op = 0, grid_tck[3] = {0, 0, 0};
-  size_t smem_op = 0, smem_tck[3] = {0, 0, 0};
+  int block_op = 0, block_tck = 0, grid_op = 0, grid_tck[3] = {0, 0, 0}, grid_tckc[3] = {0, 0, 0};
+  size_t smem_op = 0, smem_tck[3] = {0, 0, 0}, smem_tckc[3] = {0, 0, 0};  // [1] reduction 2, [2] none
   cudaStream_t s = nullptr;  // branch stream
   cudaEvent_t done = nullptr;
 };
@@ -1313,8 +1344,10 @@ int batch_launch_steps(dg_batch* b, int method, int red, int steps, cudaStream_t
     const int mode = b->basis == DG_BASIS_G ? (g.aff ? 2 : 1) : 0;
     e = cudaStreamWaitEvent(g.s, b->fork, 0);
     for (int s = 0; s < steps && e == cudaSuccess; ++s) {
-      if (method == 1) {  // ADER: predictor, then update
-        e = tck(g.n, g.items_tck, g.n_tck, b->inst, red, cnt++, g.grid_tck[ti], g.block_tck, g.smem_tck[ti], g.s);
+      if (method == 1) {  // ADER: predictor, then update (FP32 Gauss-point states: column form)
+        const bool col = b->prec == DG_FP32 && b->basis == DG_BASIS_G;
+        e = tck(g.n, g.items_tck, g.n_tck, b->inst, red, cnt++, col ? g.grid_tckc[ti] : g.grid_tck[ti], g.block_tck,
+                col ? g.smem_tckc[ti] : g.smem_tck[ti], g.s, col ? (g.aff ? 2 : 1) : 0);
         if (e == cudaSuccess)
           e = op(g.n, g.items_op, g.n_op, b->inst, 5, cnt++, g.grid_op, g.block_op, g.smem_op, g.s, mode);
         b->launches += 2;
@@ -1453,6 +1486,10 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     g.smem_op = std::max(g.smem_op, (size_t)eo * g_kt.smem[prec][nn](0, 2));
     g.smem_tck[1] = std::max(g.smem_tck[1], (size_t)et * g_kt.smem[prec][nn](1, 2));
     g.smem_tck[2] = std::max(g.smem_tck[2], (size_t)et * g_kt.smem[prec][nn](1, 0));
+    if (prec == DG_FP32) {
+      g.smem_tckc[1] = std::max(g.smem_tckc[1], (size_t)et * g_kt.tckc_smem[prec][nn](2));
+      g.smem_tckc[2] = std::max(g.smem_tckc[2], (size_t)et * g_kt.tckc_smem[prec][nn](0));
+    }
     b->ctx.push_back(c);
   }
   // Item order: largest solves first (balance at the end of a launch), and
@@ -1478,6 +1515,10 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     g.grid_op = sms * std::max(1, occ(nn, 0, g.block_op, g.smem_op));
     g.grid_tck[1] = sms * std::max(1, occ(nn, 1, g.block_tck, g.smem_tck[1]));
     g.grid_tck[2] = sms * std::max(1, occ(nn, 2, g.block_tck, g.smem_tck[2]));
+    if (prec == DG_FP32) {
+      g.grid_tckc[1] = sms * std::max(1, occ(nn, g.aff ? 5 : 3, g.block_tck, g.smem_tckc[1]));
+      g.grid_tckc[2] = sms * std::max(1, occ(nn, g.aff ? 6 : 4, g.block_tck, g.smem_tckc[2]));
+    }
     // cut each solve into items of about (elements of the degree) / (8 x
     // blocks) elements, in whole slices, so every block sees ~8 items
     auto cut = [](std::vector<BatchItem>& v, int grid) {

@@ -77,6 +77,9 @@ struct KernelTable {
   TckFn tck[2][DG_NMAX + 1];      // reduction every 0 or 2 derivatives
   TckFn tck_odd[2][DG_NMAX + 1];  // reduction every 1 or 3 derivatives
   MaxThr0Fn tck_odd_maxthr[2][DG_NMAX + 1];
+  TckFn tckc[2][DG_NMAX + 1];     // column form, Gauss-basis states, every reduction
+  int (*tckc_smem[2][DG_NMAX + 1])(int red);  // bytes per element
+  MaxThr0Fn tckc_maxthr[2][DG_NMAX + 1];
   EnergyFn energy[2][DG_NMAX + 1];
   SmemFn smem[2][DG_NMAX + 1];
   MaxThrFn maxthr[2][DG_NMAX + 1];
@@ -110,6 +113,14 @@ void register_tck_odd_f64(KernelTable* t);
 void register_tck_odd_f32(KernelTable* t);
 int upload_tck_odd_f64(const double* d, const float* f);
 int upload_tck_odd_f32(const double* d, const float* f);
+void register_tckc_f64_lo(KernelTable* t);
+void register_tckc_f64_hi(KernelTable* t);
+void register_tckc_f32_lo(KernelTable* t);
+void register_tckc_f32_hi(KernelTable* t);
+int upload_tckc_f64_lo(const double* d, const float* f);
+int upload_tckc_f64_hi(const double* d, const float* f);
+int upload_tckc_f32_lo(const double* d, const float* f);
+int upload_tckc_f32_hi(const double* d, const float* f);
 
 struct BatchItem;
 struct BatchInst;
@@ -122,10 +133,14 @@ cudaError_t launch_batch_basis_f64(int n, const BatchItem* items, int nitems, co
                                    int* counter, int grid, int block, size_t smem, cudaStream_t st);
 cudaError_t launch_batch_basis_f32(int n, const BatchItem* items, int nitems, const BatchInst* inst, int to_g,
                                    int* counter, int grid, int block, size_t smem, cudaStream_t st);
+// mode (FP32 only; FP64 always takes the line form): 0 line form, 1 column
+// form, 2 column form on affine elements with constant coefficients
 cudaError_t launch_batch_tck_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
-                                 int* counter, int grid, int block, size_t smem, cudaStream_t st);
+                                 int* counter, int grid, int block, size_t smem, cudaStream_t st, int mode);
 cudaError_t launch_batch_tck_f32(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
-                                 int* counter, int grid, int block, size_t smem, cudaStream_t st);
+                                 int* counter, int grid, int block, size_t smem, cudaStream_t st, int mode);
+// which: 0 operator, 1 / 2 predictor line form (reduction 2 / 0), FP32 also
+// 3 / 4 column form, 5 / 6 column form on affine elements (reduction 2 / 0)
 int batch_occupancy_f64(int n, int which, int block, size_t smem);
 int batch_occupancy_f32(int n, int which, int block, size_t smem);
 int batch_max_threads_f64(int n, int which);  // which: 0 operator, 1 predictor

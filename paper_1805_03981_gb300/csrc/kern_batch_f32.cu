@@ -1,5 +1,6 @@
-// Batched persistent kernels (one launch per degree), float.
-#include "kern_inst.cuh"
+// Batched persistent kernels (one launch per degree), float.  The predictor
+// of Gauss-point states takes the column form (tckc.cuh).
+#include "tckc.cuh"
 
 namespace dg {
 namespace {
@@ -26,14 +27,24 @@ cudaError_t basis_n(const BatchItem* items, int nitems, const BatchInst* inst, i
   batch_basis_kernel<N, float><<<grid, block, smem, st>>>(items, nitems, inst, to_g, counter);
   return cudaGetLastError();
 }
+// mode: 0 GL states (line form), 1 Gauss-point states (column form), 2 the
+// same on affine elements with constant coefficients
+template <int N, int RED>
+cudaError_t tck_nr(const BatchItem* items, int nitems, const BatchInst* inst, int* counter, int grid,
+                   int block, size_t smem, cudaStream_t st, int mode) {
+  if (mode == 2)
+    batch_tckc_kernel<N, float, RED, true><<<grid, block, smem, st>>>(items, nitems, inst, counter);
+  else if (mode == 1)
+    batch_tckc_kernel<N, float, RED, false><<<grid, block, smem, st>>>(items, nitems, inst, counter);
+  else
+    batch_tck_kernel<N, float, RED><<<grid, block, smem, st>>>(items, nitems, inst, counter);
+  return cudaGetLastError();
+}
 template <int N>
 cudaError_t tck_n(const BatchItem* items, int nitems, const BatchInst* inst, int red, int* counter,
-                  int grid, int block, size_t smem, cudaStream_t st) {
-  if (red == 2)
-    batch_tck_kernel<N, float, 2><<<grid, block, smem, st>>>(items, nitems, inst, counter);
-  else
-    batch_tck_kernel<N, float, 0><<<grid, block, smem, st>>>(items, nitems, inst, counter);
-  return cudaGetLastError();
+                  int grid, int block, size_t smem, cudaStream_t st, int mode) {
+  if (red == 2) return tck_nr<N, 2>(items, nitems, inst, counter, grid, block, smem, st, mode);
+  return tck_nr<N, 0>(items, nitems, inst, counter, grid, block, smem, st, mode);
 }
 template <int N>
 int occ_n(int which, int block, size_t smem) {
@@ -42,8 +53,16 @@ int occ_n(int which, int block, size_t smem) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_op_kernel<N, float, EPI_LSRK, 1>, block, smem);
   else if (which == 1)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tck_kernel<N, float, 2>, block, smem);
-  else
+  else if (which == 2)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tck_kernel<N, float, 0>, block, smem);
+  else if (which == 3)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tckc_kernel<N, float, 2, false>, block, smem);
+  else if (which == 4)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tckc_kernel<N, float, 0, false>, block, smem);
+  else if (which == 5)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tckc_kernel<N, float, 2, true>, block, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tckc_kernel<N, float, 0, true>, block, smem);
   cudaGetLastError();
   return nb;
 }
@@ -57,7 +76,11 @@ int maxthr_n(int which) {
                min(min(kernel_max_threads(batch_op_kernel<N, float, EPI_LSRK, 2>),
                        kernel_max_threads(batch_op_kernel<N, float, EPI_ADD, 2>)),
                    kernel_max_threads(batch_basis_kernel<N, float>)));
-  return min(kernel_max_threads(batch_tck_kernel<N, float, 2>), kernel_max_threads(batch_tck_kernel<N, float, 0>));
+  return min(min(kernel_max_threads(batch_tck_kernel<N, float, 2>), kernel_max_threads(batch_tck_kernel<N, float, 0>)),
+             min(min(kernel_max_threads(batch_tckc_kernel<N, float, 2, false>),
+                     kernel_max_threads(batch_tckc_kernel<N, float, 0, false>)),
+                 min(kernel_max_threads(batch_tckc_kernel<N, float, 2, true>),
+                     kernel_max_threads(batch_tckc_kernel<N, float, 0, true>))));
 }
 template <int N>
 cudaError_t allow_n() {
@@ -68,6 +91,10 @@ cudaError_t allow_n() {
     if (r != cudaSuccess) return r;
   if ((e = allow_smem(batch_basis_kernel<N, float>)) != cudaSuccess) return e;
   if ((e = allow_smem(batch_tck_kernel<N, float, 2>)) != cudaSuccess) return e;
+  if ((e = allow_smem(batch_tckc_kernel<N, float, 2, false>)) != cudaSuccess) return e;
+  if ((e = allow_smem(batch_tckc_kernel<N, float, 0, false>)) != cudaSuccess) return e;
+  if ((e = allow_smem(batch_tckc_kernel<N, float, 2, true>)) != cudaSuccess) return e;
+  if ((e = allow_smem(batch_tckc_kernel<N, float, 0, true>)) != cudaSuccess) return e;
   return allow_smem(batch_tck_kernel<N, float, 0>);
 }
 
@@ -93,8 +120,8 @@ cudaError_t launch_batch_op_f32(int n, const BatchItem* items, int nitems, const
   return cudaErrorInvalidValue;
 }
 cudaError_t launch_batch_tck_f32(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
-                                     int* counter, int grid, int block, size_t smem, cudaStream_t st) {
-#define C_(N) tck_n<N>(items, nitems, inst, red, counter, grid, block, smem, st)
+                                     int* counter, int grid, int block, size_t smem, cudaStream_t st, int mode) {
+#define C_(N) tck_n<N>(items, nitems, inst, red, counter, grid, block, smem, st, mode)
   DG_SWITCH_N(n, C_)
 #undef C_
   return cudaErrorInvalidValue;

@@ -93,7 +93,7 @@ cudaError_t launch_batch_op_f64(int n, const BatchItem* items, int nitems, const
   return cudaErrorInvalidValue;
 }
 cudaError_t launch_batch_tck_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
-                                     int* counter, int grid, int block, size_t smem, cudaStream_t st) {
+                                     int* counter, int grid, int block, size_t smem, cudaStream_t st, int) {
 #define C_(N) tck_n<N>(items, nitems, inst, red, counter, grid, block, smem, st)
   DG_SWITCH_N(n, C_)
 #undef C_

@@ -41,8 +41,9 @@ _EPI_KIND = {0: "operator", 1: "lsrk_stage", 2: "ader_update"}
 # and the build flags.  The launch configuration that matters is part of each
 # row (elements per block).
 DIGEST_FILES = ("dg_kernels.cuh", "kern_inst.cuh", "kern_f64_lo.cu", "kern_f64_hi.cu", "kern_f32_lo.cu",
-                "kern_f32_hi.cu", "kern_tck_odd_f64.cu", "kern_tck_odd_f32.cu", "tables.h", "tables.cpp",
-                "setup.cu")
+                "kern_f32_hi.cu", "kern_tck_odd_f64.cu", "kern_tck_odd_f32.cu", "tckc.cuh",
+                "kern_tckc_f64_lo.cu", "kern_tckc_f64_hi.cu", "kern_tckc_f32_lo.cu", "kern_tckc_f32_hi.cu",
+                "tables.h", "tables.cpp", "setup.cu")
 
 
 def sources_digest():
@@ -63,7 +64,7 @@ def kernel_kind(name):
     m = re.search(r"\b(op|opg|opga)_kernel<\s*\d+\s*,\s*\w+\s*,\s*(\d+)\s*>", name)
     if m:
         return _EPI_KIND.get(int(m.group(2)))
-    if re.search(r"\btck_kernel<", name):
+    if re.search(r"\btckc?_kernel<", name):
         return "tck"
     return None
 
