@@ -1268,8 +1268,9 @@ struct BatchGroup {
   int aff = 0;  // affine elements with constant coefficients (compact kernels in the Gauss basis)
   BatchItem* items_op = nullptr;
   BatchItem* items_tck = nullptr;
-  int n_op = 0, n_tck = 0;
-  int block_op = 0, block_tck = 0, grid_op = 0, grid_tck[3] = {0, 0, 0}, grid_tckc[3] = {0, 0, 0};
+  BatchItem* slices_tckc = nullptr;  // FP32 column-form predictor: one block per slice
+  int n_op = 0, n_tck = 0, n_tckc = 0;
+  int block_op = 0, block_tck = 0, grid_op = 0, grid_tck[3] = {0, 0, 0};
   size_t smem_op = 0, smem_tck[3] = {0, 0, 0}, smem_tckc[3] = {0, 0, 0};  // [1] reduction 2, [2] none
   cudaStream_t s = nullptr;  // branch stream
   cudaEvent_t done = nullptr;
@@ -1346,8 +1347,11 @@ int batch_launch_steps(dg_batch* b, int method, int red, int steps, cudaStream_t
     for (int s = 0; s < steps && e == cudaSuccess; ++s) {
       if (method == 1) {  // ADER: predictor, then update (FP32 Gauss-point states: column form)
         const bool col = b->prec == DG_FP32 && b->basis == DG_BASIS_G;
-        e = tck(g.n, g.items_tck, g.n_tck, b->inst, red, cnt++, col ? g.grid_tckc[ti] : g.grid_tck[ti], g.block_tck,
-                col ? g.smem_tckc[ti] : g.smem_tck[ti], g.s, col ? (g.aff ? 2 : 1) : 0);
+        if (col)
+          e = tck(g.n, g.slices_tckc, g.n_tckc, b->inst, red, cnt++, 0, g.block_tck, g.smem_tckc[ti], g.s,
+                  g.aff ? 2 : 1);
+        else
+          e = tck(g.n, g.items_tck, g.n_tck, b->inst, red, cnt++, g.grid_tck[ti], g.block_tck, g.smem_tck[ti], g.s, 0);
         if (e == cudaSuccess)
           e = op(g.n, g.items_op, g.n_op, b->inst, 5, cnt++, g.grid_op, g.block_op, g.smem_op, g.s, mode);
         b->launches += 2;
@@ -1515,9 +1519,15 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     g.grid_op = sms * std::max(1, occ(nn, 0, g.block_op, g.smem_op));
     g.grid_tck[1] = sms * std::max(1, occ(nn, 1, g.block_tck, g.smem_tck[1]));
     g.grid_tck[2] = sms * std::max(1, occ(nn, 2, g.block_tck, g.smem_tck[2]));
+    // the column form's slices: every solve in blocks of its own elements per
+    // block, in the order of the work items (largest solves first)
+    std::vector<BatchItem> slices;
     if (prec == DG_FP32) {
-      g.grid_tckc[1] = sms * std::max(1, occ(nn, g.aff ? 5 : 3, g.block_tck, g.smem_tckc[1]));
-      g.grid_tckc[2] = sms * std::max(1, occ(nn, g.aff ? 6 : 4, g.block_tck, g.smem_tckc[2]));
+      std::vector<BatchItem> whole = htck[gk];
+      std::sort(whole.begin(), whole.end(), by_size);
+      for (const auto& w : whole)
+        for (int e0 = w.e0; e0 < w.e0 + w.ne; e0 += w.epb)
+          slices.push_back({w.inst, e0, std::min(w.epb, w.e0 + w.ne - e0), w.n, w.epb});
     }
     // cut each solve into items of about (elements of the degree) / (8 x
     // blocks) elements, in whole slices, so every block sees ~8 items
@@ -1539,12 +1549,18 @@ extern "C" int dg_batch_create(dg_ctx* const* ctxs, void* const* U, const double
     std::sort(htck[gk].begin(), htck[gk].end(), by_size);
     g.n_op = (int)hop[gk].size();
     g.n_tck = (int)htck[gk].size();
+    g.n_tckc = (int)slices.size();
     if ((rc = batch_alloc(b, (void**)&g.items_op, sizeof(BatchItem) * g.n_op)) ||
         (rc = batch_alloc(b, (void**)&g.items_tck, sizeof(BatchItem) * g.n_tck)))
       return bail(rc);
+    if (g.n_tckc && (rc = batch_alloc(b, (void**)&g.slices_tckc, sizeof(BatchItem) * g.n_tckc))) return bail(rc);
     e = cudaMemcpyAsync(g.items_op, hop[gk].data(), sizeof(BatchItem) * g.n_op, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(g.items_tck, htck[gk].data(), sizeof(BatchItem) * g.n_tck, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && g.n_tckc) {
+      e = cudaMemcpyAsync(g.slices_tckc, slices.data(), sizeof(BatchItem) * g.n_tckc, cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // slices goes out of scope with this iteration
+    }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.s, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
     b->groups.push_back(g);

@@ -134,13 +134,14 @@ cudaError_t launch_batch_basis_f64(int n, const BatchItem* items, int nitems, co
 cudaError_t launch_batch_basis_f32(int n, const BatchItem* items, int nitems, const BatchInst* inst, int to_g,
                                    int* counter, int grid, int block, size_t smem, cudaStream_t st);
 // mode (FP32 only; FP64 always takes the line form): 0 line form, 1 column
-// form, 2 column form on affine elements with constant coefficients
+// form, 2 column form on affine elements with constant coefficients.  The
+// column form takes a list of slices (one block each; grid and counter
+// unused) instead of persistent work items.
 cudaError_t launch_batch_tck_f64(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
                                  int* counter, int grid, int block, size_t smem, cudaStream_t st, int mode);
 cudaError_t launch_batch_tck_f32(int n, const BatchItem* items, int nitems, const BatchInst* inst, int red,
                                  int* counter, int grid, int block, size_t smem, cudaStream_t st, int mode);
-// which: 0 operator, 1 / 2 predictor line form (reduction 2 / 0), FP32 also
-// 3 / 4 column form, 5 / 6 column form on affine elements (reduction 2 / 0)
+// which: 0 operator, 1 / 2 predictor (reduction 2 / 0)
 int batch_occupancy_f64(int n, int which, int block, size_t smem);
 int batch_occupancy_f32(int n, int which, int block, size_t smem);
 int batch_max_threads_f64(int n, int which);  // which: 0 operator, 1 predictor

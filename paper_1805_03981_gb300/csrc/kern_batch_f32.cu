@@ -32,10 +32,10 @@ cudaError_t basis_n(const BatchItem* items, int nitems, const BatchInst* inst, i
 template <int N, int RED>
 cudaError_t tck_nr(const BatchItem* items, int nitems, const BatchInst* inst, int* counter, int grid,
                    int block, size_t smem, cudaStream_t st, int mode) {
-  if (mode == 2)
-    batch_tckc_kernel<N, float, RED, true><<<grid, block, smem, st>>>(items, nitems, inst, counter);
+  if (mode == 2)  // items are slices, one block each
+    batch_tckc_kernel<N, float, RED, true><<<nitems, block, smem, st>>>(items, inst);
   else if (mode == 1)
-    batch_tckc_kernel<N, float, RED, false><<<grid, block, smem, st>>>(items, nitems, inst, counter);
+    batch_tckc_kernel<N, float, RED, false><<<nitems, block, smem, st>>>(items, inst);
   else
     batch_tck_kernel<N, float, RED><<<grid, block, smem, st>>>(items, nitems, inst, counter);
   return cudaGetLastError();
@@ -53,16 +53,8 @@ int occ_n(int which, int block, size_t smem) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_op_kernel<N, float, EPI_LSRK, 1>, block, smem);
   else if (which == 1)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tck_kernel<N, float, 2>, block, smem);
-  else if (which == 2)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tck_kernel<N, float, 0>, block, smem);
-  else if (which == 3)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tckc_kernel<N, float, 2, false>, block, smem);
-  else if (which == 4)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tckc_kernel<N, float, 0, false>, block, smem);
-  else if (which == 5)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tckc_kernel<N, float, 2, true>, block, smem);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tckc_kernel<N, float, 0, true>, block, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_tck_kernel<N, float, 0>, block, smem);
   cudaGetLastError();
   return nb;
 }

@@ -429,26 +429,25 @@ __global__ void tckc_kernel(const TckParams p) {
   tckc_block<N, Real, RED, AFF>(p, e0, min(epb, p.E - e0), reinterpret_cast<Real*>(smem_raw));
 }
 
-// Batched form (the work items and counter of batch_tck_kernel): the same
-// per-element code, so a solve's result does not depend on the batch.
+// One slice of a work item, kept out of line: inlined into the persistent
+// loop, the compiler hoists the slice's many loop-invariant addresses into
+// registers (twice the registers of tckc_kernel, and spills from n = 7).
 template <int N, typename Real, int RED, bool AFF>
-__global__ void batch_tckc_kernel(const BatchItem* __restrict__ items, int nitems,
-                                  const BatchInst* __restrict__ inst, int* counter) {
+__device__ __noinline__ void tckc_slice(const TckParams& p, int e0, int ne, Real* sm) {
+  tckc_block<N, Real, RED, AFF>(p, e0, ne, sm);
+}
+
+// Batched form: one launch per degree over a list of slices (an instance
+// and up to epb of its elements), one block per slice, in the order of the
+// list.  The per-element code is tckc_block's, so a solve's result does not
+// depend on the batch.  Unlike the other batched kernels it is not
+// persistent: inside a persistent loop the compiler keeps twice the
+// registers live (250 instead of 128 at n = 6) and spills from n = 7.
+template <int N, typename Real, int RED, bool AFF>
+__global__ void batch_tckc_kernel(const BatchItem* __restrict__ slices, const BatchInst* __restrict__ inst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Real* sm = reinterpret_cast<Real*>(smem_raw);
-  __shared__ int s_item;
-  for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();
-    const int it = s_item;
-    __syncthreads();
-    if (it >= nitems) break;
-    const BatchItem w = items[it];
-    for (int e0 = w.e0; e0 < w.e0 + w.ne; e0 += w.epb) {
-      tckc_block<N, Real, RED, AFF>(inst[w.inst].tck, e0, min(w.epb, w.e0 + w.ne - e0), sm);
-      __syncthreads();
-    }
-  }
+  const BatchItem w = slices[blockIdx.x];
+  tckc_block<N, Real, RED, AFF>(inst[w.inst].tck, w.e0, w.ne, reinterpret_cast<Real*>(smem_raw));
 }
 
 template <int N, typename Real, int RED>
