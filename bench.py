@@ -65,7 +65,7 @@ def parse():
                     help="predictor kernel for Gauss-point states (dg_set_predictor_kernel)")
     ap.add_argument("--workload", default="curved_pulse",
                     choices=["curved_pulse", "plane_wave", "batched", "served", "reduction",
-                             "time_to_accuracy", "time_to_accuracy_2d"])
+                             "time_to_accuracy", "time_to_accuracy_2d", "basis_change"])
     ap.add_argument("--lam", type=float, default=20.0, help="served: arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="served: arrival window, seconds")
     ap.add_argument("--nrange", default="8,24", help="served: elements per axis, min,max")
@@ -469,6 +469,67 @@ def reduction_bench(args, dgw, torch):
     return 0
 
 
+def basis_change_bench(args, dgw, torch):
+    """What the basis change (Sec. 3.2) and the degree reduction (Sec. 3.3)
+    save, measured: for k = 1..7 on the curved-pulse recipe at about 28M DoF
+    per k, device time per ADER step (predictor + update) with
+      alg1:   GL states, the predictor without the basis change (Alg. 1),
+              no reduction;
+      alg2:   GL states, the predictor with the on-the-fly basis change
+              (Alg. 2), no reduction;
+      alg2_3: Gauss-point states, Alg. 2 with reduction every 2nd
+              derivative (the bench default);
+    and per LSRK(5,4) step (Gauss-point states), next to the op-count models
+    of the three predictors.  The measured counterpart of the paper's
+    Fig. comp-opcounts-RK-ADER, which shows counts only."""
+    from paper_1805_03981_gb300 import opcount
+    prec = dgw.DG_FP64 if args.prec == "fp64" else dgw.DG_FP32
+    rows = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn(args.warmup)
+        torch.cuda.synchronize()
+        ev0.record()
+        fn(args.steps)
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / args.steps
+
+    for k in range(1, 8):
+        n = k + 1
+        N = max(4, round((28.3e6 / (4 * n ** 3)) ** (1.0 / 3.0)))
+        cfg = workload(N, k)
+        dof = 4 * n ** 3 * N ** 3
+        s = dgw.Solver(cfg["mesh"], k, prec, cfg["alpha"], cfg["rho"], cfg["c"])
+        aff = s.is_affine()
+        row = {"k": k, "N": N, "dof": dof}
+        U = s.to_device(cfg["U0"])
+        for name, basis, pred, red in (("alg1", dgw.BASIS_GL, dgw.PRED_GL_PROJECTION, 0),
+                                       ("alg2", dgw.BASIS_GL, dgw.PRED_AUTO, 0),
+                                       ("alg2_3", dgw.BASIS_G, dgw.PRED_AUTO, 2)):
+            s.set_basis(basis)
+            s.set_predictor_kernel(pred)
+            ms = timed(lambda m: s.step_ader(U, cfg["dt"], m, red))
+            row[name + "_ms_per_step"] = ms
+            row[name + "_ns_per_dof_step"] = ms * 1e6 / dof
+        s.set_basis(dgw.BASIS_G)
+        s.set_predictor_kernel(dgw.PRED_AUTO)
+        ms = timed(lambda m: s.step_lsrk(U, cfg["dt"], m))
+        row["lsrk_ms_per_step"] = ms
+        row["lsrk_ns_per_dof_step"] = ms * 1e6 / dof
+        row["model_tck_flops_per_elem"] = {"alg1": opcount.tck_flops_alg1(n, aff),
+                                           "alg2": opcount.tck_flops(n, 0, "gl", aff),
+                                           "alg2_3": opcount.tck_flops(n, 2, "g", aff)}
+        rows.append(row)
+        s.close()
+    out = {"basis_change": {"workload": "curved_pulse recipe at ~28M DoF per k, " + args.prec.upper()
+                                        + "; device time per ADER step with the three predictors and per LSRK(5,4) step",
+                            "steps": args.steps, "rows": rows}}
+    print(json.dumps(out))
+    return 0
+
+
 def batched_bench(args, dgw, torch):
     """256 independent seeded solves (N ~ U{4..24} elements per axis, k ~
     U{2..7}, random smooth rho and c in [0.55, 1.95], curving <= 0.05, walls,
@@ -692,6 +753,8 @@ def main():
         return time_to_accuracy_bench(args, dgw, torch)
     if args.workload == "time_to_accuracy_2d":
         return time_to_accuracy_2d_bench(args, dgw, torch)
+    if args.workload == "basis_change":
+        return basis_change_bench(args, dgw, torch)
     N, k = args.size, args.k
     cfg = workload(N, k, args.workload)
     if args.accuracy:

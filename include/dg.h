@@ -229,11 +229,23 @@ int dg_get_basis(const dg_ctx* ctx);
  *  DG_PRED_AUTO     the column form in FP32, the line form in FP64 (default;
  *                   the FP64 pipe is the bound there, and the line form
  *                   keeps whole warps busy at the reduced Gauss sets).
- * Takes effect on 3D contexts only.  Errors: DG_EINVAL.
+ *  DG_PRED_GL_PROJECTION
+ *                   the predictor without the basis change (Sec. 3.2,
+ *                   Alg. 1), for GL states (DG_BASIS_GL steppers and dg_tck)
+ *                   with reduce_every 0: each derivative is evaluated at the
+ *                   Gauss points, integrated against the GL functions and
+ *                   projected with the inverse GL mass matrix.  Equal to the
+ *                   other forms in exact arithmetic, several times their
+ *                   work; it exists to measure what Secs. 3.2-3.3 save.
+ *                   Other states or reductions, and HDG-ADER, return
+ *                   DG_EUNSUPPORTED when a predictor runs.
+ * Takes effect on 3D contexts only.  Errors: DG_EINVAL, DG_EUNSUPPORTED
+ * (DG_PRED_GL_PROJECTION on a 2D context).
  */
 #define DG_PRED_AUTO 0
 #define DG_PRED_LINES 1
 #define DG_PRED_COLUMNS 2
+#define DG_PRED_GL_PROJECTION 3
 int dg_set_predictor_kernel(dg_ctx* ctx, int kind);
 int dg_get_predictor_kernel(const dg_ctx* ctx);
 

@@ -24,7 +24,7 @@ EXPORTED_SYMBOLS = [
     "dg_set_predictor_kernel", "dg_get_predictor_kernel",
 ]
 BASIS_GL, BASIS_G = 0, 1
-PRED_AUTO, PRED_LINES, PRED_COLUMNS = 0, 1, 2
+PRED_AUTO, PRED_LINES, PRED_COLUMNS, PRED_GL_PROJECTION = 0, 1, 2, 3
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
 KINDS = ["operator", "lsrk_stage", "ader_update", "tck", "other"]
 
@@ -356,7 +356,7 @@ class Solver:
         self._check(self.lib.dg_set_basis(self.ctx, int(basis)))
 
     def set_predictor_kernel(self, kind):
-        """PRED_AUTO, PRED_LINES or PRED_COLUMNS (include/dg.h)."""
+        """PRED_AUTO, PRED_LINES, PRED_COLUMNS or PRED_GL_PROJECTION (include/dg.h)."""
         self._check(self.lib.dg_set_predictor_kernel(self.ctx, int(kind)))
 
     def predictor_kernel(self):

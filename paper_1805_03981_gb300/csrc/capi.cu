@@ -56,6 +56,7 @@ int init_device(int dev, std::string* err) {
     register_tckc_f64_hi(&g_kt);
     register_tckc_f32_lo(&g_kt);
     register_tckc_f32_hi(&g_kt);
+    register_tckn(&g_kt);
     register_2d(&g_kt2);
     g_kt_ready = true;
   }
@@ -64,11 +65,11 @@ int init_device(int dev, std::string* err) {
     return DG_EINVAL;
   }
   if (!(g_dev_ready >> dev & 1ull)) {
-    int (*up[13])(const double*, const float*) = {
+    int (*up[14])(const double*, const float*) = {
         upload_f64_lo,      upload_f64_hi,      upload_f32_lo,      upload_f32_hi,      upload_batch_f64,
         upload_batch_f32,   upload_tck_odd_f64, upload_tck_odd_f32, upload_tckc_f64_lo, upload_tckc_f64_hi,
-        upload_tckc_f32_lo, upload_tckc_f32_hi, upload_2d};
-    for (int i = 0; i < 13; ++i) {
+        upload_tckc_f32_lo, upload_tckc_f32_hi, upload_tckn,        upload_2d};
+    for (int i = 0; i < 14; ++i) {
       const int e = up[i](g_tab.tab, g_tab_f);
       if (e) {
         cudaGetLastError();
@@ -454,6 +455,19 @@ int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaS
   const bool col = gbasis && use_columns(ctx);
   int epb = ctx->epb_tck;
   const int n2 = ctx->n * ctx->n;
+  if (ctx->pred_kernel == DG_PRED_GL_PROJECTION) {  // Alg. 1: GL states, no reduction
+    if (gbasis || red != 0 || W)
+      return ctx->fail(DG_EUNSUPPORTED,
+                       "the GL-projection predictor takes GL states, reduce_every 0 and no HDG derivative");
+    const int per = g_kt.tckn_smem[ctx->prec][ctx->n](0);
+    const int thr = g_kt.tckn_maxthr[ctx->prec][ctx->n]();
+    while (epb > 1 && (epb * per > 200 * 1024 || epb * n2 > thr)) --epb;
+    dg_ctx::Span span(ctx, DG_KIND_TCK, st);
+    DG_CK(g_kt.tckn[ctx->prec][ctx->n](p, 0, epb, st), "predictor kernel launch");
+    span.done();
+    ctx->launches++;
+    return DG_OK;
+  }
   if (col) {
     const int per = g_kt.tckc_smem[ctx->prec][ctx->n](red);
     const int thr = g_kt.tckc_maxthr[ctx->prec][ctx->n]();
@@ -1003,8 +1017,11 @@ int dg_get_basis(const dg_ctx* ctx) { return ctx ? ctx->basis : DG_EINVAL; }
 
 int dg_set_predictor_kernel(dg_ctx* ctx, int kind) {
   if (!ctx) return DG_EINVAL;
-  if (kind != DG_PRED_AUTO && kind != DG_PRED_LINES && kind != DG_PRED_COLUMNS)
-    return ctx->fail(DG_EINVAL, "predictor kernel must be DG_PRED_AUTO, DG_PRED_LINES or DG_PRED_COLUMNS");
+  if (kind != DG_PRED_AUTO && kind != DG_PRED_LINES && kind != DG_PRED_COLUMNS && kind != DG_PRED_GL_PROJECTION)
+    return ctx->fail(DG_EINVAL,
+                     "predictor kernel must be DG_PRED_AUTO, DG_PRED_LINES, DG_PRED_COLUMNS or DG_PRED_GL_PROJECTION");
+  if (kind == DG_PRED_GL_PROJECTION && ctx->dim == 2)
+    return ctx->fail(DG_EUNSUPPORTED, "not built for 2D meshes");
   ctx->pred_kernel = kind;
   return DG_OK;
 }

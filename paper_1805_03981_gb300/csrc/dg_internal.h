@@ -80,6 +80,9 @@ struct KernelTable {
   TckFn tckc[2][DG_NMAX + 1];     // column form, Gauss-basis states, every reduction
   int (*tckc_smem[2][DG_NMAX + 1])(int red);  // bytes per element
   MaxThr0Fn tckc_maxthr[2][DG_NMAX + 1];
+  TckFn tckn[2][DG_NMAX + 1];     // without the basis change (Alg. 1), GL states, no reduction
+  int (*tckn_smem[2][DG_NMAX + 1])(int red);
+  MaxThr0Fn tckn_maxthr[2][DG_NMAX + 1];
   EnergyFn energy[2][DG_NMAX + 1];
   SmemFn smem[2][DG_NMAX + 1];
   MaxThrFn maxthr[2][DG_NMAX + 1];
@@ -121,6 +124,8 @@ int upload_tckc_f64_lo(const double* d, const float* f);
 int upload_tckc_f64_hi(const double* d, const float* f);
 int upload_tckc_f32_lo(const double* d, const float* f);
 int upload_tckc_f32_hi(const double* d, const float* f);
+void register_tckn(KernelTable* t);
+int upload_tckn(const double* d, const float* f);
 
 struct BatchItem;
 struct BatchInst;

@@ -92,6 +92,20 @@ def tck_flops(n, red=2, basis="gl", affine=False):
     return f
 
 
+def tck_flops_alg1(n, affine=False):
+    """The predictor without the basis change (Sec. 3.2, Alg. 1): per
+    derivative, GL -> G interpolation (12 contractions), the collocation
+    derivative and chain rule at the Gauss points, the w det J weights, the
+    integration against the GL functions (12), and the inverse GL mass matrix
+    V^-1 diag V^-T (24 and a division per point); no degree reduction.
+    Once per element: w det J from the inverse Jacobian (about 30 per point)."""
+    N3 = n ** 3
+    deriv_contr, deriv_pt = (6, 36) if affine else (12, 36)
+    per = (12 * contraction(N3, n) + deriv_contr * contraction(N3, n) + deriv_pt * N3 + 4 * N3
+           + 12 * contraction(N3, n) + 24 * contraction(N3, n) + 4 * N3 + 2 * 4 * N3)
+    return 30 * N3 + 4 * N3 + n * per
+
+
 def geometry_reals(n, curved=True):
     """Per-element geometry values read by the operator: 9 metric + 2 mass
     diagonal per cell point, 6 per face point."""

@@ -43,6 +43,7 @@ _EPI_KIND = {0: "operator", 1: "lsrk_stage", 2: "ader_update"}
 DIGEST_FILES = ("dg_kernels.cuh", "kern_inst.cuh", "kern_f64_lo.cu", "kern_f64_hi.cu", "kern_f32_lo.cu",
                 "kern_f32_hi.cu", "kern_tck_odd_f64.cu", "kern_tck_odd_f32.cu", "tckc.cuh",
                 "kern_tckc_f64_lo.cu", "kern_tckc_f64_hi.cu", "kern_tckc_f32_lo.cu", "kern_tckc_f32_hi.cu",
+                "tckn.cuh", "kern_tckn.cu",
                 "tables.h", "tables.cpp", "setup.cu")
 
 
@@ -64,7 +65,7 @@ def kernel_kind(name):
     m = re.search(r"\b(op|opg|opga)_kernel<\s*\d+\s*,\s*\w+\s*,\s*(\d+)\s*>", name)
     if m:
         return _EPI_KIND.get(int(m.group(2)))
-    if re.search(r"\btckc?_kernel<", name):
+    if re.search(r"\btck[cn]?_kernel<", name):
         return "tck"
     return None
 

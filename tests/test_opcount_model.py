@@ -28,3 +28,16 @@ def test_predictor_share_grows_with_degree():
     # step grows with the degree
     shares = [opcount.paper_scheme_ops(k)["tck"] / opcount.paper_scheme_ops(k)["ader"] for k in range(1, 13)]
     assert all(b > a for a, b in zip(shares, shares[1:]))
+
+
+def test_predictor_without_basis_change_costs_more():
+    """Alg. 1 (projection in the GL basis for every derivative) costs more
+    than Alg. 2 with the on-the-fly basis change, which costs more than
+    Alg. 2 with degree reduction every second derivative (Secs. 3.2-3.3),
+    and the gap widens with the degree."""
+    ratios = []
+    for n in range(2, 9):
+        a1, a2, a23 = (opcount.tck_flops_alg1(n), opcount.tck_flops(n, 0, "gl"), opcount.tck_flops(n, 2, "g"))
+        assert a1 > a2 > a23, n
+        ratios.append(a1 / a23)
+    assert all(b > a for a, b in zip(ratios, ratios[1:]))
