@@ -130,6 +130,6 @@ def test_predictor_kernel_argument():
     for kind in (dgw.PRED_LINES, dgw.PRED_COLUMNS, dgw.PRED_AUTO):
         s.set_predictor_kernel(kind)
         assert s.predictor_kernel() == kind
-    for bad in (-1, 3):
+    for bad in (-1, 4):
         with pytest.raises(dgw.DGError):
             s.set_predictor_kernel(bad)
