@@ -274,3 +274,33 @@ def test_affine_steppers_match_oracle(k, basis):
         torch.cuda.synchronize()
         s32.check_device()
         assert rel_l2(V.cpu().numpy(), ref) < 2e-5, method
+
+
+@pytest.mark.parametrize("geometry", ["affine", "curved"])
+@pytest.mark.parametrize("k", [2, 4])
+def test_operator_tilings_fp32(geometry, k):
+    """The FP32 Gauss-point operators (staged tiles) with 1 to 4 elements per
+    block over a 27-element periodic mesh: neighbours that are block-mates
+    (x-neighbours, and y-neighbours where a block wraps a row, the periodic
+    seam included) take their traces from the staged tiles, the others from
+    global memory; the last block is ragged.  LSRK and ADER steps against
+    the oracle."""
+    torch = _cuda()
+    cfg = (_affine_piecewise(3, k, seed=70 + k, periodic=True) if geometry == "affine"
+           else _curved(3, k, seed=70 + k, periodic=True))
+    s, o = pair(cfg)
+    refs = {"lsrk": o.lsrk(cfg["U0"], 0.003, 2), "ader": o.ader(cfg["U0"], 0.003, 2, 2)}
+    s32 = dgw.Solver(cfg["mesh"], k, dgw.DG_FP32, 1.0, cfg["rho"], cfg["c"])
+    s32.set_basis(dgw.BASIS_G)
+    assert s32.is_affine() == (geometry == "affine")
+    for epb in (1, 2, 3, 4):
+        s32.set_tiling(epb, 0)
+        for method, ref in refs.items():
+            V = s32.to_device(cfg["U0"])
+            if method == "lsrk":
+                s32.step_lsrk(V, 0.003, 2)
+            else:
+                s32.step_ader(V, 0.003, 2, 2)
+            torch.cuda.synchronize()
+            s32.check_device()
+            assert rel_l2(V.cpu().numpy(), ref) < 2e-5, (epb, method)
