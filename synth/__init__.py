@@ -2,7 +2,7 @@
 
 This package builds the *inputs* of a solve -- hexahedral cube meshes (with
 optional curving and relabelled element axes), coefficient fields, initial
-states and the analytic solutions used to judge accuracy.  It holds none of the
+states and the analytic solutions used to measure accuracy.  It holds none of the
 discontinuous Galerkin arithmetic: no quadrature, no operator, no time
 stepping.  Both the FP64 CPU oracle (``oracle/``) and the CUDA path
 (``paper_1805_03981_gb300``) read what it produces, and it imports neither.
