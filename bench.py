@@ -79,7 +79,10 @@ def parse():
                     help="instead of timing: run this many steps of each method in FP32 and FP64 "
                          "and report the relative l2 differences and errors against the exact plane wave")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--cpu-steps", type=int, default=0,
+                    help="steps of the oracle's sample (default: 20 on the 4^3 curved pulse, 2 on larger samples)")
+    ap.add_argument("--cpu-size", type=int, default=0,
+                    help="elements per axis of the oracle's sample (default 4 curved pulse, 16 plane wave)")
     ap.add_argument("--kset", default="1,4,7", help="time_to_accuracy: degrees")
     ap.add_argument("--t-end", type=float, default=1.0, help="time_to_accuracy: end time")
     return ap.parse_args()
@@ -178,7 +181,8 @@ CPU_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
 import synth, oracle
-cfg = synth.configs.curved_pulse(N={n}, k={k})
+cfg = (synth.configs.plane_wave(N={n}, k={k}) if {workload!r} == "plane_wave"
+       else synth.configs.curved_pulse(N={n}, k={k}))
 o = oracle.Oracle(cfg["mesh"], {k}, cfg["rho"], cfg["c"], 1.0)
 U1 = cfg["U0"].copy(); U2 = cfg["U0"].copy()
 for _ in range({warm}):
@@ -192,10 +196,10 @@ print(json.dumps({{"times": times, "dof": int(U1.size)}}))
 """
 
 
-def run_oracle(n, k, warm, steps):
+def run_oracle(n, k, warm, steps, workload="curved_pulse"):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = CPU_SNIPPET.format(root=ROOT, n=n, k=k, warm=warm, steps=steps)
+    code = CPU_SNIPPET.format(root=ROOT, n=n, k=k, warm=warm, steps=steps, workload=workload)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
@@ -204,10 +208,10 @@ def run_oracle(n, k, warm, steps):
     return 2 * out["dof"] * len(out["times"]) / total, total, out
 
 
-def cpu_sample_desc(n, k, steps):
+def cpu_sample_desc(n, k, steps, workload="curved_pulse"):
     return (f"FP64 oracle (dense element matrices, numpy, 1 thread) on the {n}^3-element instance of "
-            f"the same recipe (k={k}, {4 * (k + 1) ** 3 * n ** 3} DoF): {steps} steps of 1 LSRK + 1 ADER step, "
-            f"oracle set-up excluded")
+            f"the same {workload} recipe (k={k}, {4 * (k + 1) ** 3 * n ** 3} DoF): {steps} steps of 1 LSRK + "
+            f"1 ADER step, oracle set-up excluded")
 
 
 # ------------------------------------------------------------------ reference arm
@@ -873,11 +877,13 @@ def main():
            "k_steps_per_call_value": world * 2 * dof * args.steps / solve_s}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "curved_pulse":
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("curved_pulse", "plane_wave"):
         try:
-            v, total, _ = run_oracle(4, k, 1, args.cpu_steps)
+            n_cpu = args.cpu_size or (4 if args.workload == "curved_pulse" else 16)
+            st_cpu = args.cpu_steps or (20 if n_cpu <= 4 else 2)
+            v, total, _ = run_oracle(n_cpu, k, 1, st_cpu, args.workload)
             cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": cpu_sample_desc(4, k, args.cpu_steps), "seconds": total}
+                   "sample": cpu_sample_desc(n_cpu, k, st_cpu, args.workload), "seconds": total}
         except Exception as exc:  # the GPU number stands without it
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(exc)[:200]}
 
