@@ -39,15 +39,15 @@ def test_batch_bitwise_equals_alone(prec, method):
     alone = []
     for c, s in zip(cfgs, solvers):
         U = s.to_device(c["U0"])
-        if method == "ader":
-            s.step_ader(U, c["dt"], steps, 2)
+        if method.startswith("ader"):
+            s.step_ader(U, c["dt"], steps, 0 if method == "ader_red0" else 2)
         else:
             s.step_lsrk(U, c["dt"], steps)
         alone.append(U)
     states = [s.to_device(c["U0"]) for c, s in zip(cfgs, solvers)]
     b = dgw.Batch(solvers, states, [c["dt"] for c in cfgs])
-    if method == "ader":
-        b.step_ader(steps, 2)
+    if method.startswith("ader"):
+        b.step_ader(steps, 0 if method == "ader_red0" else 2)
     else:
         b.step_lsrk(steps)
     torch.cuda.synchronize()
@@ -84,7 +84,7 @@ def test_tune_sets_a_valid_tiling():
 
 
 @pytest.mark.parametrize("prec", [dgw.DG_FP64, dgw.DG_FP32])
-@pytest.mark.parametrize("method", ["ader", "lsrk"])
+@pytest.mark.parametrize("method", ["ader", "ader_red0", "lsrk"])
 def test_batch_gauss_basis_bitwise_equals_alone(prec, method):
     """Gauss-basis batches (general and affine solves mixed) give each solve
     exactly the state of its own Gauss-basis stepping."""

@@ -112,14 +112,15 @@ def test_columns_equal_lines(k, geometry):
 
 
 @pytest.mark.parametrize("k", [3, 5])
-def test_columns_hdg_ader_vs_oracle(k):
+@pytest.mark.parametrize("red", [1, 2, 3])
+def test_columns_hdg_ader_vs_oracle(k, red):
     torch = _cuda()
     cfg = _curved(2, k, seed=400 + k)
     s, o = pair(cfg)
     dt = 0.003
-    U = _ader(s, cfg["U0"], dgw.PRED_COLUMNS, dt, 2, 2, hdg=True)
+    U = _ader(s, cfg["U0"], dgw.PRED_COLUMNS, dt, 2, red, hdg=True)
     torch.cuda.synchronize()
-    assert rel_l2(U.cpu().numpy(), o.hdg_ader(cfg["U0"], dt, 2, 2)) < 1e-12
+    assert rel_l2(U.cpu().numpy(), o.hdg_ader(cfg["U0"], dt, 2, red)) < 1e-12
 
 
 def test_predictor_kernel_argument():
