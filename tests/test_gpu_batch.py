@@ -39,15 +39,15 @@ def test_batch_bitwise_equals_alone(prec, method):
     alone = []
     for c, s in zip(cfgs, solvers):
         U = s.to_device(c["U0"])
-        if method.startswith("ader"):
-            s.step_ader(U, c["dt"], steps, 0 if method == "ader_red0" else 2)
+        if method == "ader":
+            s.step_ader(U, c["dt"], steps, 2)
         else:
             s.step_lsrk(U, c["dt"], steps)
         alone.append(U)
     states = [s.to_device(c["U0"]) for c, s in zip(cfgs, solvers)]
     b = dgw.Batch(solvers, states, [c["dt"] for c in cfgs])
-    if method.startswith("ader"):
-        b.step_ader(steps, 0 if method == "ader_red0" else 2)
+    if method == "ader":
+        b.step_ader(steps, 2)
     else:
         b.step_lsrk(steps)
     torch.cuda.synchronize()
@@ -100,16 +100,16 @@ def test_batch_gauss_basis_bitwise_equals_alone(prec, method):
     for c, s in zip(cfgs, solvers):
         s.set_basis(dgw.BASIS_G)
         U = s.to_device(c["U0"])
-        if method == "ader":
-            s.step_ader(U, c["dt"], steps, 2)
+        if method.startswith("ader"):
+            s.step_ader(U, c["dt"], steps, 0 if method == "ader_red0" else 2)
         else:
             s.step_lsrk(U, c["dt"], steps)
         alone.append(U)
     states = [s.to_device(c["U0"]) for c, s in zip(cfgs, solvers)]
     b = dgw.Batch(solvers, states, [c["dt"] for c in cfgs])
     b.set_basis(dgw.BASIS_G, convert_each_call=True)
-    if method == "ader":
-        b.step_ader(steps, 2)
+    if method.startswith("ader"):
+        b.step_ader(steps, 0 if method == "ader_red0" else 2)
     else:
         b.step_lsrk(steps)
     torch.cuda.synchronize()
