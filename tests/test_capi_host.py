@@ -86,3 +86,66 @@ def test_argument_validation(lib):
     assert lib.dg_get_state(None, None, None, 0) == -1
     assert lib.dg_set_state(None, None, None, 0) == -1
     lib.dg_destroy(None)  # NULL-safe
+
+
+def _setup_rc(lib, mesh, dim=3):
+    """dg_mesh_setup's (or dg_mesh_setup_2d's) status for a mesh; a context
+    it returns (a valid mesh on a machine with a GPU) is destroyed."""
+    keep = [np.ascontiguousarray(mesh["nodes"], np.float64), np.ascontiguousarray(mesh["nbr"], np.int32),
+            np.ascontiguousarray(mesh["nbr_face"], np.int8), np.ascontiguousarray(mesh["orient"], np.int8)]
+    ptrs = (keep[0].ctypes.data_as(C.POINTER(C.c_double)), keep[1].ctypes.data_as(C.POINTER(C.c_int32)),
+            keep[2].ctypes.data_as(C.POINTER(C.c_int8)), keep[3].ctypes.data_as(C.POINTER(C.c_int8)))
+    ctx = C.c_void_p()
+    if dim == 3:
+        d = _lib.MeshDesc(mesh["n_elem"], mesh["geom_degree"], *ptrs)
+        rc = lib.dg_mesh_setup(C.byref(d), 2, 0, 1.0, 0, C.byref(ctx))
+    else:
+        d = _lib.MeshDesc2D(mesh["n_elem"], mesh["geom_degree"], *ptrs)
+        rc = lib.dg_mesh_setup_2d(C.byref(d), 2, 0, 1.0, None, None, 0, C.byref(ctx))
+    if rc == 0:
+        lib.dg_destroy(ctx)
+    else:
+        assert not ctx.value
+    return rc
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_mesh_validation_fuzz(lib, dim):
+    """Seeded random corruptions of a periodic mesh with rotated element
+    frames: out-of-range neighbours, faces and orientation codes, broken
+    reciprocity, swapped entries.  Set-up must reject each one cleanly
+    (DG_EMESH, with a message) or, where a corruption happens to leave a
+    consistent mesh, accept it (on a machine without a GPU: DG_ECUDA); it
+    never crashes and never returns a context on error."""
+    rng = np.random.default_rng(11 + dim)
+    if dim == 3:
+        base = synth.cube_mesh(3, q=1, periodic=True, frames=synth.mesh.random_frames(27, rng))
+        nf, no = 6, 8
+    else:
+        from synth import mesh2d
+        base = mesh2d.square_mesh(4, q=1, periodic=True, frames=mesh2d.random_frames_2d(16, rng))
+        nf, no = 4, 2
+    E = base["n_elem"]
+    assert _setup_rc(lib, base, dim) in (0, -3)          # the uncorrupted mesh is consistent
+    seen = set()
+    for trial in range(300):
+        m = {k: (np.array(v, copy=True) if isinstance(v, np.ndarray) else v) for k, v in base.items()}
+        e, f = int(rng.integers(E)), int(rng.integers(nf))
+        kind = trial % 5
+        if kind == 0:
+            m["nbr"][e, f] = int(rng.integers(-3, E + 3))
+        elif kind == 1:
+            m["nbr_face"][e, f] = int(rng.integers(-2, nf + 3))
+        elif kind == 2:
+            m["orient"][e, f] = int(rng.integers(-2, no + 3))
+        elif kind == 3:
+            e2, f2 = int(rng.integers(E)), int(rng.integers(nf))
+            m["nbr"][e, f], m["nbr"][e2, f2] = m["nbr"][e2, f2], m["nbr"][e, f]
+        else:
+            m["nbr"][e, f] = -1                          # a wall on one side only
+        rc = _setup_rc(lib, m, dim)
+        assert rc in (-7, 0, -3), (trial, kind, rc)
+        if rc == -7:
+            assert lib.dg_last_error(None)
+        seen.add(rc)
+    assert -7 in seen
