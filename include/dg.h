@@ -239,8 +239,11 @@ int dg_get_basis(const dg_ctx* ctx);
  *                   work; it exists to measure what Secs. 3.2-3.3 save.
  *                   Other states or reductions, and HDG-ADER, return
  *                   DG_EUNSUPPORTED when a predictor runs.
- * Takes effect on 3D contexts only.  Errors: DG_EINVAL, DG_EUNSUPPORTED
- * (DG_PRED_GL_PROJECTION on a 2D context).
+ * Takes effect on 3D contexts stepped on their own.  Batches (and so the
+ * server) choose for themselves: the column form for FP32 Gauss-point
+ * states, the line form otherwise; each batched solve then matches the same
+ * solve stepped alone with DG_PRED_AUTO bit for bit.  Errors: DG_EINVAL,
+ * DG_EUNSUPPORTED (DG_PRED_GL_PROJECTION on a 2D context).
  */
 #define DG_PRED_AUTO 0
 #define DG_PRED_LINES 1
