@@ -41,3 +41,18 @@ def test_predictor_without_basis_change_costs_more():
         assert a1 > a2 > a23, n
         ratios.append(a1 / a23)
     assert all(b > a for a, b in zip(ratios, ratios[1:]))
+
+
+def test_bench_roofline_counts():
+    """The algorithmic counts behind the bench's roofline figures: the LSRK
+    stage of the default workload (curved pulse 32^3, k=5, FP64,
+    Gauss-point states) moves 1.87 GB and 2.59 GFLOP per launch (four state
+    vectors, the per-point geometry, connectivity; the operator with the
+    stage update, walls on the cube's boundary faces), and that of the
+    FP32 plane wave 64^3 at k=4 (affine compact data) 2.16 GB and 10.2 GFLOP."""
+    E = 32 ** 3
+    assert opcount.bytes_per_element("lsrk_stage", 6, 8, 2, affine=False) * E == 1869742080
+    assert round(opcount.flops_per_element("lsrk_stage", 6, 2, 1.0 - 1.0 / 32, "g", False) * E) == 2586968064
+    E = 64 ** 3
+    assert opcount.bytes_per_element("lsrk_stage", 5, 4, 2, affine=True) * E == 2156920832
+    assert round(opcount.flops_per_element("lsrk_stage", 5, 2, 1.0, "g", True) * E) == 10243276800
