@@ -149,3 +149,22 @@ def test_mesh_validation_fuzz(lib, dim):
             assert lib.dg_last_error(None)
         seen.add(rc)
     assert -7 in seen
+
+
+def test_header_and_library_from_plain_c(lib, tmp_path):
+    """include/dg.h compiles as C99 and libdg.so links into a C program,
+    whose GPU-free calls behave as documented (tests/c/abi_check.c)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(dgw.library_path())
+    exe = str(tmp_path / "abi_check")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c", "abi_check.c"), "-L", libdir, "-ldg",
+                        "-Wl,-rpath," + libdir, "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "c abi ok" in r.stdout
