@@ -1,0 +1,234 @@
+"""The pins constrain the oracle: each test plants one plausible mistake in
+an oracle instance (a sign, a dropped term, a transposed operand, a wrong
+table, a coefficient typo, a wrong orientation map), on the CPU, re-runs the
+measurement of the pin that should catch it, and checks that the pin's own
+criterion holds for the oracle as written and fails for the mutant.
+"""
+import math
+
+import numpy as np
+import pytest
+import sympy as sp
+
+import oracle
+import oracle.dg as odg
+import synth
+from oracle import LSRK54_A, LSRK54_B
+from oracle.basis import gauss_1d, gauss_lobatto_1d, tensor_points
+from oracle_helpers import SHEAR, linear_map, single_element_mesh
+from test_oracle_operator import _poly_fields
+from test_oracle_timestep import _sym_minus_S, stability_poly
+
+
+# --- operator: polynomial consistency (interior elements reproduce -S u) ---
+def _consistency(mutate=None):
+    k, N, alpha = 3, 4, 1.0
+    rng = np.random.default_rng(13)
+    mesh = synth.cube_mesh(N, q=1, periodic=True, deform=linear_map(SHEAR))
+    x = synth.solution_node_positions(mesh, k)
+    rho0, c0 = 1.3, 0.7
+    n3 = (k + 1) ** 3
+    o = oracle.Oracle(mesh, k, np.full((N ** 3, n3), rho0), np.full((N ** 3, n3), c0), alpha)
+    if mutate:
+        mutate(o)
+    u, g = _poly_fields(x, rng, k)
+    U = np.transpose(u, (0, 2, 1)).copy()
+    R = o.apply(U)
+    Rex = np.zeros_like(U)
+    Rex[:, 1:] = -np.transpose(g[:, :, 0, :], (0, 2, 1)) / rho0
+    Rex[:, 0] = -rho0 * c0 ** 2 * (g[:, :, 1, 0] + g[:, :, 2, 1] + g[:, :, 3, 2])
+    interior = [e for e in range(N ** 3) if all(1 <= v <= N - 2 for v in (e % N, (e // N) % N, e // (N * N)))]
+    return np.abs(R[interior] - Rex[interior]).max() / np.abs(Rex[interior]).max()
+
+
+def _drop_face(o):
+    o.s[:, 3] = 0.0                          # the +eta face integral forgotten
+
+
+def _transpose_cell(o):
+    o.B = np.ascontiguousarray(np.swapaxes(o.B, 2, 3))   # test and trial functions swapped
+
+
+def _mass_typo(o):
+    o.Minv_p = o.Minv_p * 1.001              # a slightly wrong pressure mass
+
+
+def _normal_sign(o):
+    o.nrm[:, 4] = -o.nrm[:, 4]               # an inward normal on one face
+
+
+@pytest.mark.parametrize("mutant", [_drop_face, _transpose_cell, _mass_typo, _normal_sign])
+def test_consistency_pin_catches(mutant):
+    assert _consistency() < 1e-11
+    assert _consistency(mutant) > 1e-4, mutant.__name__
+
+
+# --- operator: energy identity (central conserves, upwind dissipates) ------
+def _energy_rate(alpha, mutate=None):
+    k, N = 3, 3
+    n3 = (k + 1) ** 3
+    rng = np.random.default_rng(7)
+    mesh = synth.cube_mesh(N, q=1, periodic=True, deform=linear_map(SHEAR))
+    rho = rng.uniform(0.5, 2.0, size=(N ** 3, n3))
+    c = rng.uniform(0.5, 2.0, size=(N ** 3, n3))
+    o = oracle.Oracle(mesh, k, rho, c, alpha)
+    if mutate:
+        mutate(o)
+    U = rng.uniform(-1, 1, size=(N ** 3, 4, n3))
+    R = o.apply(U)
+    return o.mass_inner(U, R) / np.sqrt(o.mass_inner(U, U) * o.mass_inner(R, R))
+
+
+def test_energy_pin_catches_antidissipative_flux():
+    assert _energy_rate(1.0) < -1e-3
+
+    def flip(o):
+        o.alpha = -1.0                       # the upwind penalty with the wrong sign
+    assert _energy_rate(1.0, flip) > 1e-3
+
+
+def test_energy_pin_catches_unbalanced_central_flux():
+    assert abs(_energy_rate(0.0)) < 1e-13
+
+    def lopsided(o):
+        o.Zp = 2.0 * o.Zp                    # weights of p* and (v.n)* no longer sum to one
+    assert abs(_energy_rate(0.0, lopsided)) > 1e-4
+
+
+# --- flux: the upwind flux is the exact Riemann solution -------------------
+def _riemann_residual(mutate=None, k=1):
+    N, n = 2, k + 1
+    n3 = n ** 3
+    mesh = synth.cube_mesh(N, q=1, periodic=True)
+    ex = np.arange(N ** 3) % N
+    rho = np.where(ex == 0, 1.0, 2.0)[:, None] * np.ones((1, n3))
+    c = np.where(ex == 0, 1.0, 1.5)[:, None] * np.ones((1, n3))
+    ZL, ZR = 1.0, 3.0
+    o = oracle.Oracle(mesh, k, rho, c, alpha=1.0)
+    if mutate:
+        mutate(o)
+    sL = np.array([0.7, 0.4, -0.2, 0.1])
+    sR = np.array([-0.3, -0.5, 0.6, 0.2])
+    U = np.where((ex == 0)[:, None, None], sL[None, :, None], sR[None, :, None]) * np.ones((1, 1, n3))
+    R = o.apply(U)
+    xgl = gauss_lobatto_1d(n)
+    phi = (1 + xgl[np.arange(n3) % n]) / 2
+    area = (1.0 / N) ** 2
+    pstar = sL[0] - (phi @ (o.Mv[0] @ R[0, 1])) / area
+    vstar = sL[1] - (phi @ (o.Mp[0] @ R[0, 0])) / area
+    return max(abs(pstar + ZL * vstar - (sL[0] + ZL * sL[1])), abs(pstar - ZR * vstar - (sR[0] - ZR * sR[1])))
+
+
+def test_riemann_pin_catches_swapped_impedances():
+    assert _riemann_residual() < 1e-12
+
+    def swap(o):
+        o.Zm, o.Zp = o.Zp.copy(), o.Zm.copy()   # each side weighted by its own impedance
+    assert _riemann_residual(swap) > 1e-3
+
+
+# --- orientation: relabelled element axes change nothing physical ----------
+def _relabel_difference():
+    k, N = 3, 3
+    rng = np.random.default_rng(5)
+    frames = synth.mesh.random_frames(N ** 3, rng)
+    deform = synth.mesh.curving(0.04)
+    fields_fn = lambda x: np.stack([np.sin(2 * np.pi * x[..., 0] + 1) * np.cos(2 * np.pi * x[..., 2]),
+                                    np.cos(2 * np.pi * x[..., 1]), np.sin(2 * np.pi * (x[..., 0] + x[..., 2])),
+                                    np.cos(2 * np.pi * x[..., 1] + 0.3)], -1)
+    out = []
+    for fr in (None, frames):
+        mesh = synth.cube_mesh(N, q=k, periodic=True, deform=deform, frames=fr)
+        x = synth.solution_node_positions(mesh, k)
+        o = oracle.Oracle(mesh, k, np.ones(x.shape[:2]), np.ones(x.shape[:2]), 1.0)
+        R = o.apply(np.transpose(fields_fn(x), (0, 2, 1)).copy())
+        key = np.round(x, 9)
+        order = np.lexsort((key[..., 0], key[..., 1], key[..., 2]), axis=-1)
+        out.append(np.take_along_axis(R, order[:, None, :], axis=2))
+    return np.abs(out[0] - out[1]).max() / np.abs(out[0]).max()
+
+
+def test_relabelling_pin_catches_wrong_orientation_map(monkeypatch):
+    assert _relabel_difference() < 1e-11
+    right = odg.orient_perm
+
+    def no_swap(o, m):
+        return right(o & ~1, m)              # the axis-swap bit of the code ignored
+    monkeypatch.setattr(odg, "orient_perm", no_swap)
+    assert _relabel_difference() > 1e-3
+
+
+# --- LSRK: the stage loop realises the fourth-order stability polynomial ---
+def test_lsrk_pins_catch_a_coefficient_typo():
+    A = list(LSRK54_A)
+    A[2] = A[2] * (1 + 1e-6)                 # one digit wrong in one coefficient
+    g = stability_poly(A, LSRK54_B)
+    assert max(abs(g[j] - 1.0 / math.factorial(j)) for j in range(5)) > 1e-9
+    cfg = synth.configs.standing_wave(N=2, k=2)
+    o = oracle.Oracle(cfg["mesh"], 2, cfg["rho"], cfg["c"], 1.0)
+    U0 = synth.configs.random_state(8, 2, 3)
+    dt = 0.01
+    g0 = stability_poly(LSRK54_A, LSRK54_B)
+    acc, term = g0[0] * U0, U0
+    for j in range(1, 6):
+        term = dt * o.apply(term)
+        acc = acc + g0[j] * term
+    assert np.abs(o.lsrk(U0, dt, 1) - acc).max() / np.abs(U0).max() < 1e-14
+    assert np.abs(o.lsrk(U0, dt, 1, A=A) - acc).max() / np.abs(U0).max() > 1e-12
+
+
+# --- TCK: Taylor terms equal (-S)^j u computed symbolically ----------------
+def _tck_symbolic_error(mutate=None):
+    k = 3
+    n, n3 = k + 1, (k + 1) ** 3
+    A = np.array([[0.31, 0.05, -0.02], [0.03, 0.27, 0.04], [0.06, -0.01, 0.22]])
+    Ainv = np.linalg.inv(A)
+    rho, c = 1.4, 0.8
+    o = oracle.Oracle(single_element_mesh(A), k, np.full((1, n3), rho), np.full((1, n3), c))
+    if mutate:
+        mutate(o)
+    rng = np.random.default_rng(30)
+    xi = sp.symbols("x0 x1 x2")
+    flds = []
+    for _ in range(4):
+        expr = 0
+        for a in range(n):
+            for b in range(n):
+                for cc in range(n):
+                    expr += float(rng.normal()) * xi[0] ** a * xi[1] ** b * xi[2] ** cc
+        flds.append(expr)
+    pts = tensor_points(gauss_lobatto_1d(n))
+    ev = lambda f, P: np.array(sp.lambdify(xi, f, "numpy")(P[:, 0], P[:, 1], P[:, 2]) + 0 * P[:, 0])
+    U = np.stack([ev(f, pts) for f in flds])[None]
+    _, terms = o.tck(U, 0.03, 0, return_terms=True)
+    cur, err, scale = flds, 0.0, np.abs(U).max()
+    for j, (m, T) in enumerate(terms[1:], start=1):
+        cur = _sym_minus_S(cur, Ainv, rho, c, xi)
+        ex = np.stack([ev(f, tensor_points(gauss_1d(m)[0])) for f in cur])
+        scale = max(np.abs(ex).max(), scale)
+        err = max(err, np.abs(T[0] - ex).max() / scale)
+    return err
+
+
+def test_tck_pin_catches_wrong_derivative_table():
+    assert _tck_symbolic_error() < 1e-11
+
+    def scaled_derivative(o):
+        t = o._tck_level(o.n)
+        t["D"] = t["D"] * (1 + 1e-6)         # a derivative table off in the sixth digit
+    assert _tck_symbolic_error(scaled_derivative) > 1e-8
+
+    def wrong_metric(o):
+        t = o._tck_level(o.n)
+        t["Jinv"] = np.ascontiguousarray(np.swapaxes(t["Jinv"], 2, 3))   # J^-1 transposed
+    assert _tck_symbolic_error(wrong_metric) > 1e-3
+
+
+# --- quadrature: n Gauss points integrate degree 2n-1 exactly -------------
+def test_exactness_pin_catches_perturbed_weights():
+    n = 4
+    x, w = gauss_1d(n)
+    exact = 2.0 / (2 * n - 1)                # integral of x^(2n-2) over [-1, 1]
+    assert abs(np.sum(w * x ** (2 * n - 2)) - exact) < 1e-14
+    w_bad = w * (1 + 1e-7 * np.arange(n))
+    assert abs(np.sum(w_bad * x ** (2 * n - 2)) - exact) > 1e-9
