@@ -232,3 +232,66 @@ def test_exactness_pin_catches_perturbed_weights():
     assert abs(np.sum(w * x ** (2 * n - 2)) - exact) < 1e-14
     w_bad = w * (1 + 1e-7 * np.arange(n))
     assert abs(np.sum(w_bad * x ** (2 * n - 2)) - exact) > 1e-9
+
+
+# --- degree reduction: the projection is Legendre truncation --------------
+def _projection_error(m, r, mutate=None):
+    from numpy.polynomial import legendre as leg
+    k = m - 1
+    o = oracle.Oracle(single_element_mesh(np.diag([0.5, 0.5, 0.5])), k,
+                      np.ones((1, (k + 1) ** 3)), np.ones((1, (k + 1) ** 3)))
+    if mutate:
+        mutate(o, m)
+    rng = np.random.default_rng(100 * m + r)
+    C = rng.normal(size=(4, m, m, m))
+
+    def values(C, npts):
+        V = leg.legvander(gauss_1d(npts)[0], C.shape[1] - 1)
+        return np.einsum("fijl,ai,bj,cl->fcba", C, V, V, V).reshape(4, -1)
+
+    got = o._project(values(C, m)[None], m, r)[0]
+    want = values(C[:, :m - r, :m - r, :m - r], m - r)
+    return np.abs(got - want).max() / np.abs(want).max()
+
+
+def test_projection_pin_catches_interpolation_in_place_of_projection():
+    assert _projection_error(5, 2) < 1e-12
+
+    def interpolate(o, m):
+        # the reduced values taken by evaluating the m-point interpolant at
+        # the (m-2) points instead of projecting: exact only for degree < m-2
+        from oracle.basis import basis_3d
+        o._tck_level(m)["P"] = basis_3d(gauss_1d(m)[0], tensor_points(gauss_1d(m - 2)[0]))
+    assert _projection_error(5, 2, interpolate) > 1e-3
+
+
+# --- HDG-ADER: one step equals ADER where the DG derivative is collocated ---
+def _hdg_vs_ader(mutate=None):
+    k, N = 2, 6
+    rng = np.random.default_rng(42)
+    mesh = synth.cube_mesh(N, q=1, periodic=True, deform=linear_map(SHEAR))
+    x = synth.solution_node_positions(mesh, k)
+    n3 = (k + 1) ** 3
+    o = oracle.Oracle(mesh, k, np.full((N ** 3, n3), 1.3), np.full((N ** 3, n3), 0.7))
+    u, _ = _poly_fields(x, rng, k)
+    U = np.transpose(u, (0, 2, 1)).copy()
+    a = o.ader(U, 0.01, 1, 2)
+    if mutate:
+        mutate(o)
+    h = o.hdg_ader(U, 0.01, 1, 2)
+    deep = [e for e in range(N ** 3) if all(2 <= v <= N - 3 for v in (e % N, (e // N) % N, e // (N * N)))]
+    return np.abs(h[deep] - a[deep]).max() / np.abs(a[deep]).max()
+
+
+def test_hdg_pin_catches_a_first_term_built_from_u():
+    assert _hdg_vs_ader() < 1e-12
+    plain_tck = odg.Oracle.tck
+
+    def tck_ignoring_w(self, U, dt, reduce_every=2, return_terms=False, first=None):
+        return plain_tck(self, U, dt, reduce_every, return_terms, first=U)   # T_1 from U, not from W
+
+    def mutate(o):
+        o.tck = tck_ignoring_w.__get__(o)
+    # the first term enters with dt^2 / 2, so the mutant differs by ~1e-5:
+    # far outside the pin's 1e-12
+    assert _hdg_vs_ader(mutate) > 1e-8
