@@ -295,3 +295,63 @@ def test_hdg_pin_catches_a_first_term_built_from_u():
     # the first term enters with dt^2 / 2, so the mutant differs by ~1e-5:
     # far outside the pin's 1e-12
     assert _hdg_vs_ader(mutate) > 1e-8
+
+
+# --- the 2D oracle: consistency and energy pins on quadrilaterals ---------
+def _consistency_2d(mutate=None, k=3):
+    from oracle import Oracle2D
+    from synth import mesh2d
+    N = 5
+    A2 = np.array([[1.0, 0.3], [-0.2, 0.9]])
+    mesh = mesh2d.square_mesh(N, q=1, periodic=True, deform=lambda x: x @ A2.T)
+    x = mesh2d.solution_node_positions_2d(mesh, k)
+    rng = np.random.default_rng(k)
+    co = rng.normal(size=(3, k + 1, k + 1))
+    rho0, c0 = 1.3, 0.7
+    terms = [(a, b) for a in range(k + 1) for b in range(k + 1) if a + b <= k]
+    f = lambda c: sum(c[a, b] * x[..., 0] ** a * x[..., 1] ** b for a, b in terms)
+    dx = lambda c: sum(c[a, b] * a * x[..., 0] ** (a - 1) * x[..., 1] ** b for a, b in terms if a > 0)
+    dy = lambda c: sum(c[a, b] * b * x[..., 0] ** a * x[..., 1] ** (b - 1) for a, b in terms if b > 0)
+    n2 = (k + 1) ** 2
+    o = Oracle2D(mesh, k, np.full((N * N, n2), rho0), np.full((N * N, n2), c0))
+    if mutate:
+        mutate(o)
+    U = np.stack([f(co[i]) for i in range(3)], axis=1)
+    R = o.apply(U)
+    Rex = np.stack([-rho0 * c0 ** 2 * (dx(co[1]) + dy(co[2])), -dx(co[0]) / rho0, -dy(co[0]) / rho0], axis=1)
+    inner = [e for e in range(N * N) if 1 <= e % N <= N - 2 and 1 <= e // N <= N - 2]
+    return np.abs(R[inner] - Rex[inner]).max() / np.abs(Rex[inner]).max()
+
+
+def _energy_rate_2d(alpha, mutate=None):
+    from oracle import Oracle2D
+    from synth import mesh2d
+    k, N = 3, 3
+    rng = np.random.default_rng(5)
+    A2 = np.array([[1.0, 0.3], [-0.2, 0.9]])
+    mesh = mesh2d.square_mesh(N, q=1, periodic=False, deform=lambda x: x @ A2.T,
+                              frames=mesh2d.random_frames_2d(N * N, rng))
+    n2 = (k + 1) ** 2
+    o = Oracle2D(mesh, k, rng.uniform(0.5, 2.0, size=(N * N, n2)), rng.uniform(0.5, 2.0, size=(N * N, n2)), alpha)
+    if mutate:
+        mutate(o)
+    U = rng.uniform(-1, 1, size=(N * N, 3, n2))
+    R = o.apply(U)
+    return o.mass_inner(U, R) / np.sqrt(o.mass_inner(U, U) * o.mass_inner(R, R))
+
+
+def test_2d_pins_catch_planted_mistakes():
+    assert _consistency_2d() < 1e-11
+
+    def drop_face(o):
+        o.s[:, 2] = 0.0
+    assert _consistency_2d(drop_face) > 1e-4
+
+    def transpose_cell(o):
+        o.B = np.ascontiguousarray(np.swapaxes(o.B, 2, 3))
+    assert _consistency_2d(transpose_cell) > 1e-4
+    assert _energy_rate_2d(1.0) < -1e-4
+
+    def flip(o):
+        o.alpha = -1.0
+    assert _energy_rate_2d(1.0, flip) > 1e-4
