@@ -16,5 +16,6 @@ Parity status per function is stated in each module's header.
 """
 from .basis import (gauss_1d, gauss_lobatto_1d, lagrange_1d,  # noqa: F401
                     lagrange_deriv_1d, tensor_points)
-from .dg import Oracle, LSRK54_A, LSRK54_B  # noqa: F401
+from .dg import (Oracle, LSRK54_A, LSRK54_B, LSRK45_KCL_A, LSRK45_KCL_B,  # noqa: F401
+                 LSRK59_KCL_A, LSRK59_KCL_B)
 from .dg2d import Oracle2D  # noqa: F401

@@ -19,7 +19,10 @@ Scheme (the paper's Sec. 2 with the readings listed in the design notes):
   tau = 1/(rho c) when Z- = Z+; alpha = 0 is the central flux.
   Walls use the mirror state p+ = p-, v+ = v- - 2 (v-.n) n, Z+ = Z-.
 * LSRK: 2N-storage five-stage fourth-order scheme (Sec. 2.2),
-      dU <- A_s dU + dt R(U);  U <- U + B_s dU,  s = 1..5.
+      dU <- A_s dU + dt R(U);  U <- U + B_s dU,  s = 1..5;
+  and the paper's two-register schemes LSRK4(5) and LSRK5(9) (Sec. 2.2):
+      Y_{i+1} = S_i + dt A_i R(Y_i),  S_{i+1} = S_i + dt B_i R(Y_i),
+  Y_1 = S_1 = u_n, u_{n+1} = S_{s+1}.
 * ADER, Sec. 2.3 Eqs. (5)-(6): Ubar = sum_{j=0}^{k+1} dt^{j+1}/(j+1)! T_j with
   T_0 = u, T_j = -S T_{j-1} evaluated by collocation in the Gauss points
   (Algorithm 2), the degree reduced every second derivative by the
@@ -29,9 +32,12 @@ Scheme (the paper's Sec. 2 with the readings listed in the design notes):
 Parity pins (tests/test_oracle_*.py): exact quadrature of M and B on affine
 elements against exact integrals; polynomial consistency R = -S u in interior
 elements; the semi-discrete energy identity (central: 0, upwind: <= 0);
-invariance under relabelled element axes; LSRK stability polynomial; TCK
-terms against symbolic (-S)^j u; convergence of both schemes to the analytic
-standing wave at the expected rates.  Curved meshes with variable
+invariance under relabelled element axes; LSRK stability polynomials and,
+for the two-register schemes, all Butcher order conditions up to their order
+and the paper's critical Courant numbers; TCK terms against symbolic
+(-S)^j u; convergence of both schemes to the analytic standing wave at the
+expected rates; the energy 1/2 U^T M U and the L2 errors against closed
+forms on graded meshes.  Curved meshes with variable
 coefficients are covered by the same code path; beyond the energy identity
 (which is not exact there) and convergence, their parity is unpinned by the
 paper.
@@ -53,6 +59,28 @@ LSRK54_B = [1432997174477.0 / 9575080441755.0,
             1720146321549.0 / 2090206949498.0,
             3134564353537.0 / 4481467310338.0,
             2277821191437.0 / 14882151754819.0]
+
+
+# The two-register (2R) schemes of Kennedy, Carpenter & Lewis (2000), the
+# paper's LSRK4(5) and LSRK5(9) (Sec. 2.2): RK4(3)5[2R+]C, five stages of
+# order four, and RK5(4)9[2R+]S, nine stages of order five.  In Butcher form
+# a_{i,j} = b_j for j < i-1 and a_{i,i-1} = A_{i-1}: stage i+1 starts from
+# u_n plus all earlier increments weighted by b, except the newest, which
+# is weighted by A_i.  Published coefficients (rationals).
+LSRK45_KCL_A = [970286171893.0 / 4311952581923.0, 6584761158862.0 / 12103376702013.0,
+                2251764453980.0 / 15575788980749.0, 26877169314380.0 / 34165994151039.0]
+LSRK45_KCL_B = [1153189308089.0 / 22510343858157.0, 1772645290293.0 / 4653164025191.0,
+                -1672844663538.0 / 4480602732383.0, 2114624349019.0 / 3568978502595.0,
+                5198255086312.0 / 14908931495163.0]
+LSRK59_KCL_A = [1107026461565.0 / 5417078080134.0, 38141181049399.0 / 41724347789894.0,
+                493273079041.0 / 11940823631197.0, 1851571280403.0 / 6147804934346.0,
+                11782306865191.0 / 62590030070788.0, 9452544825720.0 / 13648368537481.0,
+                4435885630781.0 / 26285702406235.0, 2357909744247.0 / 11371140753790.0]
+LSRK59_KCL_B = [2274579626619.0 / 23610510767302.0, 693987741272.0 / 12394497460941.0,
+                -347131529483.0 / 15096185902911.0, 1144057200723.0 / 32081666971178.0,
+                1562491064753.0 / 11797114684756.0, 13113619727965.0 / 44346030145118.0,
+                393957816125.0 / 7825732611452.0, 720647959663.0 / 6565743875477.0,
+                3559252274877.0 / 14424734981077.0]
 
 
 def face_tangential_axes(f):
@@ -250,6 +278,25 @@ class Oracle:
                 R = self.apply(U)
                 dU = A[s] * dU + dt * R
                 U = U + B[s] * dU
+            if callback is not None:
+                callback(step, U)
+        return U
+
+    def lsrk2r(self, U, dt, nsteps, A=LSRK59_KCL_A, B=LSRK59_KCL_B, callback=None):
+        """nsteps of a two-register low-storage Runge-Kutta scheme: with
+        k_i = R(Y_i), Y_1 = u_n and S_i = u_n + dt sum_{j<i} B_j k_j,
+        Y_{i+1} = S_i + dt A_i k_i and u_{n+1} = S_{s+1}."""
+        U = np.array(U, float, copy=True)
+        s = len(B)
+        for step in range(nsteps):
+            acc = U.copy()
+            Y = U
+            for i in range(s):
+                R = self.apply(Y)
+                if i < s - 1:
+                    Y = acc + dt * A[i] * R
+                acc = acc + dt * B[i] * R
+            U = acc
             if callback is not None:
                 callback(step, U)
         return U

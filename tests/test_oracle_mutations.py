@@ -355,3 +355,141 @@ def test_2d_pins_catch_planted_mistakes():
     def flip(o):
         o.alpha = -1.0
     assert _energy_rate_2d(1.0, flip) > 1e-4
+
+
+# --- diagnostics: energy and L2 error closed forms -------------------------
+import types
+
+from oracle.basis import basis_3d, tensor_weights
+import test_oracle_energy_norms as en
+
+
+def _energy_closed_form(mutate=None, dim=3, k=2):
+    N = 3
+    mesh = en._graded_mesh(dim, N)
+    x = en._box_nodes(mesh, k, dim)
+    E, npts = x.shape[0], x.shape[1]
+    U = np.zeros((E, dim + 1, npts))
+    U[:, 0] = 1.0 + x[..., 0]
+    U[:, 1] = U[:, 2] = 1.0
+    o = en._make(dim, mesh, k, 1.0 + x[..., 0], np.full((E, npts), 2.0))
+    if mutate:
+        mutate(o)
+    return abs(o.energy(U) - 27.0 / 16.0)
+
+
+def _energy_density(o, U, pressure_weight, velocity_weight, half=0.5):
+    u = np.einsum("qa,eva->evq", o.Phi, np.asarray(U, float))
+    dens = velocity_weight(o) * np.sum(u[:, 1:] ** 2, axis=1) + pressure_weight(o) * u[:, 0] ** 2
+    return half * float(np.sum(o.wdet * dens))
+
+
+def _no_half(o):
+    o.energy = types.MethodType(
+        lambda self, U: _energy_density(self, U, lambda s: 1 / (s.rho_q * s.c_q ** 2), lambda s: s.rho_q, 1.0), o)
+
+
+def _pressure_times_impedance(o):
+    o.energy = types.MethodType(
+        lambda self, U: _energy_density(self, U, lambda s: s.rho_q * s.c_q ** 2, lambda s: s.rho_q), o)
+
+
+def _velocity_without_density(o):
+    o.energy = types.MethodType(
+        lambda self, U: _energy_density(self, U, lambda s: 1 / (s.rho_q * s.c_q ** 2), lambda s: 1.0), o)
+
+
+@pytest.mark.parametrize("mutant", [_no_half, _pressure_times_impedance, _velocity_without_density])
+def test_energy_closed_form_pin_catches(mutant):
+    assert _energy_closed_form() < 1e-13
+    assert _energy_closed_form(mutant) > 1e-2, mutant.__name__
+
+
+def test_energy_closed_form_pin_catches_2d_dropped_half():
+    assert _energy_closed_form(dim=2) < 1e-13
+    bad = lambda o: setattr(o, "energy", types.MethodType(lambda self, U: 2 * type(self).energy(self, U), o))
+    assert _energy_closed_form(bad, dim=2) > 1e-2
+
+
+def _l2_closed_form(mutate=None):
+    k, N = 2, 3
+    mesh = en._graded_mesh(3, N)
+    x = en._box_nodes(mesh, k, 3)
+    E, npts = x.shape[0], x.shape[1]
+    ones = np.ones((E, npts))
+    o = oracle.Oracle(mesh, k, ones, ones, 1.0)
+    if mutate:
+        mutate(o)
+    U = np.zeros((E, 4, npts))
+    U[:, 0] = 0.5
+    U[:, 1] = x[..., 0]
+
+    def exact(xx, t):
+        out = np.zeros(xx.shape[:-1] + (4,))
+        out[..., 0] = out[..., 1] = xx[..., 0]
+        out[..., 2] = xx[..., 1]
+        return out
+    ep, ev = o.l2_error(U, exact, 0.0)
+    return max(abs(ep - 0.5), abs(ev - np.sqrt(0.5)))
+
+
+def _l2_variant(o, use_detJ=True, mapped=True):
+    """l2_error written again with one planted change."""
+    def f(self, U, exact, t, extra=2):
+        xe, we = gauss_1d(self.n + extra)
+        Qe = tensor_points(xe)
+        phi = basis_3d(self.xgl, Qe)
+        x = self.positions(Qe) if mapped else np.broadcast_to(Qe, (self.E,) + Qe.shape)
+        wd = tensor_weights(we)[None, :] * (np.linalg.det(self.jacobian(Qe)) if use_detJ else 1.0)
+        uh = np.einsum("qa,eva->eqv", phi, np.asarray(U, float))
+        ue = exact(x, t)
+        ep = np.sum(wd * (uh[..., 0] - ue[..., 0]) ** 2) / np.sum(wd * ue[..., 0] ** 2)
+        ev = np.sum(wd[..., None] * (uh[..., 1:] - ue[..., 1:]) ** 2) / np.sum(wd[..., None] * ue[..., 1:] ** 2)
+        return float(np.sqrt(ep)), float(np.sqrt(ev))
+    o.l2_error = types.MethodType(f, o)
+
+
+def test_l2_closed_form_pin_catches():
+    assert _l2_closed_form() < 1e-13
+    assert _l2_closed_form(lambda o: _l2_variant(o)) < 1e-13          # the restatement itself is right
+    assert _l2_closed_form(lambda o: _l2_variant(o, use_detJ=False)) > 1e-3
+    assert _l2_closed_form(lambda o: _l2_variant(o, mapped=False)) > 1e-3
+
+
+# --- the two-register LSRK schemes ----------------------------------------
+def test_2r_order_conditions_catch_a_coefficient_typo():
+    from oracle import LSRK59_KCL_A, LSRK59_KCL_B
+    from test_oracle_lsrk2r import butcher, order_conditions
+    res = order_conditions(*butcher(LSRK59_KCL_A, LSRK59_KCL_B))
+    assert max(abs(r) for q in res for r in res[q]) < 1e-14
+    A = list(LSRK59_KCL_A)
+    A[4] *= 1.000001                                     # sixth digit of one coefficient
+    res = order_conditions(*butcher(A, LSRK59_KCL_B))
+    assert max(abs(r) for q in res for r in res[q]) > 1e-8
+
+
+def test_2r_step_pin_catches_a_loop_that_restarts_from_u():
+    """A two-register loop that builds every stage from u_n instead of the
+    running sum S_i fails the step-equals-polynomial pin."""
+    from oracle import LSRK59_KCL_A, LSRK59_KCL_B
+    from test_oracle_lsrk2r import stability_poly_2r
+    cfg = synth.configs.curved_pulse(N=2, k=2)
+    o = oracle.Oracle(cfg["mesh"], 2, cfg["rho"], cfg["c"], 1.0)
+    U0 = synth.configs.random_state(8, 2, 3)
+    dt = 0.01
+    g = stability_poly_2r(LSRK59_KCL_A, LSRK59_KCL_B)
+    acc, term = g[0] * U0, U0
+    for j in range(1, len(g)):
+        term = dt * o.apply(term)
+        acc = acc + g[j] * term
+
+    def wrong(U):
+        s, Y, S = len(LSRK59_KCL_B), U, U.copy()
+        for i in range(s):
+            R = o.apply(Y)
+            if i < s - 1:
+                Y = U + dt * LSRK59_KCL_A[i] * R
+            S = S + dt * LSRK59_KCL_B[i] * R
+        return S
+    assert np.abs(o.lsrk2r(U0, dt, 1) - acc).max() / np.abs(U0).max() < 1e-14
+    assert np.abs(wrong(U0) - acc).max() / np.abs(U0).max() > 1e-8
