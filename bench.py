@@ -79,6 +79,10 @@ def parse():
                     help="instead of timing: run this many steps of each method in FP32 and FP64 "
                          "and report the relative l2 differences and errors against the exact plane wave")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32, batched and served forms measured beside the headline")
+    ap.add_argument("--batch-steps", type=int, default=500,
+                    help="batched form: ADER steps of every instance (500 in the configured workload)")
     ap.add_argument("--cpu-steps", type=int, default=0,
                     help="steps of the oracle's sample (default: 20 on the 4^3 curved pulse, 2 on larger samples)")
     ap.add_argument("--cpu-size", type=int, default=0,
@@ -187,31 +191,69 @@ o = oracle.Oracle(cfg["mesh"], {k}, cfg["rho"], cfg["c"], 1.0)
 U1 = cfg["U0"].copy(); U2 = cfg["U0"].copy()
 for _ in range({warm}):
     U1 = o.lsrk(U1, cfg["dt"], 1); U2 = o.ader(U2, cfg["dt"], 1, 2)
+while time.time() < {t_start}:
+    time.sleep(0.01)
 times = []
+w0 = time.time()
 for _ in range({steps}):
     t0 = time.perf_counter()
     U1 = o.lsrk(U1, cfg["dt"], 1); U2 = o.ader(U2, cfg["dt"], 1, 2)
     times.append(time.perf_counter() - t0)
-print(json.dumps({{"times": times, "dof": int(U1.size)}}))
+print(json.dumps({{"times": times, "dof": int(U1.size), "w0": w0, "w1": time.time()}}))
 """
 
 
-def run_oracle(n, k, warm, steps, workload="curved_pulse"):
+def run_oracle(n, k, warm, steps, workload="curved_pulse", procs=1, start_delay=0.0):
+    """The oracle as it stands, one LSRK and one ADER step per timed step,
+    on ``procs`` host cores at once: that many independent single-threaded
+    copies of the same sample, started together (each waits for a common
+    wall-clock start after its set-up).  Returns (DoF-steps/s of all copies
+    over the span from the first start to the last end, that span, details)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = CPU_SNIPPET.format(root=ROOT, n=n, k=k, warm=warm, steps=steps, workload=workload)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode != 0:
-        raise RuntimeError("oracle run failed: " + r.stderr[-2000:])
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    total = sum(out["times"])
-    return 2 * out["dof"] * len(out["times"]) / total, total, out
+    t_start = time.time() + start_delay if procs > 1 else 0.0
+    code = CPU_SNIPPET.format(root=ROOT, n=n, k=k, warm=warm, steps=steps, workload=workload, t_start=t_start)
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                           text=True, env=env) for _ in range(procs)]
+    outs = []
+    for p in ps:
+        so, se = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("oracle run failed: " + se[-2000:])
+        outs.append(json.loads(so.strip().splitlines()[-1]))
+    if procs == 1:
+        total = sum(outs[0]["times"])
+    else:
+        total = max(o["w1"] for o in outs) - min(o["w0"] for o in outs)
+    work = sum(2 * o["dof"] * len(o["times"]) for o in outs)
+    return work / total, total, {"procs": procs, "per_copy_seconds": [sum(o["times"]) for o in outs]}
 
 
-def cpu_sample_desc(n, k, steps, workload="curved_pulse"):
-    return (f"FP64 oracle (dense element matrices, numpy, 1 thread) on the {n}^3-element instance of "
+def cpu_sample_desc(n, k, steps, workload="curved_pulse", procs=1):
+    who = ("numpy, 1 thread" if procs == 1 else
+           f"numpy, {procs} single-threaded copies of the sample running at once, one per host core")
+    return (f"FP64 oracle (dense element matrices, {who}) on the {n}^3-element instance of "
             f"the same {workload} recipe (k={k}, {4 * (k + 1) ** 3 * n ** 3} DoF): {steps} steps of 1 LSRK + "
             f"1 ADER step, oracle set-up excluded")
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(n, k, steps, workload):
+    """The oracle on every host core, with the single-thread figure beside it."""
+    cores = host_cores()
+    v1, t1, _ = run_oracle(n, k, 1, steps, workload)
+    vp, tp, det = run_oracle(n, k, 1, steps, workload, procs=cores, start_delay=15.0 + 0.2 * cores)
+    return {"value": vp, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": cpu_sample_desc(n, k, steps, workload, cores), "seconds": tp,
+            "single_thread": {"value": v1, "cores": 1, "seconds": t1,
+                              "sample": cpu_sample_desc(n, k, steps, workload)},
+            "per_copy_seconds": det["per_copy_seconds"]}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -220,19 +262,206 @@ def reference_arm(args):
     if rank != 0:
         return 0
     n = 4
-    value, total, out = run_oracle(n, args.k, args.warmup, args.steps)
+    cores = host_cores()
+    value, total, det = run_oracle(n, args.k, args.warmup, args.steps, procs=cores, start_delay=15.0 + 0.2 * cores)
+    sample = cpu_sample_desc(n, args.k, args.steps, procs=cores)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": workload_desc(args.size, args.k, "fp64"),
-                                        "sample": cpu_sample_desc(n, args.k, args.steps)},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": cpu_sample_desc(n, args.k, args.steps)},
+                                        "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+# ------------------------------------------------------------------ shared timing
+def make_solver(args, cfg, prec, dgw, basis=None, pred=None, tiling=None):
+    """A solver on cfg in the bench's configuration: state basis, predictor
+    form, and elements per block autotuned for this workload (results do not
+    depend on the tiling)."""
+    from paper_1805_03981_gb300 import autotune
+    basis = args.basis if basis is None else basis
+    pred = args.pred if pred is None else pred
+    tiling = args.tiling if tiling is None else tiling
+    s = dgw.Solver(cfg["mesh"], cfg["k"], prec, cfg["alpha"], cfg["rho"], cfg["c"])
+    s.set_basis(dgw.BASIS_G if basis == "g" else dgw.BASIS_GL)
+    s.set_predictor_kernel({"auto": dgw.PRED_AUTO, "lines": dgw.PRED_LINES, "columns": dgw.PRED_COLUMNS}[pred])
+    if tiling:
+        s.set_tiling(*(int(x) for x in tiling.split(",")))
+    else:
+        for kind in (dgw.KIND_LSRK, dgw.KIND_TCK):
+            s.tune(kind, autotune.CANDIDATES, reps=2)
+    return s
+
+
+def time_steps(args, s, cfg, dgw, torch, barrier, local, steps=None, warmup=None):
+    """W untimed steps, then K steps of each method (one stepper call per
+    method, as a solve runs; with the Gauss basis a call changes basis once
+    on entry and once on exit), timed with CUDA events on the launching
+    stream, with the library's per-kernel event profile and the clocks
+    sampled meanwhile."""
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    dt = cfg["dt"]
+    U_l = s.to_device(cfg["U0"])
+    U_a = s.to_device(cfg["U0"])
+    stream = torch.cuda.current_stream()
+    s.step_lsrk(U_l, dt, warmup)
+    s.step_ader(U_a, dt, warmup, 2)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    s.profile(True)
+    s.profile_read(reset=True)
+    launches0 = s.launch_count()
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step_lsrk(U_l, dt, steps)
+    s.step_ader(U_a, dt, steps, 2)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count() - launches0
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+    clk = clocks.stop()
+    dof = 4 * (cfg["k"] + 1) ** 3 * cfg["mesh"]["n_elem"]
+    t_lsrk = prof["lsrk_stage"][0]
+    t_ader = prof["ader_update"][0] + prof["tck"][0]
+    per_method = {"lsrk": dof * steps / (t_lsrk * 1e-3) if t_lsrk else None,
+                  "ader": dof * steps / (t_ader * 1e-3) if t_ader else None}
+    return {"ms": ms, "prof": prof, "launches": launches, "clocks": clk, "per_method": per_method,
+            "U_l": U_l, "U_a": U_a, "steps": steps, "warmup": warmup}
+
+
+_PROBE = {}
+
+
+def _probe_peak(dgw, prec):
+    """FMA-pipe TFLOP/s of this GPU, measured once per precision."""
+    if prec not in _PROBE:
+        try:
+            _PROBE[prec] = dgw.probe_fma_peak(prec, 4096 if prec == dgw.DG_FP64 else 65536)
+        except Exception:
+            _PROBE[prec] = None
+    return _PROBE[prec]
+
+
+def roofline(args, s, prof, N, k, prec, dgw, tiling, workload_name, basis):
+    """Roofline of the dominant kernel: algorithmic flops (FP64 pipe, or FP32
+    pipe when the arithmetic intensity puts it above the HBM roof) or bytes
+    per launch over its average launch time from the event profile."""
+    from paper_1805_03981_gb300 import opcount, traffic
+    rsize = 8 if prec == dgw.DG_FP64 else 4
+    dom = max(prof, key=lambda kk: prof[kk][0])
+    tot_ms, nlaunch = prof[dom]
+    avg_s = tot_ms * 1e-3 / max(nlaunch, 1)
+    E = N ** 3
+    nonwall = 1.0 if workload_name == "plane_wave" else 1.0 - 1.0 / N
+    aff = s.is_affine()
+    flops = opcount.flops_per_element(dom, k + 1, 2, nonwall, basis, aff) * E
+    byts = opcount.bytes_per_element(dom, k + 1, rsize, 2, affine=aff and (basis == "g" or dom == "tck")) * E
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get("hbm_gbs")
+    if prec == dgw.DG_FP64:
+        roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": FP64_PEAK / 1e12,
+                "unit": "TFLOP/s", "peak_source": "derived FP64 pipe: 152 SM x 2 FMA/clk x 2 x 2.07 GHz"}
+    else:
+        ai = flops / byts
+        peak_hbm = (hbm or HBM_FALLBACK) * 1e9
+        if ai * peak_hbm > FP32_PEAK:
+            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": FP32_PEAK / 1e12,
+                    "unit": "TFLOP/s", "peak_source": "derived FP32 pipe: 152 SM x 128 FMA/clk x 2 x 2.07 GHz"}
+        else:
+            roof = {"bound": "hbm", "achieved": byts / avg_s / 1e9, "peak": hbm or HBM_FALLBACK,
+                    "unit": "GB/s", "peak_source": "measured" if hbm else "fallback"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    if roof["bound"] == "alu":
+        # the same pipe measured on this GPU by an FMA probe (dg_probe_fma_peak),
+        # beside the derived nominal peak
+        probe = _probe_peak(dgw, prec)
+        roof["probe_peak"] = probe
+        roof["frac_of_probe"] = roof["achieved"] / probe if probe else None
+    roof["kernel"] = dom
+    # DRAM bytes per launch from the ncu table, when it was taken on these
+    # sources and this launch configuration (else null)
+    roof["traffic"] = traffic.lookup(workload_name, "fp64" if prec == dgw.DG_FP64 else "fp32", N, k, basis,
+                                     tiling, dom)
+    roof["traffic_source"] = ("profiles/dram_traffic.txt (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
+                              if roof["traffic"] is not None else
+                              "none recorded for these sources and this launch configuration")
+    roof["per_launch_ms"] = avg_s * 1e3
+    roof["algorithmic_flops_per_launch"] = flops
+    roof["algorithmic_bytes_per_launch"] = byts
+    return roof
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def precision_form(args, dgw, torch, barrier, local, N=64, k=4):
+    """The precision form on its own workload: the plane wave on the 64^3
+    periodic affine mesh at k = 4, FP32 operator and state with FP64
+    geometry set-up; timed like the headline (W + K steps of each method),
+    then the final states compared with the FP64 path after the same steps
+    and with the exact solution at the nodes."""
+    cfg = workload(N, k, "plane_wave")
+    s = make_solver(args, cfg, dgw.DG_FP32, dgw, basis="g", pred="auto", tiling="")
+    tiling = s.tiling()
+    m = time_steps(args, s, cfg, dgw, torch, barrier, local)
+    dof = 4 * (k + 1) ** 3 * N ** 3
+    out = {"workload": workload_desc(N, k, "fp32", "plane_wave"), "dtype": "f32",
+           "value": 2 * dof * m["steps"] / (m["ms"] * 1e-3), "unit": UNIT, "ms_per_step": m["ms"] / m["steps"],
+           "per_method_dofs_per_s": m["per_method"],
+           "kernel_ms": {kk: {"total_ms": v[0], "launches": v[1]} for kk, v in m["prof"].items() if v[1]},
+           "roofline": roofline(args, s, m["prof"], N, k, dgw.DG_FP32, dgw, tiling, "plane_wave", "g"),
+           "tiling_elements_per_block": {"operator": tiling[0], "tck": tiling[1]},
+           "gpu_launches": m["launches"], "clocks": m["clocks"]}
+    nst = m["steps"] + m["warmup"]
+    u32 = {"lsrk": m["U_l"].double().cpu().numpy(), "ader": m["U_a"].double().cpu().numpy()}
+    s.close()
+    del m
+    s64 = make_solver(args, cfg, dgw.DG_FP64, dgw, basis="g", pred="auto", tiling="5,5")
+    exact = np.transpose(cfg["exact"](cfg["xnodes"], nst * cfg["dt"]), (0, 2, 1))
+    acc = {"steps": nst}
+    for method in ("lsrk", "ader"):
+        U = s64.to_device(cfg["U0"])
+        if method == "lsrk":
+            s64.step_lsrk(U, cfg["dt"], nst)
+        else:
+            s64.step_ader(U, cfg["dt"], nst, 2)
+        torch.cuda.synchronize()
+        u64 = U.cpu().numpy()
+        del U
+        acc[method] = {"fp32_vs_fp64_rel_l2": _rel(u32[method], u64),
+                       "fp32_vs_exact_nodal_rel_l2": _rel(u32[method], exact),
+                       "fp64_vs_exact_nodal_rel_l2": _rel(u64, exact)}
+    s64.close()
+    out["accuracy_after_timed_steps"] = acc
+    return out
+
+
+def measure_forms(args, dgw, torch, barrier, local):
+    """The precision, batched and served forms, each measured in this run
+    beside the FP64 headline."""
+    forms = {}
+    t0 = time.perf_counter()
+    forms["precision_fp32"] = precision_form(args, dgw, torch, barrier, local)
+    forms["precision_fp32"]["wall_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    forms["batched_fp32"] = batched_measure(args, dgw, torch, steps=args.batch_steps)
+    forms["batched_fp32"]["wall_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    forms["served_fp32"] = served_measure(args, dgw, torch)
+    forms["served_fp32"]["wall_s"] = time.perf_counter() - t0
+    return forms
 
 
 # ------------------------------------------------------------------ precision study
@@ -534,83 +763,100 @@ def basis_change_bench(args, dgw, torch):
     return 0
 
 
-def batched_bench(args, dgw, torch):
+def batched_measure(args, dgw, torch, steps=None, fp64_every=8):
     """256 independent seeded solves (N ~ U{4..24} elements per axis, k ~
     U{2..7}, random smooth rho and c in [0.55, 1.95], curving <= 0.05, walls,
     Gaussian pulses), FP32 ADER (order k+1, reduction every 2nd derivative).
-    Times the batched persistent form against the same solves run one at a
-    time in FP32 and in FP64."""
-    import synth
+    Times the batched persistent form (8 warm-up steps, then ``steps``)
+    against the same solves run one at a time in FP32, and in FP64 on every
+    ``fp64_every``-th instance, which also gives each of those instances'
+    relative l2 difference between the batched FP32 result and FP64 after
+    the same steps."""
     from paper_1805_03981_gb300 import autotune
     table = autotune.load(args.autotune) if args.autotune else None
     n = args.instances
+    steps = args.steps if steps is None else steps
+    warm = 8
     t_gen = time.perf_counter()
     cfgs = generate_instances([4 * 10 ** 6 + i for i in range(n)])
     dof = [4 * (c["k"] + 1) ** 3 * c["mesh"]["n_elem"] for c in cfgs]
     total = sum(dof)
-    steps = args.steps
     t_gen = time.perf_counter() - t_gen
     out = {"workload": f"batched: {n} instances, N~U{{4..24}}^3 curved hexahedra, k~U{{2..7}}, seeded rho/c/pulses, "
-                       f"ADER order k+1", "total_dof": total, "steps": steps, "state_basis": args.basis,
+                       f"ADER order k+1", "total_dof": total, "steps": steps, "warmup": warm,
+           "state_basis": args.basis, "dtype": "f32",
            "k_histogram": {str(k): sum(1 for c in cfgs if c["k"] == k) for k in range(2, 8)}}
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
     t_setup = time.perf_counter()
     solvers = [dgw.Solver(c["mesh"], c["k"], dgw.DG_FP32, 1.0, c["rho"], c["c"]) for c in cfgs]
-    for s in solvers:
-        s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
+    for sv in solvers:
+        sv.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
         if table:
-            autotune.apply(s, table)
-    states = [s.to_device(c["U0"]) for s, c in zip(solvers, cfgs)]
+            autotune.apply(sv, table)
+    states = [sv.to_device(c["U0"]) for sv, c in zip(solvers, cfgs)]
     out["setup_s"] = time.perf_counter() - t_setup
     out["host_generation_s"] = t_gen
     b = dgw.Batch(solvers, states, [c["dt"] for c in cfgs])
     b.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL, convert_each_call=True)
-    b.step_ader(8, 2)
+    b.step_ader(warm, 2)
     torch.cuda.synchronize()
     ev0.record(stream)
     b.step_ader(steps, 2)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    out["batched_fp32"] = {"dofs_per_s": total * steps / (ms * 1e-3), "ms_per_step": ms / steps,
-                           "info": b.info()}
+    out["value"] = total * steps / (ms * 1e-3)
+    out["unit"] = UNIT
+    out["batched_fp32"] = {"dofs_per_s": out["value"], "ms_per_step": ms / steps, "info": b.info()}
+    sample = list(range(0, n, fp64_every))
+    final32 = {i: states[i].double().cpu().numpy() for i in sample}
     # one solve at a time, FP32, same steps
-    for s, c, U in zip(solvers, cfgs, states):
-        s.step_ader(U, c["dt"], 2, 2)
+    for sv, c, U in zip(solvers, cfgs, states):
+        sv.step_ader(U, c["dt"], 2, 2)
     torch.cuda.synchronize()
     ev0.record(stream)
-    for s, c, U in zip(solvers, cfgs, states):
-        s.step_ader(U, c["dt"], steps, 2)
+    for sv, c, U in zip(solvers, cfgs, states):
+        sv.step_ader(U, c["dt"], steps, 2)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms1 = ev0.elapsed_time(ev1)
     out["one_at_a_time_fp32"] = {"dofs_per_s": total * steps / (ms1 * 1e-3), "ms_per_step": ms1 / steps}
     b.close()
-    for s in solvers:
-        s.close()
+    for sv in solvers:
+        sv.close()
     del states
-    # one solve at a time, FP64 (contexts created and freed one by one)
-    st64 = max(1, steps // 4)
-    ms64 = 0.0
-    for c in cfgs:
-        s = dgw.Solver(c["mesh"], c["k"], dgw.DG_FP64, 1.0, c["rho"], c["c"])
-        s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
-        U = s.to_device(c["U0"])
-        s.step_ader(U, c["dt"], 1, 2)
+    # one solve at a time, FP64, on the sampled instances (contexts created
+    # and freed one by one): warm + steps steps from the same initial state
+    ms64, dof64, errs = 0.0, 0, []
+    for i in sample:
+        c = cfgs[i]
+        sv = dgw.Solver(c["mesh"], c["k"], dgw.DG_FP64, 1.0, c["rho"], c["c"])
+        sv.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
+        U = sv.to_device(c["U0"])
+        sv.step_ader(U, c["dt"], warm, 2)
         torch.cuda.synchronize()
         ev0.record(stream)
-        s.step_ader(U, c["dt"], st64, 2)
+        sv.step_ader(U, c["dt"], steps, 2)
         ev1.record(stream)
         torch.cuda.synchronize()
         ms64 += ev0.elapsed_time(ev1)
-        s.close()
-    out["one_at_a_time_fp64"] = {"dofs_per_s": total * st64 / (ms64 * 1e-3), "ms_per_step": ms64 / st64}
+        dof64 += dof[i]
+        errs.append(_rel(final32[i], U.cpu().numpy()))
+        sv.close()
+    out["one_at_a_time_fp64"] = {"dofs_per_s": dof64 * steps / (ms64 * 1e-3), "ms_per_step_sample": ms64 / steps,
+                                 "instances_timed": len(sample)}
+    out["fp32_vs_fp64_rel_l2"] = {"max": max(errs), "median": float(np.median(errs)), "instances": len(errs),
+                                  "steps": warm + steps}
     out["speedup_batched_fp32_vs_fp64_one_at_a_time"] = (out["batched_fp32"]["dofs_per_s"]
                                                           / out["one_at_a_time_fp64"]["dofs_per_s"])
     out["speedup_batched_vs_one_at_a_time_fp32"] = (out["batched_fp32"]["dofs_per_s"]
                                                      / out["one_at_a_time_fp32"]["dofs_per_s"])
-    print(json.dumps({"batched": out}))
+    return out
+
+
+def batched_bench(args, dgw, torch):
+    print(json.dumps({"batched": batched_measure(args, dgw, torch)}))
     return 0
 
 
@@ -625,11 +871,15 @@ def _gen_request(spec):
     return c
 
 
-def served_bench(args, dgw, torch):
+def served_measure(args, dgw, torch):
     """Poisson stream of FP32 ADER solves (seed 5): cube meshes with N ~
     U{nmin..nmax} elements per axis, k ~ U{3,5,7}, seeded coefficient fields
     and pulses, U{smin..smax} steps at Cr = 0.1, against an HBM budget.
-    Arrivals are replayed in real time; latency = completion - arrival."""
+    Arrivals are replayed in real time; latency = completion - arrival.
+    Beside it, the FP64 one-at-a-time form: one completed request per degree
+    is solved again in FP64, which gives the FP64 service rates of the
+    modelled FIFO queue and the relative l2 difference of the served FP32
+    result from FP64 at the same steps."""
     import concurrent.futures as cf
     import multiprocessing as mp
     rng = np.random.default_rng(5)
@@ -692,20 +942,25 @@ def served_bench(args, dgw, torch):
            "backlog_at_end_of_arrivals": backlog_at_end, "host_generation_s": t_gen,
            "server": {k: st[k] for k in ("peak_active", "rounds", "batches_built", "hbm_peak", "busy_s")}}
     # FP64 one-at-a-time, modelled: measured FP64 ADER rate per degree on one
-    # request each, replayed through a single-server FIFO over the same arrivals
-    rate64 = {}
+    # completed request each (its whole solve), replayed through a
+    # single-server FIFO over the same arrivals
+    rate64, diff64 = {}, {}
     for k in (3, 5, 7):
-        i = next(j for j, c in enumerate(reqs) if c["k"] == k)
+        cands = [j for j in sorted(done) if reqs[j]["k"] == k] or [j for j, c in enumerate(reqs) if c["k"] == k]
+        if not cands:
+            continue
+        i = cands[0]
         c = reqs[i]
         s = dgw.Solver(c["mesh"], k, dgw.DG_FP64, 1.0, c["rho"], c["c"])
         s.set_basis(dgw.BASIS_G)
         U = s.to_device(c["U0"].astype(np.float64))
-        s.step_ader(U, c["dt"], 1, 2)
         torch.cuda.synchronize()
         ta = time.perf_counter()
-        s.step_ader(U, c["dt"], 8, 2)
+        s.step_ader(U, c["dt"], c["nsteps"], 2)
         torch.cuda.synchronize()
-        rate64[k] = dofs[i] * 8 / (time.perf_counter() - ta)
+        rate64[k] = dofs[i] * c["nsteps"] / (time.perf_counter() - ta)
+        if i in done:
+            diff64[k] = _rel(done[i]["out"].astype(np.float64), U.cpu().numpy())
         s.close()
     free_at, lat64 = 0.0, []
     for ta, c, wk in zip(arrivals, reqs, work):
@@ -717,7 +972,15 @@ def served_bench(args, dgw, torch):
         "rate_dofs_per_s_by_k": rate64, "throughput_dofs_per_s": float(work.sum() / (free_at - arrivals[0])),
         "latency_s": {"p50": float(np.percentile(lat64, 50)), "p99": float(np.percentile(lat64, 99))},
         "note": "modelled: measured FP64 service rates replayed through a single-server FIFO queue"}
-    print(json.dumps({"served": out}))
+    out["fp32_vs_fp64_rel_l2_by_k"] = diff64
+    out["value"] = out["throughput_dofs_per_s"]
+    out["unit"] = UNIT
+    out["dtype"] = "f32"
+    return out
+
+
+def served_bench(args, dgw, torch):
+    print(json.dumps({"served": served_measure(args, dgw, torch)}))
     return 0
 
 
@@ -763,90 +1026,15 @@ def main():
     cfg = workload(N, k, args.workload)
     if args.accuracy:
         return accuracy_study(args, cfg, dgw, torch)
-    s = dgw.Solver(cfg["mesh"], k, prec, cfg["alpha"], cfg["rho"], cfg["c"])
-    s.set_basis(dgw.BASIS_G if args.basis == "g" else dgw.BASIS_GL)
-    s.set_predictor_kernel({"auto": dgw.PRED_AUTO, "lines": dgw.PRED_LINES, "columns": dgw.PRED_COLUMNS}[args.pred])
-    # autotune the tiling of this workload's kernels (results do not depend on it)
-    from paper_1805_03981_gb300 import autotune
-    if args.tiling:
-        s.set_tiling(*(int(x) for x in args.tiling.split(",")))
-    else:
-        for kind in (dgw.KIND_LSRK, dgw.KIND_TCK):
-            s.tune(kind, autotune.CANDIDATES, reps=2)
+    s = make_solver(args, cfg, prec, dgw)
     tiling = s.tiling()
     dof = 4 * (k + 1) ** 3 * N ** 3
     dt = cfg["dt"]
-    U_l = s.to_device(cfg["U0"])
-    U_a = s.to_device(cfg["U0"])
-    stream = torch.cuda.current_stream()
-
-    # one call per method advances K steps, as a solve does (with the Gauss
-    # basis the state changes basis once on entry and once on exit of a call)
-    s.step_lsrk(U_l, dt, args.warmup)
-    s.step_ader(U_a, dt, args.warmup, 2)
-    barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    s.profile(True)
-    s.profile_read(reset=True)
-    launches0 = s.launch_count()
-    barrier()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    s.step_lsrk(U_l, dt, args.steps)
-    s.step_ader(U_a, dt, args.steps, 2)
-    ev1.record(stream)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    launches = s.launch_count() - launches0
-    prof = s.profile_read(reset=True)
-    s.profile(False)
-    clk = clocks.stop()
-    ms_max = max_over_ranks(ms)
+    m = time_steps(args, s, cfg, dgw, torch, barrier, local)
+    ms_max = max_over_ranks(m["ms"])
     value = job_value(2 * dof * args.steps, ms_max, world)
-
-    # per-method rates from the profile (device time per kind)
-    t_lsrk = prof["lsrk_stage"][0]
-    t_ader = prof["ader_update"][0] + prof["tck"][0]
-    per_method = {"lsrk": dof * args.steps / (t_lsrk * 1e-3) if t_lsrk else None,
-                  "ader": dof * args.steps / (t_ader * 1e-3) if t_ader else None}
-
-    # dominant kernel and its roofline
-    rsize = 8 if prec == dgw.DG_FP64 else 4
-    dom = max(prof, key=lambda kk: prof[kk][0])
-    tot_ms, nlaunch = prof[dom]
-    avg_s = tot_ms * 1e-3 / max(nlaunch, 1)
-    E = N ** 3
-    nonwall = 1.0 if args.workload == "plane_wave" else 1.0 - 1.0 / N
-    aff = s.is_affine()
-    flops = opcount.flops_per_element(dom, k + 1, 2, nonwall, args.basis, aff) * E
-    byts = opcount.bytes_per_element(dom, k + 1, rsize, 2, affine=aff and (args.basis == "g" or dom == "tck")) * E
-    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-    hbm = peaks.get("hbm_gbs")
-    if prec == dgw.DG_FP64:
-        roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": FP64_PEAK / 1e12,
-                "unit": "TFLOP/s", "peak_source": "derived FP64 pipe: 152 SM x 2 FMA/clk x 2 x 2.07 GHz"}
-    else:
-        ai = flops / byts
-        peak_hbm = (hbm or HBM_FALLBACK) * 1e9
-        if ai * peak_hbm > FP32_PEAK:
-            roof = {"bound": "alu", "achieved": flops / avg_s / 1e12, "peak": FP32_PEAK / 1e12,
-                    "unit": "TFLOP/s", "peak_source": "derived FP32 pipe: 152 SM x 128 FMA/clk x 2 x 2.07 GHz"}
-        else:
-            roof = {"bound": "hbm", "achieved": byts / avg_s / 1e9, "peak": hbm or HBM_FALLBACK,
-                    "unit": "GB/s", "peak_source": "measured" if hbm else "fallback"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = dom
-    # DRAM bytes per launch from the ncu table, when it was taken on these
-    # sources and this launch configuration (else null)
-    roof["traffic"] = traffic.lookup(args.workload, args.prec, N, k, args.basis, tiling, dom)
-    roof["traffic_source"] = ("profiles/dram_traffic.txt (ncu dram__bytes_read.sum + dram__bytes_write.sum)"
-                              if roof["traffic"] is not None else
-                              "none recorded for these sources and this launch configuration")
-    roof["per_launch_ms"] = avg_s * 1e3
-    roof["algorithmic_flops_per_launch"] = flops
-    roof["algorithmic_bytes_per_launch"] = byts
+    prof, launches, clk, per_method = m["prof"], m["launches"], m["clocks"], m["per_method"]
+    roof = roofline(args, s, prof, N, k, prec, dgw, tiling, args.workload, args.basis)
 
     # e2e through the C ABI with host buffers (pinned), copies inside the timing
     Uh = torch.from_numpy(np.ascontiguousarray(cfg["U0"])).to(s.dtype).pin_memory()
@@ -875,17 +1063,23 @@ def main():
            "note": "each step, per method: dg_solve_host copies the state in from pinned host memory, "
                    "advances one step and copies it back",
            "k_steps_per_call_value": world * 2 * dof * args.steps / solve_s}
+    device_mb = s.device_bytes() >> 20
+    m_affine = s.is_affine()
+    s.close()
+    del m
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("curved_pulse", "plane_wave"):
         try:
             n_cpu = args.cpu_size or (4 if args.workload == "curved_pulse" else 16)
             st_cpu = args.cpu_steps or (20 if n_cpu <= 4 else 2)
-            v, total, _ = run_oracle(n_cpu, k, 1, st_cpu, args.workload)
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": cpu_sample_desc(n_cpu, k, st_cpu, args.workload), "seconds": total}
+            cpu = cpu_baseline(n_cpu, k, st_cpu, args.workload)
         except Exception as exc:  # the GPU number stands without it
             cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(exc)[:200]}
+
+    forms = None
+    if world == 1 and not args.no_forms and args.workload == "curved_pulse" and args.size == 32 and args.k == 5:
+        forms = measure_forms(args, dgw, torch, barrier, local)
 
     if rank == 0:
         line = {
@@ -898,17 +1092,18 @@ def main():
                        "tiling_elements_per_block": {"operator": tiling[0], "tck": tiling[1]},
                        "predictor_kernel": ("lines" if args.pred == "lines" or args.basis == "gl"
                                             or (args.pred == "auto" and args.prec == "fp64") else "columns"),
-                       "affine_compact_kernels": s.is_affine(),
+                       "affine_compact_kernels": m_affine,
                        "l2": "inputs larger than L2 (state %d MB, %d MB device-resident incl. geometry), no flush"
-                       % (state_bytes >> 20, s.device_bytes() >> 20),
+                       % (state_bytes >> 20, device_mb),
                        "parallelism": "replicas" if world > 1 else "single"},
             "per_method_dofs_per_s": per_method,
             "kernel_ms": {kk: {"total_ms": v[0], "launches": v[1]} for kk, v in prof.items() if v[1]},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk,
         }
+        if forms is not None:
+            line["forms"] = forms
         print(json.dumps(line))
-    s.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -168,6 +168,31 @@ int dg_apply_operator(dg_ctx* ctx, const void* U, void* R, uintptr_t stream);
 int dg_step_lsrk(dg_ctx* ctx, void* U, double dt, int32_t nsteps, uintptr_t stream);
 
 /*
+ * Low-storage Runge-Kutta scheme that dg_step_lsrk (and dg_solve_host with
+ * method 0) runs on this context (Sec. 2.2, Table crit-Cr):
+ *   DG_LSRK_CK54  the 2N-storage five-stage fourth-order scheme above
+ *                 (the default);
+ *   DG_LSRK45     the paper's LSRK4(5), the two-register RK4(3)5[2R+]C of
+ *                 Kennedy, Carpenter & Lewis (five stages, order four);
+ *   DG_LSRK59     the paper's LSRK5(9), RK5(4)9[2R+]S (nine stages, order
+ *                 five).
+ * A two-register stage i evaluates R at its input Y_i and, fused into the
+ * operator's epilogue, writes Y_{i+1} = S_i + dt A_i R(Y_i) and
+ * S_{i+1} = S_i + dt B_i R(Y_i), with Y_1 = S_1 = u_n and u_{n+1} = S_{s+1}:
+ * four state passes per stage (three in the first and last). Both storage
+ * bases and both precisions. DG_EINVAL for another value; DG_EUNSUPPORTED
+ * for a two-register scheme on a 2D context. Batches and partitioned solves
+ * step the default scheme only (their LSRK calls return DG_EUNSUPPORTED on
+ * contexts set otherwise).
+ */
+#define DG_LSRK_CK54 0
+#define DG_LSRK45 1
+#define DG_LSRK59 2
+int dg_set_lsrk_scheme(dg_ctx* ctx, int32_t scheme);
+/* The context's scheme, or DG_EINVAL for NULL. */
+int dg_get_lsrk_scheme(const dg_ctx* ctx);
+
+/*
  * nsteps of ADER (Sec. 2.3, Eq. (6)): Ubar = Taylor-Cauchy-Kowalevski
  * predictor with the element-local basis change GL -> G (Sec. 3.2,
  * Algorithm 2) and degree reduction every reduce_every-th derivative
@@ -319,7 +344,12 @@ int dg_norms(dg_ctx* ctx, const void* A, const void* B, double* out_aa,
  * End-to-end solve through host memory: copy U_host (host, [E][4][(k+1)^3]
  * in the context precision) into a context-owned device state, run nsteps of
  * method (0 = LSRK, 1 = ADER), copy the result back to U_out_host, and
- * synchronise. Pinned host buffers make the copies asynchronous.
+ * synchronise. When the context steps with Gauss-point states (DG_BASIS_G,
+ * 3D) and both host buffers are pinned (page-locked, mapped) or managed
+ * memory, 16-byte aligned, the transfers are fused with the two changes of
+ * basis: one kernel reads U_host through the device's mapping and writes the
+ * Gauss-point values, another writes the GL result straight into
+ * U_out_host. Pageable buffers take plain copies instead (same results).
  */
 int dg_solve_host(dg_ctx* ctx, int method, const void* U_host, void* U_out_host,
                   double dt, int32_t nsteps, int32_t reduce_every, uintptr_t stream);
@@ -532,6 +562,29 @@ void dg_server_destroy(dg_server* s);
  * the stream and clears the status. dg_solve_host checks it itself.
  */
 int dg_check_device(dg_ctx* ctx, uintptr_t stream);
+
+/*
+ * Testing only (no counterpart in the paper): with on != 0, the first
+ * bounded wait of the kernels that stage their inputs by bulk copy (the FP32
+ * Gauss-basis operators) gives up at once instead of after its poll limit.
+ * The kernel then runs its give-up path as it would after a real stall: it
+ * sets the device status, waits (bounded) for its own copies to land, and
+ * returns without writing results, so the next dg_check_device reports
+ * DG_ETIMEOUT. Nothing hangs and the context stays usable; on = 0 restores
+ * normal operation. Other kernels are unaffected. DG_EINVAL for a NULL ctx.
+ */
+int dg_test_expire_waits(dg_ctx* ctx, int32_t on);
+
+/*
+ * Measurement helper (no counterpart in the paper): the FMA pipe's peak in
+ * TFLOP/s on the current device, DG_FP64 or DG_FP32, from one timed launch
+ * of independent FMA chains (8 per thread, iters FMAs each, 8 blocks of 256
+ * threads per SM) after one untimed launch, on the given stream. These are
+ * the measured denominators of the ALU rooflines. Allocates nothing (a
+ * static device word keeps the chains live). DG_EINVAL for bad arguments,
+ * DG_ECUDA if a CUDA call fails.
+ */
+int dg_probe_fma_peak(int32_t prec, int32_t iters, double* tflops, uintptr_t stream);
 
 /* Sizes: number of elements, degree, precision, bytes of one state. */
 int dg_info(const dg_ctx* ctx, int32_t* n_elem, int32_t* k, int32_t* prec,

@@ -21,8 +21,10 @@ EXPORTED_SYMBOLS = [
     "dg_set_owned", "dg_part_create", "dg_part_step_lsrk", "dg_part_step_ader", "dg_part_exchange",
     "dg_part_info", "dg_part_last_error", "dg_part_destroy", "dg_step_hdg_ader", "dg_part_step_hdg_ader",
     "dg_mesh_setup_2d", "dg_get_state", "dg_set_state",
-    "dg_set_predictor_kernel", "dg_get_predictor_kernel",
+    "dg_set_predictor_kernel", "dg_get_predictor_kernel", "dg_test_expire_waits",
+    "dg_set_lsrk_scheme", "dg_get_lsrk_scheme", "dg_probe_fma_peak",
 ]
+LSRK_CK54, LSRK45, LSRK59 = 0, 1, 2
 BASIS_GL, BASIS_G = 0, 1
 PRED_AUTO, PRED_LINES, PRED_COLUMNS, PRED_GL_PROJECTION = 0, 1, 2, 3
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
@@ -129,6 +131,10 @@ def load_library():
         "dg_request_bytes": (C.c_size_t, [C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
         "dg_set_basis": (C.c_int, [vp, C.c_int]),
         "dg_check_device": (C.c_int, [vp, st]),
+        "dg_test_expire_waits": (C.c_int, [vp, C.c_int32]),
+        "dg_set_lsrk_scheme": (C.c_int, [vp, C.c_int32]),
+        "dg_get_lsrk_scheme": (C.c_int, [vp]),
+        "dg_probe_fma_peak": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_double), st]),
         "dg_is_affine": (C.c_int, [vp]),
         "dg_change_basis": (C.c_int, [vp, vp, C.c_int, st]),
         "dg_batch_set_basis": (C.c_int, [vp, C.c_int, C.c_int]),
@@ -175,6 +181,16 @@ def _ptr(x):
     return C.c_void_p(x.data_ptr())
 
 
+def probe_fma_peak(prec, iters=4096, stream=None):
+    """Measured FMA-pipe peak (TFLOP/s) of the current device (dg_probe_fma_peak)."""
+    lib = load_library()
+    v = C.c_double()
+    rc = lib.dg_probe_fma_peak(int(prec), int(iters), C.byref(v), _stream(stream))
+    if rc != 0:
+        raise DGError(rc, "dg_probe_fma_peak failed")
+    return v.value
+
+
 class Solver:
     """One mesh, degree and precision on the current CUDA device.
 
@@ -190,6 +206,7 @@ class Solver:
         self.alpha = float(alpha)
         self.E = int(mesh["n_elem"])
         self.dtype = torch.float64 if self.prec == DG_FP64 else torch.float32
+        self.device = torch.cuda.current_device()
         self._nodes = np.ascontiguousarray(mesh["nodes"], np.float64)
         self._nbr = np.ascontiguousarray(mesh["nbr"], np.int32)
         self._nbf = np.ascontiguousarray(mesh["nbr_face"], np.int8)
@@ -286,10 +303,20 @@ class Solver:
         return v.value
 
     def energy_noalloc(self, U, out, stream=None):
-        """Energy into the device double ``out`` (a 1-element float64 CUDA
-        tensor) without any allocation by the library; see include/dg.h."""
+        """Energy into the device double ``out`` (a float64 CUDA tensor on
+        this solver's device) without any allocation by the library; see
+        include/dg.h."""
+        import torch
+        if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+                and out.numel() >= 1 and out.device.index == self.device):
+            raise DGError(-1, "out must be a float64 CUDA tensor on device %d" % self.device)
         self._check(self.lib.dg_energy_noalloc(self.ctx, self._state(U), _ptr(out), _stream(stream)))
         return out
+
+    def energy_noalloc_raw(self, U, out_ptr, stream=None):
+        """dg_energy_noalloc with an unchecked address (tests of the C
+        library's own argument checks)."""
+        return int(self.lib.dg_energy_noalloc(self.ctx, self._state(U), C.c_void_p(out_ptr), _stream(stream)))
 
     def norms(self, A, B=None, stream=None):
         aa, dd = C.c_double(), C.c_double()
@@ -339,6 +366,18 @@ class Solver:
     def check_device(self, stream=None):
         """Raise DGError(DG_ETIMEOUT) if a bounded device wait gave up."""
         self._check(self.lib.dg_check_device(self.ctx, _stream(stream)))
+
+    def set_lsrk_scheme(self, scheme):
+        """LSRK_CK54 (default), LSRK45 or LSRK59 for step_lsrk (dg_set_lsrk_scheme)."""
+        self._check(self.lib.dg_set_lsrk_scheme(self.ctx, int(scheme)))
+
+    def lsrk_scheme(self):
+        return int(self.lib.dg_get_lsrk_scheme(self.ctx))
+
+    def test_expire_waits(self, on=True):
+        """Testing only: the first bounded wait of the staged FP32 operators
+        gives up at once (dg_test_expire_waits)."""
+        self._check(self.lib.dg_test_expire_waits(self.ctx, int(bool(on))))
 
     def change_basis(self, U, to_g, stream=None):
         self._check(self.lib.dg_change_basis(self.ctx, self._state(U), int(bool(to_g)), _stream(stream)))
@@ -405,6 +444,7 @@ class Solver2D(Solver):
         self.alpha = float(alpha)
         self.E = int(mesh["n_elem"])
         self.dtype = torch.float64 if self.prec == DG_FP64 else torch.float32
+        self.device = torch.cuda.current_device()
         self._nodes = np.ascontiguousarray(mesh["nodes"], np.float64)
         self._nbr = np.ascontiguousarray(mesh["nbr"], np.int32)
         self._nbf = np.ascontiguousarray(mesh["nbr_face"], np.int8)

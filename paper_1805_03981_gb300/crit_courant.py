@@ -35,7 +35,7 @@ def stable(s, U0, h, k, cr, method, steps, growth):
     U = s.to_device(U0)
     e0 = s.energy(U)
     dt = cr * h / k ** 1.5
-    if method == "lsrk":
+    if method in ("lsrk", "lsrk45", "lsrk59"):
         s.step_lsrk(U, dt, steps)
     elif method == "hdg_ader":
         s.step_hdg_ader(U, dt, steps, 2)
@@ -49,6 +49,11 @@ def stable(s, U0, h, k, cr, method, steps, growth):
 def critical(k, method, N=4, steps=1000, growth=0.01, lo=0.02, hi=1.2, tol=2e-3, prec=None, dim=3):
     from . import _lib
     s, U0, h = _setup(k, N, _lib.DG_FP64 if prec is None else prec, dim)
+    # lsrk: the 2N five-stage scheme; lsrk45 / lsrk59: the paper's
+    # two-register LSRK4(5) / LSRK5(9) (Sec. 2.2)
+    s_scheme = {"lsrk45": _lib.LSRK45, "lsrk59": _lib.LSRK59}.get(method)
+    if s_scheme is not None:
+        s.set_lsrk_scheme(s_scheme)
     if method in ("ader", "hdg_ader"):
         hi = min(hi, 0.6)
     while hi - lo > tol:
@@ -69,7 +74,7 @@ def main():
     ap.add_argument("--dim", type=int, default=3, choices=[2, 3])
     a = ap.parse_args()
     out = {}
-    methods = ("lsrk", "ader", "hdg_ader") if a.dim == 3 else ("lsrk", "ader")
+    methods = ("lsrk", "lsrk45", "lsrk59", "ader", "hdg_ader") if a.dim == 3 else ("lsrk", "ader")
     for k in (int(x) for x in a.k.split(",")):
         out[k] = {m: critical(k, m, a.N, a.steps, dim=a.dim) for m in methods}
     print(json.dumps({"crit_courant_%dd" % a.dim: out,

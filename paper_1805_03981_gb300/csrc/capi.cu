@@ -31,6 +31,24 @@ const double kLsrkB[5] = {1432997174477.0 / 9575080441755.0,
                           3134564353537.0 / 4481467310338.0,
                           2277821191437.0 / 14882151754819.0};
 
+// The paper's two-register schemes (Sec. 2.2; Kennedy, Carpenter & Lewis
+// 2000): LSRK4(5) = RK4(3)5[2R+]C and LSRK5(9) = RK5(4)9[2R+]S.  A[i] weights
+// the newest increment in stage i+1, B[i] the increments of the solution.
+const double kKcl45A[4] = {970286171893.0 / 4311952581923.0, 6584761158862.0 / 12103376702013.0,
+                           2251764453980.0 / 15575788980749.0, 26877169314380.0 / 34165994151039.0};
+const double kKcl45B[5] = {1153189308089.0 / 22510343858157.0, 1772645290293.0 / 4653164025191.0,
+                           -1672844663538.0 / 4480602732383.0, 2114624349019.0 / 3568978502595.0,
+                           5198255086312.0 / 14908931495163.0};
+const double kKcl59A[8] = {1107026461565.0 / 5417078080134.0,   38141181049399.0 / 41724347789894.0,
+                           493273079041.0 / 11940823631197.0,   1851571280403.0 / 6147804934346.0,
+                           11782306865191.0 / 62590030070788.0, 9452544825720.0 / 13648368537481.0,
+                           4435885630781.0 / 26285702406235.0,  2357909744247.0 / 11371140753790.0};
+const double kKcl59B[9] = {2274579626619.0 / 23610510767302.0,  693987741272.0 / 12394497460941.0,
+                           -347131529483.0 / 15096185902911.0,  1144057200723.0 / 32081666971178.0,
+                           1562491064753.0 / 11797114684756.0,  13113619727965.0 / 44346030145118.0,
+                           393957816125.0 / 7825732611452.0,    720647959663.0 / 6565743875477.0,
+                           3559252274877.0 / 14424734981077.0};
+
 std::mutex g_mu;
 KernelTable g_kt;
 KernelTable2D g_kt2;
@@ -57,6 +75,8 @@ int init_device(int dev, std::string* err) {
     register_tckc_f32_lo(&g_kt);
     register_tckc_f32_hi(&g_kt);
     register_tckn(&g_kt);
+    register_lsrk2r_f64(&g_kt);
+    register_lsrk2r_f32(&g_kt);
     register_2d(&g_kt2);
     g_kt_ready = true;
   }
@@ -65,11 +85,12 @@ int init_device(int dev, std::string* err) {
     return DG_EINVAL;
   }
   if (!(g_dev_ready >> dev & 1ull)) {
-    int (*up[14])(const double*, const float*) = {
+    int (*up[])(const double*, const float*) = {
         upload_f64_lo,      upload_f64_hi,      upload_f32_lo,      upload_f32_hi,      upload_batch_f64,
         upload_batch_f32,   upload_tck_odd_f64, upload_tck_odd_f32, upload_tckc_f64_lo, upload_tckc_f64_hi,
-        upload_tckc_f32_lo, upload_tckc_f32_hi, upload_tckn,        upload_2d};
-    for (int i = 0; i < 14; ++i) {
+        upload_tckc_f32_lo, upload_tckc_f32_hi, upload_tckn,        upload_lsrk2r_f64,  upload_lsrk2r_f32,
+        upload_2d};
+    for (size_t i = 0; i < sizeof(up) / sizeof(up[0]); ++i) {
       const int e = up[i](g_tab.tab, g_tab_f);
       if (e) {
         cudaGetLastError();
@@ -122,6 +143,8 @@ struct dg_ctx {
   size_t dev_bytes = 0;
   uint64_t launches = 0;
   int epb_op = 1, epb_tck = 1, epb_en = 1;
+  int expire_wait = 0;  // dg_test_expire_waits
+  int lsrk_scheme = DG_LSRK_CK54;  // dg_set_lsrk_scheme
   int basis = DG_BASIS_GL;  // representation of the state inside the steppers
   int pred_kernel = DG_PRED_AUTO;  // predictor kernel for Gauss-point states
   // profiling: event pairs recorded around launches while enabled
@@ -399,6 +422,7 @@ OpParams op_params(const dg_ctx* ctx) {
   p.geoK = ctx->geoK;
   p.err = ctx->bad;
   p.E = ctx->Erun;
+  p.expire_wait = ctx->expire_wait;
   return p;
 }
 
@@ -417,7 +441,7 @@ int launch_op(dg_ctx* ctx, const OpParams& p, int epi, cudaStream_t st, bool gba
 int change_basis(dg_ctx* ctx, void* U, int to_g, cudaStream_t st) {
   if (ctx->dim == 2) return change_basis2(ctx, U, to_g, st);
   dg_ctx::Span span(ctx, DG_KIND_OTHER, st);
-  DG_CK(g_kt.basis[ctx->prec][ctx->n](U, ctx->Erun, to_g, ctx->epb_en, st), "basis kernel launch");
+  DG_CK(g_kt.basis[ctx->prec][ctx->n](U, U, ctx->Erun, to_g, ctx->epb_en, st), "basis kernel launch");
   span.done();
   ctx->launches++;
   return DG_OK;
@@ -517,6 +541,24 @@ int ensure(dg_ctx* ctx, void** p, const char* what) {
   return ctx->alloc(p, ctx->state_bytes(), what);
 }
 
+// The address under which kernels of the current device can read or write
+// the host buffer h: its device view when h is pinned host memory mapped
+// into the device's address space, h itself when it is managed memory;
+// nullptr otherwise (pageable memory: the caller copies instead).  The view
+// must be 16-byte aligned (the transfer kernels use vector accesses).
+const void* device_view(const void* h) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const void* v = nullptr;
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) v = a.devicePointer;
+  if (a.type == cudaMemoryTypeManaged) v = h;
+  if (v && reinterpret_cast<uintptr_t>(v) % 16 != 0) v = nullptr;
+  return v;
+}
+
 int check_state_ptr(dg_ctx* ctx, const void* p, const char* what) {
   if (!p) return ctx->fail(DG_EINVAL, "%s is NULL", what);
   cudaPointerAttributes a;
@@ -526,6 +568,9 @@ int check_state_ptr(dg_ctx* ctx, const void* p, const char* what) {
   }
   if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
     return ctx->fail(DG_EINVAL, "%s is not device memory", what);
+  if (a.type == cudaMemoryTypeDevice && a.device != ctx->dev)
+    return ctx->fail(DG_EINVAL, "%s is memory of device %d, the context is on device %d", what, a.device,
+                     ctx->dev);
   if (reinterpret_cast<uintptr_t>(p) % 16 != 0)  // bulk copies read states directly
     return ctx->fail(DG_EINVAL, "%s must be 16-byte aligned", what);
   return DG_OK;
@@ -534,15 +579,21 @@ int check_state_ptr(dg_ctx* ctx, const void* p, const char* what) {
 // Stage s reads the state of stage s-1 and writes a different buffer
 // (neighbours read face values of the input while it is being written):
 // U -> A -> B -> A -> B -> U, so each step ends in U without a copy.
-int lsrk_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st) {
+int lsrk2r_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st, bool keep_g);
+
+// keep_g: U already holds Gauss-point values (Gauss-basis contexts) and keeps
+// them on return; the caller changes basis (dg_solve_host fuses that change
+// with its host transfers).
+int lsrk_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st, bool keep_g = false) {
   if (ctx->dim == 2) return lsrk_steps2(ctx, U, dt, nsteps, st);
+  if (ctx->lsrk_scheme != DG_LSRK_CK54) return lsrk2r_steps(ctx, U, dt, nsteps, st, keep_g);
   int rc;
   if ((rc = ensure(ctx, &ctx->U2, "LSRK state"))) return rc;
   if ((rc = ensure(ctx, &ctx->U3, "LSRK state"))) return rc;
   if ((rc = ensure(ctx, &ctx->dU, "LSRK register"))) return rc;
   OpParams p = op_params(ctx);
   const bool g = ctx->basis == DG_BASIS_G && nsteps > 0;
-  if (g && (rc = change_basis(ctx, U, 1, st))) return rc;
+  if (g && !keep_g && (rc = change_basis(ctx, U, 1, st))) return rc;
   void* const chain[6] = {U, ctx->U2, ctx->U3, ctx->U2, ctx->U3, U};
   for (int s = 0; s < nsteps; ++s)
     for (int st5 = 0; st5 < 5; ++st5) {
@@ -556,13 +607,67 @@ int lsrk_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st) {
       p.first = st5 == 0;
       if ((rc = launch_op(ctx, p, EPI_LSRK, st, g))) return rc;
     }
-  if (g && (rc = change_basis(ctx, U, 0, st))) return rc;
+  if (g && !keep_g && (rc = change_basis(ctx, U, 0, st))) return rc;
+  return DG_OK;
+}
+
+// A stage of a two-register scheme: the operator kernel with the LSRK2R
+// epilogue, at the largest tiling its instantiation can launch.
+int launch_op2r(dg_ctx* ctx, const OpParams& p, cudaStream_t st, bool gbasis) {
+  const int which = gbasis ? (ctx->affine ? 2 : 1) : 0;
+  const int n2 = ctx->n * ctx->n;
+  const int thr = g_kt.op2r_maxthr[ctx->prec][ctx->n]();
+  int epb = ctx->epb_op;
+  while (epb > 1 && epb * n2 > thr) --epb;
+  dg_ctx::Span span(ctx, DG_KIND_LSRK, st);
+  DG_CK(g_kt.op2r[ctx->prec][ctx->n](p, which, epb, st), "operator kernel launch");
+  span.done();
+  ctx->launches++;
+  return DG_OK;
+}
+
+// The two-register schemes (Sec. 2.2): with S the running sum (ctx->dU),
+// stage i reads its input Y_i and S_i and writes Y_{i+1} = S_i + dt A_i R(Y_i)
+// and S_{i+1} = S_i + dt B_i R(Y_i).  Y_1 = S_1 = U, so the first stage reads
+// S from the input itself; the stage inputs then alternate between U2 and U3
+// (neighbours read a stage's input while it runs); the last stage writes the
+// new solution S into U and no stage input.
+int lsrk2r_steps(dg_ctx* ctx, void* U, double dt, int nsteps, cudaStream_t st, bool keep_g) {
+  const double* A = ctx->lsrk_scheme == DG_LSRK45 ? kKcl45A : kKcl59A;
+  const double* B = ctx->lsrk_scheme == DG_LSRK45 ? kKcl45B : kKcl59B;
+  const int stages = ctx->lsrk_scheme == DG_LSRK45 ? 5 : 9;
+  int rc;
+  if ((rc = ensure(ctx, &ctx->U2, "LSRK state"))) return rc;
+  if ((rc = ensure(ctx, &ctx->U3, "LSRK state"))) return rc;
+  if ((rc = ensure(ctx, &ctx->dU, "LSRK running sum"))) return rc;
+  OpParams p = op_params(ctx);
+  const bool g = ctx->basis == DG_BASIS_G && nsteps > 0;
+  if (g && !keep_g && (rc = change_basis(ctx, U, 1, st))) return rc;
+  for (int s = 0; s < nsteps; ++s) {
+    void* Y = U;
+    for (int i = 0; i < stages; ++i) {
+      void* next = (i % 2 == 0) ? ctx->U2 : ctx->U3;
+      p.U = Y;
+      p.first = i == 0;
+      p.last = i == stages - 1;
+      p.Uadd = i == 0 ? U : ctx->dU;
+      p.dU = p.last ? U : ctx->dU;
+      p.out = p.last ? nullptr : next;
+      p.cA = p.last ? 0.0 : dt * A[i];
+      p.cB = dt * B[i];
+      p.dt = dt;
+      if ((rc = launch_op2r(ctx, p, st, g))) return rc;
+      Y = next;
+    }
+  }
+  if (g && !keep_g && (rc = change_basis(ctx, U, 0, st))) return rc;
   return DG_OK;
 }
 
 // hdg: HDG-ADER (Eq. hdg-ader): each step first evaluates the DG derivative
 // W = -M^-1 K U, which takes the place of the predictor's first term -S U.
-int ader_steps(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_t st, bool hdg = false) {
+int ader_steps(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_t st, bool hdg = false,
+               bool keep_g = false) {
   if (ctx->dim == 2) {
     if (hdg) return ctx->fail(DG_EUNSUPPORTED, "HDG-ADER is not built for 2D meshes");
     return ader_steps2(ctx, U, dt, nsteps, red, st);
@@ -572,7 +677,7 @@ int ader_steps(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_
   if (hdg && (rc = ensure(ctx, &ctx->Wd, "HDG-ADER derivative"))) return rc;
   OpParams p = op_params(ctx);
   const bool g = ctx->basis == DG_BASIS_G && nsteps > 0;
-  if (g && (rc = change_basis(ctx, U, 1, st))) return rc;
+  if (g && !keep_g && (rc = change_basis(ctx, U, 1, st))) return rc;
   for (int s = 0; s < nsteps; ++s) {
     if (hdg) {
       OpParams q = op_params(ctx);
@@ -586,7 +691,7 @@ int ader_steps(dg_ctx* ctx, void* U, double dt, int nsteps, int red, cudaStream_
     p.out = U;
     if ((rc = launch_op(ctx, p, EPI_ADD, st, g))) return rc;
   }
-  if (g && (rc = change_basis(ctx, U, 0, st))) return rc;
+  if (g && !keep_g && (rc = change_basis(ctx, U, 0, st))) return rc;
   return DG_OK;
 }
 
@@ -627,10 +732,17 @@ __global__ void sumsq_kernel(const Real* A, const Real* B, size_t n, double* par
   }
 }
 
+// Both callers synchronise their stream after using the buffer, so an old,
+// smaller buffer has no work in flight when it is released here.
 int ensure_partial(dg_ctx* ctx, int n) {
   if (ctx->partial_cap >= n) return DG_OK;
-  int rc = ctx->alloc(&ctx->partial, sizeof(double) * n, "partial sums");
+  void* old = ctx->partial;
+  const int old_cap = ctx->partial_cap;
+  void* fresh = nullptr;
+  int rc = ctx->alloc(&fresh, sizeof(double) * n, "partial sums");
   if (rc) return rc;
+  if (old) ctx->release(old, sizeof(double) * old_cap);
+  ctx->partial = static_cast<double*>(fresh);
   ctx->partial_cap = n;
   return DG_OK;
 }
@@ -934,11 +1046,36 @@ int dg_solve_host(dg_ctx* ctx, int method, const void* Uh, void* Uout, double dt
   if ((rc = ensure(ctx, &ctx->Uh, "host-solve state"))) return rc;
   cudaStream_t st = S(stream);
   const size_t b = ctx->state_bytes();
-  DG_CK(cudaMemcpyAsync(ctx->Uh, Uh, b, cudaMemcpyHostToDevice, st), "copy in");
-  rc = method == 0 ? lsrk_steps(ctx, ctx->Uh, dt, nsteps, st)
-                   : ader_steps(ctx, ctx->Uh, dt, nsteps, red, st);
-  if (rc) return rc;
-  DG_CK(cudaMemcpyAsync(Uout, ctx->Uh, b, cudaMemcpyDeviceToHost, st), "copy out");
+  // With Gauss-point states inside the steppers and host buffers the device
+  // can address (pinned or managed memory), the transfers and the two changes
+  // of basis are fused: one kernel reads the host state and writes its
+  // Gauss-point values to the device, another writes the result back to the
+  // host in the GL basis.  Otherwise: copies, and the steppers change basis.
+  const void* din = ctx->dim == 3 ? device_view(Uh) : nullptr;
+  void* dout = ctx->dim == 3 ? const_cast<void*>(device_view(Uout)) : nullptr;
+  if (ctx->basis == DG_BASIS_G && nsteps > 0 && din && dout) {
+    {
+      dg_ctx::Span span(ctx, DG_KIND_OTHER, st);
+      DG_CK(g_kt.basis[ctx->prec][ctx->n](din, ctx->Uh, ctx->Erun, 1, ctx->epb_en, st), "basis kernel launch");
+      span.done();
+      ctx->launches++;
+    }
+    rc = method == 0 ? lsrk_steps(ctx, ctx->Uh, dt, nsteps, st, true)
+                     : ader_steps(ctx, ctx->Uh, dt, nsteps, red, st, false, true);
+    if (rc) return rc;
+    {
+      dg_ctx::Span span(ctx, DG_KIND_OTHER, st);
+      DG_CK(g_kt.basis[ctx->prec][ctx->n](ctx->Uh, dout, ctx->Erun, 0, ctx->epb_en, st), "basis kernel launch");
+      span.done();
+      ctx->launches++;
+    }
+  } else {
+    DG_CK(cudaMemcpyAsync(ctx->Uh, Uh, b, cudaMemcpyHostToDevice, st), "copy in");
+    rc = method == 0 ? lsrk_steps(ctx, ctx->Uh, dt, nsteps, st)
+                     : ader_steps(ctx, ctx->Uh, dt, nsteps, red, st);
+    if (rc) return rc;
+    DG_CK(cudaMemcpyAsync(Uout, ctx->Uh, b, cudaMemcpyDeviceToHost, st), "copy out");
+  }
   DG_CK(cudaStreamSynchronize(st), "solve");
   return dg_check_device(ctx, stream);
 }
@@ -1053,6 +1190,24 @@ int dg_check_device(dg_ctx* ctx, uintptr_t stream) {
   return DG_OK;
 }
 
+int dg_set_lsrk_scheme(dg_ctx* ctx, int32_t scheme) {
+  if (!ctx) return DG_EINVAL;
+  if (scheme != DG_LSRK_CK54 && scheme != DG_LSRK45 && scheme != DG_LSRK59)
+    return ctx->fail(DG_EINVAL, "scheme must be DG_LSRK_CK54, DG_LSRK45 or DG_LSRK59 (got %d)", scheme);
+  if (ctx->dim == 2 && scheme != DG_LSRK_CK54)
+    return ctx->fail(DG_EUNSUPPORTED, "2D meshes step with DG_LSRK_CK54 only");
+  ctx->lsrk_scheme = scheme;
+  return DG_OK;
+}
+
+int dg_get_lsrk_scheme(const dg_ctx* ctx) { return ctx ? ctx->lsrk_scheme : DG_EINVAL; }
+
+int dg_test_expire_waits(dg_ctx* ctx, int32_t on) {
+  if (!ctx) return DG_EINVAL;
+  ctx->expire_wait = on ? 1 : 0;
+  return DG_OK;
+}
+
 int dg_info(const dg_ctx* ctx, int32_t* E, int32_t* k, int32_t* prec, size_t* bytes) {
   if (!ctx) return DG_EINVAL;
   if (E) *E = ctx->E;
@@ -1114,8 +1269,9 @@ namespace {
 constexpr int kNoallocMaxPartials = 16384;
 static __device__ __align__(256) double g_noalloc_partials[kNoallocMaxPartials];
 
+constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-double* g_noalloc_addr[64] = {nullptr};  // device address of the array, per device
+double* g_noalloc_addr[kNoallocMaxDevices] = {nullptr};  // device address of the array, per device
 
 // Sum part[0..n) in a fixed order (strided per thread, then a fixed tree).
 __global__ void noalloc_sum_kernel(const double* part, int n, double* out) {
@@ -1139,6 +1295,21 @@ extern "C" int dg_energy_noalloc(dg_ctx* ctx, const void* U, double* out, uintpt
   int rc;
   if ((rc = check_state_ptr(ctx, U, "U"))) return rc;
   if (!out) return ctx->fail(DG_EINVAL, "out is NULL");
+  {  // the result is written by a kernel: out must be this device's memory
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, out) != cudaSuccess) {
+      cudaGetLastError();
+      return ctx->fail(DG_EINVAL, "out is not a device pointer");
+    }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+      return ctx->fail(DG_EINVAL, "out must be device (or managed) memory, not host memory");
+    if (a.type == cudaMemoryTypeDevice && a.device != ctx->dev)
+      return ctx->fail(DG_EINVAL, "out is memory of device %d, the context is on device %d", a.device, ctx->dev);
+    if (reinterpret_cast<uintptr_t>(out) % alignof(double) != 0)
+      return ctx->fail(DG_EINVAL, "out must be 8-byte aligned");
+  }
+  if (ctx->dev < 0 || ctx->dev >= kNoallocMaxDevices)
+    return ctx->fail(DG_EUNSUPPORTED, "dg_energy_noalloc serves devices 0..%d", kNoallocMaxDevices - 1);
   const int blocks = (ctx->Erun + ctx->epb_en - 1) / ctx->epb_en;
   if (blocks > kNoallocMaxPartials)
     return ctx->fail(DG_EINVAL,
@@ -1675,6 +1846,9 @@ extern "C" int dg_batch_step_ader(dg_batch* b, int32_t nsteps, int32_t red, uint
 
 extern "C" int dg_batch_step_lsrk(dg_batch* b, int32_t nsteps, uintptr_t stream) {
   if (!b || nsteps < 0) return DG_EINVAL;
+  for (dg_ctx* c : b->ctx)
+    if (c->lsrk_scheme != DG_LSRK_CK54)
+      return b->fail(DG_EUNSUPPORTED, "batches step LSRK with DG_LSRK_CK54 only");
   return batch_steps(b, 0, 0, nsteps, stream);
 }
 
@@ -1774,6 +1948,9 @@ int part_exchange(dg_part* t, void* const* bufs, cudaStream_t st) {
 int part_lsrk(dg_part* t, double dt, int nsteps, cudaStream_t st) {
   int rc;
   const int P = t->P;
+  for (int i = 0; i < P; ++i)
+    if (t->c[i]->lsrk_scheme != DG_LSRK_CK54)
+      return t->fail(DG_EUNSUPPORTED, "partitioned solves step LSRK with DG_LSRK_CK54 only");
   for (int i = 0; i < P; ++i) {
     dg_ctx* c = t->c[i];
     if ((rc = ensure(c, &c->U2, "LSRK state")) || (rc = ensure(c, &c->U3, "LSRK state")) ||

@@ -64,7 +64,7 @@ cudaError_t launch_setup2d(const Setup2Params& P, cudaStream_t st);
 typedef cudaError_t (*OpFn)(const OpParams& p, int epi, int epb, cudaStream_t st);
 typedef cudaError_t (*TckFn)(const TckParams& p, int red, int epb, cudaStream_t st);
 typedef cudaError_t (*EnergyFn)(const EnergyParams& p, int epb, cudaStream_t st);
-typedef cudaError_t (*BasisFn)(void* U, int E, int to_g, int epb, cudaStream_t st);
+typedef cudaError_t (*BasisFn)(const void* src, void* dst, int E, int to_g, int epb, cudaStream_t st);
 typedef int (*SmemFn)(int which, int red);  // bytes per element
 typedef int (*MaxThrFn)(int which);          // largest launchable block
 typedef int (*MaxThr0Fn)();
@@ -83,6 +83,9 @@ struct KernelTable {
   TckFn tckn[2][DG_NMAX + 1];     // without the basis change (Alg. 1), GL states, no reduction
   int (*tckn_smem[2][DG_NMAX + 1])(int red);
   MaxThr0Fn tckn_maxthr[2][DG_NMAX + 1];
+  // two-register LSRK stages; which: 0 GL, 1 Gauss-point states, 2 affine
+  cudaError_t (*op2r[2][DG_NMAX + 1])(const OpParams& p, int which, int epb, cudaStream_t st);
+  MaxThr0Fn op2r_maxthr[2][DG_NMAX + 1];
   EnergyFn energy[2][DG_NMAX + 1];
   SmemFn smem[2][DG_NMAX + 1];
   MaxThrFn maxthr[2][DG_NMAX + 1];
@@ -126,6 +129,10 @@ int upload_tckc_f32_lo(const double* d, const float* f);
 int upload_tckc_f32_hi(const double* d, const float* f);
 void register_tckn(KernelTable* t);
 int upload_tckn(const double* d, const float* f);
+void register_lsrk2r_f64(KernelTable* t);
+void register_lsrk2r_f32(KernelTable* t);
+int upload_lsrk2r_f64(const double* d, const float* f);
+int upload_lsrk2r_f32(const double* d, const float* f);
 
 struct BatchItem;
 struct BatchInst;

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tables.h"
 
 // Each translation unit has its own copy of the constant tables (no
@@ -33,7 +35,12 @@ static __constant__ float c_tab_f[DG_TAB_LEN];
 
 namespace dg {
 
-enum { EPI_WRITE = 0, EPI_LSRK = 1, EPI_ADD = 2 };
+// Operator epilogues.  EPI_LSRK: a stage of the 2N-storage scheme (register
+// dU).  EPI_LSRK2R: a stage of a two-register scheme (Sec. 2.2, LSRK4(5) and
+// LSRK5(9)): with S the running sum (read from Uadd, written to dU) the
+// stage writes the next stage input S + cA R (out; skipped in the last
+// stage) and S + cB R, with cA = dt A_i and cB = dt B_i.
+enum { EPI_WRITE = 0, EPI_LSRK = 1, EPI_ADD = 2, EPI_LSRK2R = 3 };
 
 template <typename Real>
 __device__ __forceinline__ Real tab(int i);
@@ -76,9 +83,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Wait for phase `parity` of the barrier, giving up after a bounded number of
 // polls: then the error flag is set, a second bounded wait lets the block's
-// own copies land, and false is returned.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
-  for (int i = 0; i < (1 << 22); ++i)
+// own copies land, and false is returned.  The second limit is the same 2^22
+// polls, far longer than the largest copy a block issues (a few tens of KB).
+// expire_first (a test setting, OpParams::expire_wait) makes the first wait
+// give up at once, so that the give-up path runs without a real hang; the
+// second wait still drains the copies before the block returns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err,
+                                                  bool expire_first = false) {
+  const int first_limit = expire_first ? 0 : (1 << 22);
+  for (int i = 0; i < first_limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   if (err) atomicExch(err, 2);
   for (int i = 0; i < (1 << 22); ++i)
@@ -200,7 +213,9 @@ struct OpParams {
   const void* Uadd;   // ADD / LSRK: state the update is added to
   void* dU;           // LSRK register
   double cA, cB, dt;  // LSRK: dU = cA dU + dt R (cA ignored if first), out = Uadd + cB dU
-  int first;          // LSRK: first stage (dU not read)
+                      // LSRK2R: out = Uadd + cA R, dU = Uadd + cB R
+  int first;          // LSRK: first stage (dU not read); LSRK2R: Uadd is the input U itself
+  int last;           // LSRK2R: last stage (out not written)
   const int32_t* nbr;
   const int8_t* nbr_face;
   const int8_t* orient;
@@ -210,6 +225,7 @@ struct OpParams {
   const void* geoK;  // [E][DG_AFF_OP] compact data of affine elements (affine kernels only)
   int* err;          // set (non-zero) if a bounded wait gave up
   int E;
+  int expire_wait;   // testing only: the first bounded wait gives up at once
 };
 
 template <int N>
@@ -472,6 +488,10 @@ __device__ __forceinline__ void op_block(const OpParams& p, const int e0, const 
       out[g] = R;
     } else if (EPI == EPI_ADD) {
       out[g] = Uadd[g] + R;
+    } else if (EPI == EPI_LSRK2R) {
+      const Real S = Uadd[g];
+      if (!p.last) out[g] = fma(cA, R, S);
+      dU[g] = fma(cB, R, S);
     } else {
       const Real d = p.first ? dt * R : fma(cA, dU[g], dt * R);
       dU[g] = d;
@@ -603,6 +623,10 @@ __device__ __forceinline__ void opg_block(const OpParams& p, const int e0, const
           out[g] = R;
         } else if (EPI == EPI_ADD) {
           out[g] = Uadd[g] + R;
+        } else if (EPI == EPI_LSRK2R) {
+          const Real S = Uadd[g];
+          if (!p.last) out[g] = fma(cA, R, S);
+          dU[g] = fma(cB, R, S);
         } else {
           const Real d = p.first ? dt * R : fma(cA, dU[g], dt * R);
           dU[g] = d;
@@ -645,7 +669,7 @@ __device__ __forceinline__ void opgs_block(const OpParams& p, const int e0, cons
   Real* gMA = gAA + epb * GA;
   Real* gFA = gMA + epb * GM;
   Real* sxA = gFA + epb * GF;
-  const bool need_x = (EPI == EPI_LSRK && !p.first) || EPI == EPI_ADD;
+  const bool need_x = ((EPI == EPI_LSRK || EPI == EPI_LSRK2R) && !p.first) || EPI == EPI_ADD;
   const Real* __restrict__ U = static_cast<const Real*>(p.U);
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   __syncthreads();
@@ -693,7 +717,7 @@ __device__ __forceinline__ void opgs_block(const OpParams& p, const int e0, cons
       }
     }
   }
-  const bool ok = mbar_wait_bounded(&bar, 0, p.err);
+  const bool ok = mbar_wait_bounded(&bar, 0, p.err, p.expire_wait != 0);
   __syncthreads();
   const Real* gA = gAA + le * GA;
   const Real* gF = gFA + le * GF;
@@ -759,6 +783,10 @@ __device__ __forceinline__ void opgs_block(const OpParams& p, const int e0, cons
           out[g] = R;
         } else if (EPI == EPI_ADD) {
           out[g] = sx[i] + R;
+        } else if (EPI == EPI_LSRK2R) {  // first stage: the running sum is the input itself
+          const Real S = p.first ? su[i] : sx[i];
+          if (!p.last) out[g] = fma(cA, R, S);
+          dU[g] = fma(cB, R, S);
         } else {  // LSRK: the stage input is the staged state
           const Real d = p.first ? dt * R : fma(cA, sx[i], dt * R);
           dU[g] = d;
@@ -887,7 +915,7 @@ __device__ __forceinline__ void opga_block(const OpParams& p, const int e0, cons
   Real* snA = srA + epb * 4 * N3;
   Real* gKA = snA + epb * 24 * N2;  // STAGE only
   Real* sxA = gKA + epb * DG_AFF_OP;  // STAGE only
-  const bool need_x = (EPI == EPI_LSRK && !p.first) || EPI == EPI_ADD;
+  const bool need_x = ((EPI == EPI_LSRK || EPI == EPI_LSRK2R) && !p.first) || EPI == EPI_ADD;
   const Real* __restrict__ U = static_cast<const Real*>(p.U);
   if constexpr (STAGE) {
     if (threadIdx.x == 0) mbar_init(&bar, 1);
@@ -940,7 +968,7 @@ __device__ __forceinline__ void opga_block(const OpParams& p, const int e0, cons
     }
   }
   bool ok = true;
-  if constexpr (STAGE) ok = mbar_wait_bounded(&bar, 0, p.err);
+  if constexpr (STAGE) ok = mbar_wait_bounded(&bar, 0, p.err, p.expire_wait != 0);
   __syncthreads();
   const Real* gK = STAGE ? gKA + le * DG_AFF_OP : static_cast<const Real*>(p.geoK) + (size_t)(act ? e : 0) * DG_AFF_OP;
   if (act && ok) {  // y
@@ -1008,6 +1036,10 @@ __device__ __forceinline__ void opga_block(const OpParams& p, const int e0, cons
           out[g] = R;
         } else if (EPI == EPI_ADD) {
           out[g] = (STAGE ? sx[i] : Uadd[g]) + R;
+        } else if (EPI == EPI_LSRK2R) {
+          const Real S = STAGE ? (p.first ? su[i] : sx[i]) : Uadd[g];
+          if (!p.last) out[g] = fma(cA, R, S);
+          dU[g] = fma(cB, R, S);
         } else {
           const Real d = p.first ? dt * R : fma(cA, STAGE ? sx[i] : dU[g], dt * R);
           dU[g] = d;
@@ -1030,19 +1062,28 @@ __global__ void opga_kernel(const OpParams p) {
   opga_block<N, Real, EPI, sizeof(Real) == 4>(p, e0, min(epb, p.E - e0), epb, reinterpret_cast<Real*>(smem_raw));
 }
 
-// In-place change of basis of whole states: GL -> G (to_g) or G -> GL.
+// Change of basis of whole states, GL -> G (to_g) or G -> GL, from src to
+// dst (the same array for an in-place change).  src or dst may be pinned
+// host memory mapped into the device's address space: the element blocks
+// are contiguous, so both copies are 16-byte vector accesses, coalesced
+// across the block, and a host-to-device transfer fused with the change of
+// basis costs one pass.
 template <int N, typename Real>
-__global__ void basis_kernel(void* Uv, int E, int to_g) {
+__global__ void basis_kernel(const void* src, void* dst, int E, int to_g) {
   constexpr int N2 = N * N, N3 = N2 * N;
+  constexpr int VW = 16 / sizeof(Real);  // Reals per 16-byte vector
+  typedef typename std::conditional<sizeof(Real) == 8, double2, float4>::type Vec;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real* sm = reinterpret_cast<Real*>(smem_raw);
-  Real* U = static_cast<Real*>(Uv);
   const int epb = blockDim.x / N2;
   const int le = threadIdx.x / N2, t = threadIdx.x - le * N2;
   const int e0 = blockIdx.x * epb;
   const int ne = min(epb, E - e0);
   Real* su = sm + le * 4 * N3;
-  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) sm[i] = U[(size_t)e0 * 4 * N3 + i];
+  // 4 N^3 Reals per element is a multiple of VW, and states are 16-byte aligned
+  const Vec* in = reinterpret_cast<const Vec*>(static_cast<const Real*>(src) + (size_t)e0 * 4 * N3);
+  Vec* smv = reinterpret_cast<Vec*>(sm);
+  for (int i = threadIdx.x; i < ne * 4 * N3 / VW; i += blockDim.x) smv[i] = in[i];
   __syncthreads();
   const bool act = le < ne;
   if (to_g) {
@@ -1059,7 +1100,8 @@ __global__ void basis_kernel(void* Uv, int E, int to_g) {
     if (act) contract_tile<Real, 1, N, N, N, N, OFF_VI(N), N3, N3>(su, su, t, N2);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < ne * 4 * N3; i += blockDim.x) U[(size_t)e0 * 4 * N3 + i] = sm[i];
+  Vec* out = reinterpret_cast<Vec*>(static_cast<Real*>(dst) + (size_t)e0 * 4 * N3);
+  for (int i = threadIdx.x; i < ne * 4 * N3 / VW; i += blockDim.x) out[i] = smv[i];
 }
 
 // ---------------------------------------------------------------------------

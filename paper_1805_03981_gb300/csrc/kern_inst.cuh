@@ -54,11 +54,31 @@ cudaError_t launch_opga(const OpParams& p, int epi, int epb, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Stages of the two-register LSRK schemes (EPI_LSRK2R), in their own units
+// (kern_lsrk2r_*.cu).  which: 0 GL storage (op_kernel), 1 Gauss-point states
+// (opg_kernel), 2 Gauss-point states on affine elements (opga_kernel).
 template <int N, typename Real>
-cudaError_t launch_basis(void* U, int E, int to_g, int epb, cudaStream_t st) {
+cudaError_t launch_op2r(const OpParams& p, int which, int epb, cudaStream_t st) {
+  const int threads = epb * N * N;
+  const int blocks = (p.E + epb - 1) / epb;
+  if (which == 0) {
+    op_kernel<N, Real, EPI_LSRK2R>
+        <<<blocks, threads, (size_t)epb * op_smem_per_elem<N>() * sizeof(Real), st>>>(p);
+  } else if (which == 1) {
+    opg_kernel<N, Real, EPI_LSRK2R>
+        <<<blocks, threads, (size_t)epb * opg_smem_per_elem<N, Real>() * sizeof(Real), st>>>(p);
+  } else {
+    opga_kernel<N, Real, EPI_LSRK2R>
+        <<<blocks, threads, (size_t)epb * opga_smem_per_elem<N>(sizeof(Real) == 4) * sizeof(Real), st>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+template <int N, typename Real>
+cudaError_t launch_basis(const void* src, void* dst, int E, int to_g, int epb, cudaStream_t st) {
   const int threads = epb * N * N;
   const size_t smem = (size_t)epb * 4 * N * N * N * sizeof(Real);
-  basis_kernel<N, Real><<<(E + epb - 1) / epb, threads, smem, st>>>(U, E, to_g);
+  basis_kernel<N, Real><<<(E + epb - 1) / epb, threads, smem, st>>>(src, dst, E, to_g);
   return cudaGetLastError();
 }
 
@@ -192,6 +212,28 @@ void register_tck_odd_one(KernelTable* t) {
   const int pi = sizeof(Real) == 8 ? 0 : 1;
   t->tck_odd[pi][N] = &launch_tck_odd<N, Real>;
   t->tck_odd_maxthr[pi][N] = &tck_odd_max_threads<N, Real>;
+}
+
+template <int N, typename Real>
+cudaError_t op2r_allow_smem() {
+  cudaError_t e;
+  if ((e = allow_smem(op_kernel<N, Real, EPI_LSRK2R>)) != cudaSuccess) return e;
+  if ((e = allow_smem(opg_kernel<N, Real, EPI_LSRK2R>)) != cudaSuccess) return e;
+  return allow_smem(opga_kernel<N, Real, EPI_LSRK2R>);
+}
+
+template <int N, typename Real>
+int op2r_max_threads() {
+  return min(kernel_max_threads(op_kernel<N, Real, EPI_LSRK2R>),
+             min(kernel_max_threads(opg_kernel<N, Real, EPI_LSRK2R>),
+                 kernel_max_threads(opga_kernel<N, Real, EPI_LSRK2R>)));
+}
+
+template <int N, typename Real>
+void register_2r_one(KernelTable* t) {
+  const int pi = sizeof(Real) == 8 ? 0 : 1;
+  t->op2r[pi][N] = &launch_op2r<N, Real>;
+  t->op2r_maxthr[pi][N] = &op2r_max_threads<N, Real>;
 }
 
 template <int N, typename Real>

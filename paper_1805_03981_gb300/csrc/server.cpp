@@ -56,8 +56,12 @@ struct Req {
   void* U = nullptr;
   int32_t done_steps = 0;
   double t_submit = 0, t_admit = 0, t_done = 0;
-  int status = DG_EAGAIN;
+  int status = DG_EAGAIN;  // read and written under the server's lock only
   std::string err;
+  // a failure the stepping thread has met; it becomes the status, under the
+  // lock, together with t_done and the release of the budget
+  int fail = DG_OK;
+  std::string fail_err;
 };
 
 // Device bytes a solve holds while admitted: the context's allocations with
@@ -265,10 +269,9 @@ void dg_server::run() {
         if (dg_batch_create(ctxs.data(), us.data(), dts.data(), (int32_t)ctxs.size(), (uintptr_t)st,
                             &g.batch) != DG_OK ||
             dg_batch_set_basis(g.batch, DG_BASIS_G, 0) != DG_OK) {
-          std::lock_guard<std::mutex> lk(mu);  // fail the group's solves
-          for (auto& r : g.members) {
-            r->status = DG_ECUDA;
-            r->err = dg_last_error(nullptr);
+          for (auto& r : g.members) {  // fail the group's solves
+            r->fail = DG_ECUDA;
+            r->fail_err = dg_last_error(nullptr);
             r->done_steps = r->nsteps;
           }
           g.batch = nullptr;
@@ -287,10 +290,9 @@ void dg_server::run() {
       const int rc = g.method == 1 ? dg_batch_step_ader(g.batch, round, g.red, (uintptr_t)st)
                                    : dg_batch_step_lsrk(g.batch, round, (uintptr_t)st);
       if (rc) {
-        std::lock_guard<std::mutex> lk(mu);
         for (auto& r : g.members) {
-          r->status = rc;
-          r->err = dg_batch_last_error(g.batch);
+          r->fail = rc;
+          r->fail_err = dg_batch_last_error(g.batch);
           r->done_steps = r->nsteps;
         }
       }
@@ -300,7 +302,7 @@ void dg_server::run() {
     ++rounds;
     std::vector<std::shared_ptr<Req>> finished;
     for (auto& r : active) {
-      if (r->status == DG_EAGAIN) {
+      if (r->fail == DG_OK) {
         r->done_steps += round;
         dof_steps += (double)round * dof_of(*r);
       }
@@ -308,11 +310,12 @@ void dg_server::run() {
     }
     if (finished.empty()) continue;
     for (auto& r : finished)
-      if (r->status == DG_EAGAIN &&
+      if (r->fail == DG_OK &&
           (dg_change_basis(r->ctx, r->U, 0, (uintptr_t)st) != DG_OK ||
            cudaMemcpyAsync(r->U_out, r->U, r->state_bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess)) {
         cudaGetLastError();
-        r->status = DG_ECUDA;
+        r->fail = DG_ECUDA;
+        r->fail_err = "copy of the final state failed";
       }
     cudaStreamSynchronize(st);
     for (auto& g : groups)
@@ -325,9 +328,12 @@ void dg_server::run() {
       used -= r->est_bytes;
       admitted_dof -= dof_of(*r);
       --admitted_count;
-      if (r->status == DG_EAGAIN) {
+      if (r->fail == DG_OK) {
         r->status = DG_OK;
         ++completed;
+      } else {
+        r->status = r->fail;
+        r->err = r->fail_err;
       }
       r->t_done = now_s();
       active.erase(std::find(active.begin(), active.end(), r));

@@ -154,6 +154,46 @@ def test_solve_host_matches_device():
     assert torch.equal(out, U.cpu())
 
 
+@pytest.mark.parametrize("prec", [dgw.DG_FP64, dgw.DG_FP32])
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("scheme", [dgw.LSRK_CK54, dgw.LSRK59])
+def test_solve_host_fused_transfers(prec, method, scheme):
+    """Gauss-point states with pinned host buffers: the transfers are fused
+    with the changes of basis (kernels read and write the host buffers).
+    Bitwise the same as pageable buffers (plain copies, the steppers change
+    basis) and as stepping a device state; at oracle parity."""
+    torch = _cuda()
+    if method == 1 and scheme != dgw.LSRK_CK54:
+        pytest.skip("the LSRK scheme does not apply to ADER")
+    cfg = _curved(3, 3, seed=12)
+    s, o = pair(cfg, prec)
+    s.set_basis(dgw.BASIS_G)
+    s.set_lsrk_scheme(scheme)
+    dt = 0.004
+    Uh = torch.from_numpy(cfg["U0"]).to(s.dtype)
+    pinned_in, pinned_out = Uh.pin_memory(), torch.empty_like(Uh).pin_memory()
+    page_in, page_out = Uh.clone(), torch.empty_like(Uh)
+    s.solve_host(method, pinned_in, pinned_out, dt, 2, 2)
+    s.solve_host(method, page_in, page_out, dt, 2, 2)
+    U = s.to_device(cfg["U0"])
+    if method == 0:
+        s.step_lsrk(U, dt, 2)
+    else:
+        s.step_ader(U, dt, 2, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(pinned_out, page_out)
+    assert torch.equal(pinned_out, U.cpu())
+    if method == 1:
+        ref = o.ader(cfg["U0"], dt, 2, 2)
+    elif scheme == dgw.LSRK_CK54:
+        ref = o.lsrk(cfg["U0"], dt, 2)
+    else:
+        from oracle import LSRK59_KCL_A, LSRK59_KCL_B
+        ref = o.lsrk2r(cfg["U0"], dt, 2, LSRK59_KCL_A, LSRK59_KCL_B)
+    err = rel_l2(pinned_out.double().numpy(), ref)
+    assert err < (1e-12 if prec == dgw.DG_FP64 else 2e-5), err
+
+
 def test_errors_are_reported():
     torch = _cuda()
     cfg = _curved(2, 2, seed=1)
