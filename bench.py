@@ -298,6 +298,15 @@ def make_solver(args, cfg, prec, dgw, basis=None, pred=None, tiling=None):
     return s
 
 
+def predictor_label(pred, basis, prec, affine):
+    """The predictor kernel a stepper runs (dg_set_predictor_kernel)."""
+    if pred == "lines" or basis == "gl" or (pred == "auto" and prec == "fp64"):
+        return "lines"
+    if pred == "auto" and prec == "fp32" and affine:
+        return "interleaved columns"
+    return "columns"
+
+
 def time_steps(args, s, cfg, dgw, torch, barrier, local, steps=None, warmup=None):
     """W untimed steps, then K steps of each method (one stepper call per
     method, as a solve runs; with the Gauss basis a call changes basis once
@@ -423,6 +432,7 @@ def precision_form(args, dgw, torch, barrier, local, N=64, k=4):
            "kernel_ms": {kk: {"total_ms": v[0], "launches": v[1]} for kk, v in m["prof"].items() if v[1]},
            "roofline": roofline(args, s, m["prof"], N, k, dgw.DG_FP32, dgw, tiling, "plane_wave", "g"),
            "tiling_elements_per_block": {"operator": tiling[0], "tck": tiling[1]},
+           "predictor_kernel": predictor_label("auto", "g", "fp32", s.is_affine()),
            "gpu_launches": m["launches"], "clocks": m["clocks"]}
     nst = m["steps"] + m["warmup"]
     u32 = {"lsrk": m["U_l"].double().cpu().numpy(), "ader": m["U_a"].double().cpu().numpy()}
@@ -1087,11 +1097,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == dgw.DG_FP64 else "f32",
             "data": "synthetic",
-            "config": {"workload": workload_desc(N, k, args.prec, args.workload), "elements": E, "k": k, "dof": dof,
+            "config": {"workload": workload_desc(N, k, args.prec, args.workload), "elements": N ** 3, "k": k, "dof": dof,
                        "state_basis_inside_steppers": "Gauss points (G)" if args.basis == "g" else "Gauss-Lobatto (GL)",
                        "tiling_elements_per_block": {"operator": tiling[0], "tck": tiling[1]},
-                       "predictor_kernel": ("lines" if args.pred == "lines" or args.basis == "gl"
-                                            or (args.pred == "auto" and args.prec == "fp64") else "columns"),
+                       "predictor_kernel": predictor_label(args.pred, args.basis, args.prec, m_affine),
                        "affine_compact_kernels": m_affine,
                        "l2": "inputs larger than L2 (state %d MB, %d MB device-resident incl. geometry), no flush"
                        % (state_bytes >> 20, device_mb),

@@ -251,9 +251,18 @@ int dg_get_basis(const dg_ctx* ctx);
  *  DG_PRED_COLUMNS  each thread keeps a z-column of the current Taylor term
  *                   and of the n-point sum in registers; x and y lines pass
  *                   through shared memory once per derivative;
- *  DG_PRED_AUTO     the column form in FP32, the line form in FP64 (default;
- *                   the FP64 pipe is the bound there, and the line form
- *                   keeps whole warps busy at the reduced Gauss sets).
+ *  DG_PRED_INTERLEAVED
+ *                   the column form with the block's elements interleaved in
+ *                   shared memory and the state staged by bulk copies, for
+ *                   FP32 meshes of affine elements with constant
+ *                   coefficients, reduce_every 0 or 2 and no HDG
+ *                   derivative (elsewhere the column form runs): fewer
+ *                   shared-memory bank conflicts and idle lanes; the column
+ *                   form's results bit for bit;
+ *  DG_PRED_AUTO     the interleaved form where it applies, else the column
+ *                   form, in FP32; the line form in FP64 (default; the FP64
+ *                   pipe is the bound there, and the line form keeps whole
+ *                   warps busy at the reduced Gauss sets).
  *  DG_PRED_GL_PROJECTION
  *                   the predictor without the basis change (Sec. 3.2,
  *                   Alg. 1), for GL states (DG_BASIS_GL steppers and dg_tck)
@@ -274,6 +283,7 @@ int dg_get_basis(const dg_ctx* ctx);
 #define DG_PRED_LINES 1
 #define DG_PRED_COLUMNS 2
 #define DG_PRED_GL_PROJECTION 3
+#define DG_PRED_INTERLEAVED 4
 int dg_set_predictor_kernel(dg_ctx* ctx, int kind);
 int dg_get_predictor_kernel(const dg_ctx* ctx);
 

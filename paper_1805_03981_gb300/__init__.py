@@ -9,4 +9,4 @@ library is missing.
 from ._lib import (DGError, probe_fma_peak, Solver, Solver2D, Batch, Server, load_library, library_path,  # noqa: F401
                    DG_FP64, DG_FP32, EXPORTED_SYMBOLS, KIND_LSRK, KIND_ADER, KIND_TCK,
                    BASIS_GL, BASIS_G, PRED_AUTO, PRED_LINES, PRED_COLUMNS,
-                   PRED_GL_PROJECTION, LSRK_CK54, LSRK45, LSRK59)
+                   PRED_GL_PROJECTION, PRED_INTERLEAVED, LSRK_CK54, LSRK45, LSRK59)

@@ -26,7 +26,7 @@ EXPORTED_SYMBOLS = [
 ]
 LSRK_CK54, LSRK45, LSRK59 = 0, 1, 2
 BASIS_GL, BASIS_G = 0, 1
-PRED_AUTO, PRED_LINES, PRED_COLUMNS, PRED_GL_PROJECTION = 0, 1, 2, 3
+PRED_AUTO, PRED_LINES, PRED_COLUMNS, PRED_GL_PROJECTION, PRED_INTERLEAVED = 0, 1, 2, 3, 4
 KIND_LSRK, KIND_ADER, KIND_TCK = 1, 2, 3
 KINDS = ["operator", "lsrk_stage", "ader_update", "tck", "other"]
 

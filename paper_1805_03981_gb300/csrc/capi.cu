@@ -75,6 +75,7 @@ int init_device(int dev, std::string* err) {
     register_tckc_f32_lo(&g_kt);
     register_tckc_f32_hi(&g_kt);
     register_tckn(&g_kt);
+    register_tcki_f32(&g_kt);
     register_lsrk2r_f64(&g_kt);
     register_lsrk2r_f32(&g_kt);
     register_2d(&g_kt2);
@@ -89,7 +90,7 @@ int init_device(int dev, std::string* err) {
         upload_f64_lo,      upload_f64_hi,      upload_f32_lo,      upload_f32_hi,      upload_batch_f64,
         upload_batch_f32,   upload_tck_odd_f64, upload_tck_odd_f32, upload_tckc_f64_lo, upload_tckc_f64_hi,
         upload_tckc_f32_lo, upload_tckc_f32_hi, upload_tckn,        upload_lsrk2r_f64,  upload_lsrk2r_f32,
-        upload_2d};
+        upload_tcki_f32,    upload_2d};
     for (size_t i = 0; i < sizeof(up) / sizeof(up[0]); ++i) {
       const int e = up[i](g_tab.tab, g_tab_f);
       if (e) {
@@ -453,7 +454,17 @@ int change_basis(dg_ctx* ctx, void* U, int to_g, cudaStream_t st) {
 // keeps every lane of the FP64 pipe busy at the reduced Gauss sets.
 bool use_columns(const dg_ctx* ctx) {
   if (ctx->pred_kernel == DG_PRED_LINES || g_kt.tckc[ctx->prec][ctx->n] == nullptr) return false;
-  return ctx->pred_kernel == DG_PRED_COLUMNS || ctx->prec == DG_FP32;
+  return ctx->pred_kernel == DG_PRED_COLUMNS || ctx->pred_kernel == DG_PRED_INTERLEAVED || ctx->prec == DG_FP32;
+}
+
+// The interleaved column form (affine elements with constant coefficients,
+// Gauss-point states, reduction every 0 or 2 derivatives, no HDG derivative,
+// FP32): the default there, or chosen with DG_PRED_INTERLEAVED.  Its results
+// are those of the column form bit for bit.
+bool use_interleaved(const dg_ctx* ctx, int red, const void* W) {
+  if (ctx->pred_kernel != DG_PRED_AUTO && ctx->pred_kernel != DG_PRED_INTERLEAVED) return false;
+  return ctx->affine && ctx->dim == 3 && (red == 0 || red == 2) && W == nullptr &&
+         g_kt.tcki[ctx->prec][ctx->n] != nullptr;
 }
 
 int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaStream_t st,
@@ -470,6 +481,7 @@ int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaS
   p.geoT_stride = ctx->tstride;
   p.geo_step = ctx->tstep;
   p.E = ctx->Erun;
+  p.err = ctx->bad;
   double fact = 1.0;
   for (int j = 0; j <= ctx->n; ++j) {  // dt^{j+1} / (j+1)!
     fact *= (j + 1);
@@ -488,6 +500,13 @@ int launch_tck(dg_ctx* ctx, const void* U, void* Ubar, double dt, int red, cudaS
     while (epb > 1 && (epb * per > 200 * 1024 || epb * n2 > thr)) --epb;
     dg_ctx::Span span(ctx, DG_KIND_TCK, st);
     DG_CK(g_kt.tckn[ctx->prec][ctx->n](p, 0, epb, st), "predictor kernel launch");
+    span.done();
+    ctx->launches++;
+    return DG_OK;
+  }
+  if (col && use_interleaved(ctx, red, W)) {
+    dg_ctx::Span span(ctx, DG_KIND_TCK, st);
+    DG_CK(g_kt.tcki[ctx->prec][ctx->n](p, red, 0, st), "predictor kernel launch");
     span.done();
     ctx->launches++;
     return DG_OK;
@@ -1154,9 +1173,11 @@ int dg_get_basis(const dg_ctx* ctx) { return ctx ? ctx->basis : DG_EINVAL; }
 
 int dg_set_predictor_kernel(dg_ctx* ctx, int kind) {
   if (!ctx) return DG_EINVAL;
-  if (kind != DG_PRED_AUTO && kind != DG_PRED_LINES && kind != DG_PRED_COLUMNS && kind != DG_PRED_GL_PROJECTION)
+  if (kind != DG_PRED_AUTO && kind != DG_PRED_LINES && kind != DG_PRED_COLUMNS && kind != DG_PRED_GL_PROJECTION &&
+      kind != DG_PRED_INTERLEAVED)
     return ctx->fail(DG_EINVAL,
-                     "predictor kernel must be DG_PRED_AUTO, DG_PRED_LINES, DG_PRED_COLUMNS or DG_PRED_GL_PROJECTION");
+                     "predictor kernel must be DG_PRED_AUTO, DG_PRED_LINES, DG_PRED_COLUMNS, DG_PRED_GL_PROJECTION "
+                     "or DG_PRED_INTERLEAVED");
   if (kind == DG_PRED_GL_PROJECTION && ctx->dim == 2)
     return ctx->fail(DG_EUNSUPPORTED, "not built for 2D meshes");
   ctx->pred_kernel = kind;

@@ -80,6 +80,7 @@ struct KernelTable {
   TckFn tckc[2][DG_NMAX + 1];     // column form, Gauss-basis states, every reduction
   int (*tckc_smem[2][DG_NMAX + 1])(int red);  // bytes per element
   MaxThr0Fn tckc_maxthr[2][DG_NMAX + 1];
+  TckFn tcki[2][DG_NMAX + 1];     // column form, interleaved: affine Gauss-point states, reduction 0 or 2
   TckFn tckn[2][DG_NMAX + 1];     // without the basis change (Alg. 1), GL states, no reduction
   int (*tckn_smem[2][DG_NMAX + 1])(int red);
   MaxThr0Fn tckn_maxthr[2][DG_NMAX + 1];
@@ -129,6 +130,8 @@ int upload_tckc_f32_lo(const double* d, const float* f);
 int upload_tckc_f32_hi(const double* d, const float* f);
 void register_tckn(KernelTable* t);
 int upload_tckn(const double* d, const float* f);
+void register_tcki_f32(KernelTable* t);
+int upload_tcki_f32(const double* d, const float* f);
 void register_lsrk2r_f64(KernelTable* t);
 void register_lsrk2r_f32(KernelTable* t);
 int upload_lsrk2r_f64(const double* d, const float* f);

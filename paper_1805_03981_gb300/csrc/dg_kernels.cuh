@@ -99,15 +99,70 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
-// out[i] = sum_j M[i][j] in[j];  M is RO x RI at table offset OFF.
+// out = M in for a centrosymmetric (SKEW = false) or skew-centrosymmetric
+// (SKEW = true) N x N matrix M, in the even-odd form stored at EO (tables.h):
+// e_j = in_j + in_{N-1-j}, o_j = in_j - in_{N-1-j} (j < N/2), p = A e (+ C in_mid),
+// q = B o, out_i = p_i + q_i, out_{N-1-i} = p_i - q_i (skew: q_i - p_i).
+// About N^2/2 + 2N operations instead of N^2 (the C_tensorial count of
+// Sec. 4.1).
+template <typename Real, int EO, int N, bool SKEW>
+__device__ __forceinline__ void mv_eo(const Real* in, Real* out) {
+  constexpr int H = N / 2;
+  constexpr bool ODD = (N & 1) != 0;
+  constexpr int A = EO, B = EO + (H + 1) * H, C = EO + 2 * (H + 1) * H;
+  Real e[H], o[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    e[j] = in[j] + in[N - 1 - j];
+    o[j] = in[j] - in[N - 1 - j];
+  }
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    Real p = tab<Real>(A + i * H) * e[0];
+#pragma unroll
+    for (int j = 1; j < H; ++j) p = fma(tab<Real>(A + i * H + j), e[j], p);
+    if constexpr (ODD) p = fma(tab<Real>(C + i), in[H], p);
+    Real q = tab<Real>(B + i * H) * o[0];
+#pragma unroll
+    for (int j = 1; j < H; ++j) q = fma(tab<Real>(B + i * H + j), o[j], q);
+    out[i] = p + q;
+    out[N - 1 - i] = SKEW ? q - p : p - q;
+  }
+  if constexpr (ODD) {
+    if constexpr (SKEW) {  // the middle row of a skew matrix is odd: only o contributes
+      Real q = tab<Real>(B + H * H) * o[0];
+#pragma unroll
+      for (int j = 1; j < H; ++j) q = fma(tab<Real>(B + H * H + j), o[j], q);
+      out[H] = q;
+    } else {  // the middle row of a centrosymmetric matrix is even
+      Real p = tab<Real>(A + H * H) * e[0];
+#pragma unroll
+      for (int j = 1; j < H; ++j) p = fma(tab<Real>(A + H * H + j), e[j], p);
+      out[H] = fma(tab<Real>(C + H), in[H], p);
+    }
+  }
+}
+
+// out[i] = sum_j M[i][j] in[j];  M is RO x RI at table offset OFF.  The
+// square basis changes V, VI and the collocation derivative D of n >= 5
+// points take the even-odd form (fewer operations); every kernel applies
+// them through this one routine, so all paths round alike.
 template <typename Real, int OFF, int RO, int RI>
 __device__ __forceinline__ void mv(const Real* in, Real* out) {
+  if constexpr (RO == RI && RI >= 5 && OFF == OFF_V(RI)) {
+    mv_eo<Real, OFF_EO(RI, 0), RI, false>(in, out);
+  } else if constexpr (RO == RI && RI >= 5 && OFF == OFF_VI(RI)) {
+    mv_eo<Real, OFF_EO(RI, 1), RI, false>(in, out);
+  } else if constexpr (RO == RI && RI >= 5 && OFF == OFF_D(RI)) {
+    mv_eo<Real, OFF_EO(RI, 2), RI, true>(in, out);
+  } else {
 #pragma unroll
-  for (int i = 0; i < RO; ++i) {
-    Real acc = tab<Real>(OFF + i * RI) * in[0];
+    for (int i = 0; i < RO; ++i) {
+      Real acc = tab<Real>(OFF + i * RI) * in[0];
 #pragma unroll
-    for (int j = 1; j < RI; ++j) acc = fma(tab<Real>(OFF + i * RI + j), in[j], acc);
-    out[i] = acc;
+      for (int j = 1; j < RI; ++j) acc = fma(tab<Real>(OFF + i * RI + j), in[j], acc);
+      out[i] = acc;
+    }
   }
 }
 
@@ -1120,6 +1175,7 @@ struct TckParams {
   int geo_step;  // geoT holds the Gauss sets m = n, n - geo_step, ... >= 2 (1 or 2)
   const void* geoKT;  // [E][DG_AFF_TCK]: J^-1 (9), -rho c^2, -1/rho
   const void* W;      // HDG-ADER: T_1 = W (the DG derivative, same basis as U) instead of -S U; else null
+  int* err;           // set (non-zero) if a bounded wait gave up (staged kernels only)
 };
 
 // m-point levels visited with reduction every RED-th derivative (RED = 0:

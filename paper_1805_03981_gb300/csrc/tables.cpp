@@ -132,6 +132,26 @@ int build_tables(HostTables* t) {
       t->tab[OFF_W(c) + a] = wg[a];
       t->tab[OFF_IW(c) + a] = 1.0 / wg[a];
     }
+    // even-odd forms of V, VI and D (see tables.h)
+    {
+      const int h = c / 2;
+      const double* mats[3] = {V, VI, D};
+      for (int w = 0; w < 3; ++w) {
+        const double* M = mats[w];
+        double* E = t->tab + OFF_EO(c, w);
+        for (int i = 0; i < dg_eo_len(c); ++i) E[i] = 0.0;
+        double* EA = E;
+        double* EB = E + (h + 1) * h;
+        double* EC = E + 2 * (h + 1) * h;
+        for (int i = 0; i <= h && i < c; ++i) {
+          for (int j = 0; j < h; ++j) {
+            EA[i * h + j] = 0.5 * (M[i * c + j] + M[i * c + (c - 1 - j)]);
+            EB[i * h + j] = 0.5 * (M[i * c + j] - M[i * c + (c - 1 - j)]);
+          }
+          if (c % 2 == 1) EC[i] = M[i * c + h];
+        }
+      }
+    }
     for (int red = 1; red <= 3; ++red) {
       if (c <= red) continue;
       const int r = c - red;

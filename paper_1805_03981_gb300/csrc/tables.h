@@ -15,6 +15,14 @@
 //     I_r [c][c-r] prolongation Gauss(c-r) -> Gauss(c):
 //                  I_r[q][b] = l^{c-r}_b(x^c_q)
 //   W  [c]         Gauss weights; IW [c] their inverses
+//   EO [3][...]    even-odd forms of V, VI (centrosymmetric, M[c-1-i][c-1-j]
+//                  = M[i][j], the point sets being symmetric) and D (skew:
+//                  = -M[i][j]); with h = c / 2, for rows i and columns j < h:
+//                  A[i][j] = (M[i][j] + M[i][c-1-j]) / 2,
+//                  B[i][j] = (M[i][j] - M[i][c-1-j]) / 2, C[i] = M[i][h]
+//                  (odd c): out = M in is then, with e_j = in_j + in_{c-1-j}
+//                  and o_j = in_j - in_{c-1-j}, p_i = A e + C_i in_h,
+//                  q_i = B o, out_i = p_i + q_i, out_{c-1-i} = +-(p_i - q_i)
 // The projection by r is exact because the c-point rule integrates the
 // product of degrees c-1 and c-r-1.
 #pragma once
@@ -28,8 +36,11 @@
 #endif
 
 DG_HD constexpr int dg_red_len(int c, int r) { return c > r ? 2 * c * (c - r) : 0; }
+// even-odd form of one centrosymmetric or skew-centrosymmetric c x c matrix
+// (h = c / 2): A [h+1][h], B [h+1][h], C [h+1]
+DG_HD constexpr int dg_eo_len(int c) { return 2 * (c / 2 + 1) * (c / 2) + (c / 2 + 1); }
 DG_HD constexpr int dg_tab_block(int c) {
-  return 3 * c * c + 2 * c + dg_red_len(c, 1) + dg_red_len(c, 2) + dg_red_len(c, 3) + 2 * c;
+  return 3 * c * c + 2 * c + dg_red_len(c, 1) + dg_red_len(c, 2) + dg_red_len(c, 3) + 2 * c + 3 * dg_eo_len(c);
 }
 DG_HD constexpr int dg_tab_base(int c) {
   return c <= 1 ? 0 : dg_tab_base(c - 1) + dg_tab_block(c - 1);
@@ -49,6 +60,8 @@ DG_HD constexpr int OFF_W(int c) {
   return dg_tab_base(c) + 3 * c * c + 2 * c + dg_red_len(c, 1) + dg_red_len(c, 2) + dg_red_len(c, 3);
 }
 DG_HD constexpr int OFF_IW(int c) { return OFF_W(c) + c; }
+// even-odd forms of V (which 0), VI (1) and D (2) of count c
+DG_HD constexpr int OFF_EO(int c, int which) { return OFF_IW(c) + c + which * dg_eo_len(c); }
 
 // Compact per-element data of affine elements with element-wise constant
 // coefficients (see setup.cu): operator block and predictor block sizes.

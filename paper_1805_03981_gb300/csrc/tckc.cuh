@@ -3,9 +3,15 @@
 // form.  It computes what tck_block computes in gmode, with the work laid
 // out for fewer shared-memory and index instructions:
 //
-// * Thread t of an element owns, at the current Gauss set of m points per
-//   direction, the z-column (x, y) = (t % m, t / m) of the current Taylor
-//   term T_j for all four fields, in registers (threads t >= m^2 idle).
+// * Each phase spreads its work items (columns, x-lines or y-lines of the
+//   current Gauss set) of all the block's elements over consecutive threads:
+//   item i of element e goes to thread e * count + i, count being the items
+//   per element.  At the full set (m = n, count n^2) thread e n^2 + t owns
+//   the z-column (x, y) = (t % n, t / n) of element e; at a reduced set the
+//   m^2 columns of every element are packed the same way, so the phase
+//   occupies ne m^2 threads in whole warps instead of m^2 of every n^2 (the
+//   idle threads skip it).  The owner of a column holds the current Taylor
+//   term T_j on it for all four fields, in registers.
 // * A derivative T_j = -S T_{j-1} (collocation at the m^3 Gauss points)
 //   differentiates along z in registers.  For x and y the column owners
 //   write their columns once to shared memory; thread t then owns the
@@ -59,12 +65,26 @@ struct TckcShape {
 
 template <typename Real>
 struct TckcCtx {
-  Real* s;        // this element's shared memory
-  const Real* g;  // this element's predictor geometry (curved)
-  Real gk[11];    // affine: (J^-1)_{d i} at gk[3 d + i], -rho c^2, -1/rho
-  int t;          // thread index within the element
-  int geo_step;   // stored Gauss sets m = n, n - geo_step, ...
-  bool act;       // the element slot holds an element
+  Real* sm;             // the block's shared memory (element slots SE Reals apart)
+  const Real* geoT;     // predictor geometry of the block's first element (curved)
+  long long geoT_stride;
+  const Real* geoKT;    // compact predictor data of the block's first element (affine)
+  int ne;               // elements in the block
+  int geo_step;         // stored Gauss sets m = n, n - geo_step, ...
+};
+
+// The work item of this thread in a phase with COUNT items per element:
+// element slot le, item t; on = the item exists.
+template <int COUNT>
+struct TckcSlot {
+  int le, t;
+  bool on;
+  template <typename Real>
+  __device__ __forceinline__ explicit TckcSlot(const TckcCtx<Real>& x) {
+    le = threadIdx.x / COUNT;
+    t = threadIdx.x - le * COUNT;
+    on = le < x.ne;
+  }
 };
 
 // geometry of the m-point set: the stored sets above it come first
@@ -82,13 +102,21 @@ __device__ __forceinline__ void tckc_derivative(Real (&c)[4][N], const TckcCtx<R
   using SH = TckcShape<N, RED, AFF>;
   constexpr int P = tckc_P(M), Q = tckc_Q(M), FT = SH::FT;
   constexpr int M2 = M * M, M3 = M2 * M;
-  Real* A = x.s;
-  Real* BX = x.s + SH::NA * FT;
+  const TckcSlot<M2> w(x);  // column (a, b), x-line (y, z) = (a, b), y-line (x, z) = (a, b)
+  Real* A = x.sm + w.le * SH::SE;
+  Real* BX = A + SH::NA * FT;
   Real* BY = BX + SH::NB * FT;
-  const bool on = x.act && x.t < M2;
-  const int a = x.t % M, b = x.t / M;
+  const bool on = w.on;
+  const int a = w.t % M, b = w.t / M;
   const int cb = a + P * b;  // column (x, y) = (a, b)
-  const Real* __restrict__ g = AFF ? nullptr : x.g + tckc_geo_off<N>(M, x.geo_step);
+  const Real* __restrict__ g =
+      AFF ? nullptr : x.geoT + (size_t)(on ? w.le : 0) * x.geoT_stride + tckc_geo_off<N>(M, x.geo_step);
+  Real gk[11];  // affine: (J^-1)_{d i} at gk[3 d + i], -rho c^2, -1/rho
+  if constexpr (AFF) {
+    const Real* k = x.geoKT + (size_t)(on ? w.le : 0) * DG_AFF_TCK;
+#pragma unroll
+    for (int i = 0; i < 11; ++i) gk[i] = __ldg(k + i);
+  }
   Real zc[SH::NB][M];
   if (on) {
     if constexpr (AFF) {
@@ -98,9 +126,9 @@ __device__ __forceinline__ void tckc_derivative(Real (&c)[4][N], const TckcCtx<R
         const Real v0 = c[1][z], v1 = c[2][z], v2 = c[3][z];
         p[z] = c[0][z];
         A[cb + Q * z] = p[z];
-        A[FT + cb + Q * z] = fma(x.gk[0], v0, fma(x.gk[1], v1, x.gk[2] * v2));
-        A[2 * FT + cb + Q * z] = fma(x.gk[3], v0, fma(x.gk[4], v1, x.gk[5] * v2));
-        w2[z] = fma(x.gk[6], v0, fma(x.gk[7], v1, x.gk[8] * v2));
+        A[FT + cb + Q * z] = fma(gk[0], v0, fma(gk[1], v1, gk[2] * v2));
+        A[2 * FT + cb + Q * z] = fma(gk[3], v0, fma(gk[4], v1, gk[5] * v2));
+        w2[z] = fma(gk[6], v0, fma(gk[7], v1, gk[8] * v2));
       }
       mv<Real, OFF_D(M), M, M>(p, zc[0]);
       mv<Real, OFF_D(M), M, M>(w2, zc[1]);
@@ -114,8 +142,8 @@ __device__ __forceinline__ void tckc_derivative(Real (&c)[4][N], const TckcCtx<R
       }
 #pragma unroll
       for (int z = 0; z < M; ++z) {
-        const Real j0 = __ldg(g + 6 * M3 + x.t + M2 * z), j1 = __ldg(g + 7 * M3 + x.t + M2 * z),
-                   j2 = __ldg(g + 8 * M3 + x.t + M2 * z);
+        const Real j0 = __ldg(g + 6 * M3 + w.t + M2 * z), j1 = __ldg(g + 7 * M3 + w.t + M2 * z),
+                   j2 = __ldg(g + 8 * M3 + w.t + M2 * z);
         zc[0][z] = fma(j0, d[1][z], fma(j1, d[2][z], j2 * d[3][z]));
         zc[1][z] = j0 * d[0][z];
         zc[2][z] = j1 * d[0][z];
@@ -163,8 +191,8 @@ __device__ __forceinline__ void tckc_derivative(Real (&c)[4][N], const TckcCtx<R
       }
 #pragma unroll
       for (int s = 0; s < M; ++s) {
-        const Real j0 = __ldg(g + 0 * M3 + x.t + M2 * s), j1 = __ldg(g + 1 * M3 + x.t + M2 * s),
-                   j2 = __ldg(g + 2 * M3 + x.t + M2 * s);
+        const Real j0 = __ldg(g + 0 * M3 + w.t + M2 * s), j1 = __ldg(g + 1 * M3 + w.t + M2 * s),
+                   j2 = __ldg(g + 2 * M3 + w.t + M2 * s);
         BX[xb + s] = fma(j0, d[1][s], fma(j1, d[2][s], j2 * d[3][s]));
         BX[FT + xb + s] = j0 * d[0][s];
         BX[2 * FT + xb + s] = j1 * d[0][s];
@@ -178,8 +206,8 @@ __device__ __forceinline__ void tckc_derivative(Real (&c)[4][N], const TckcCtx<R
       }
 #pragma unroll
       for (int s = 0; s < M; ++s) {
-        const Real j0 = __ldg(g + 3 * M3 + x.t + M2 * s), j1 = __ldg(g + 4 * M3 + x.t + M2 * s),
-                   j2 = __ldg(g + 5 * M3 + x.t + M2 * s);
+        const Real j0 = __ldg(g + 3 * M3 + w.t + M2 * s), j1 = __ldg(g + 4 * M3 + w.t + M2 * s),
+                   j2 = __ldg(g + 5 * M3 + w.t + M2 * s);
         BY[yb + P * s] = fma(j0, d[1][s], fma(j1, d[2][s], j2 * d[3][s]));
         BY[FT + yb + P * s] = j0 * d[0][s];
         BY[2 * FT + yb + P * s] = j1 * d[0][s];
@@ -194,12 +222,12 @@ __device__ __forceinline__ void tckc_derivative(Real (&c)[4][N], const TckcCtx<R
       const int i = cb + Q * z;
       if constexpr (AFF) {
         const Real dxp = BX[i], dxw = BX[FT + i], dyp = BY[i], dyw = BY[FT + i];
-        c[0][z] = x.gk[9] * (dxw + dyw + zc[1][z]);
-        c[1][z] = x.gk[10] * fma(x.gk[0], dxp, fma(x.gk[3], dyp, x.gk[6] * zc[0][z]));
-        c[2][z] = x.gk[10] * fma(x.gk[1], dxp, fma(x.gk[4], dyp, x.gk[7] * zc[0][z]));
-        c[3][z] = x.gk[10] * fma(x.gk[2], dxp, fma(x.gk[5], dyp, x.gk[8] * zc[0][z]));
+        c[0][z] = gk[9] * (dxw + dyw + zc[1][z]);
+        c[1][z] = gk[10] * fma(gk[0], dxp, fma(gk[3], dyp, gk[6] * zc[0][z]));
+        c[2][z] = gk[10] * fma(gk[1], dxp, fma(gk[4], dyp, gk[7] * zc[0][z]));
+        c[3][z] = gk[10] * fma(gk[2], dxp, fma(gk[5], dyp, gk[8] * zc[0][z]));
       } else {
-        const Real cp = __ldg(g + 9 * M3 + x.t + M2 * z), cv = __ldg(g + 10 * M3 + x.t + M2 * z);
+        const Real cp = __ldg(g + 9 * M3 + w.t + M2 * z), cv = __ldg(g + 10 * M3 + w.t + M2 * z);
         c[0][z] = cp * (zc[0][z] + BX[i] + BY[i]);
 #pragma unroll
         for (int f = 1; f < 4; ++f) c[f][z] = cv * (zc[f][z] + BX[f * FT + i] + BY[f * FT + i]);
@@ -209,57 +237,73 @@ __device__ __forceinline__ void tckc_derivative(Real (&c)[4][N], const TckcCtx<R
 }
 
 // Reference L2 projection M -> MR (Sec. 3.3) of the column registers; on
-// return the threads t < MR^2 own the columns of the MR-point set.
+// return the owners of the MR-point columns (packed) hold them.
 template <int N, typename Real, int RED, bool AFF, int M, int MR>
 __device__ __forceinline__ void tckc_project(Real (&c)[4][N], const TckcCtx<Real>& x) {
   using SH = TckcShape<N, RED, AFF>;
   constexpr int P = tckc_P(M), Q = tckc_Q(M), PR = tckc_P(MR), QR = tckc_Q(MR), FT = SH::FT;
   constexpr int OFF = OFF_PR(M, M - MR);  // MR x M
-  Real* S1 = x.s;
-  Real* S2 = x.s + 4 * FT;
-  if (x.act && x.t < M * M) {  // z, in registers
-    const int cb = x.t % M + P * (x.t / M);
+  {  // z, in the registers of the M-point column owners
+    const TckcSlot<M * M> w(x);
+    if (w.on) {
+      Real* S1 = x.sm + w.le * SH::SE;
+      const int cb = w.t % M + P * (w.t / M);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      Real o[MR];
-      mv<Real, OFF, MR, M>(c[f], o);
+      for (int f = 0; f < 4; ++f) {
+        Real o[MR];
+        mv<Real, OFF, MR, M>(c[f], o);
 #pragma unroll
-      for (int z = 0; z < MR; ++z) S1[f * FT + cb + Q * z] = o[z];
+        for (int z = 0; z < MR; ++z) S1[f * FT + cb + Q * z] = o[z];
+      }
     }
   }
   __syncthreads();
-  if (x.act && x.t < M * MR) {  // x-lines (y, z), y < M, z < MR
-    const int base = P * (x.t % M) + Q * (x.t / M);
+  {  // x-lines (y, z), y < M, z < MR
+    const TckcSlot<M * MR> w(x);
+    if (w.on) {
+      Real* S1 = x.sm + w.le * SH::SE;
+      Real* S2 = S1 + 4 * FT;
+      const int base = P * (w.t % M) + Q * (w.t / M);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      Real in[M], o[MR];
+      for (int f = 0; f < 4; ++f) {
+        Real in[M], o[MR];
 #pragma unroll
-      for (int s = 0; s < M; ++s) in[s] = S1[f * FT + base + s];
-      mv<Real, OFF, MR, M>(in, o);
+        for (int s = 0; s < M; ++s) in[s] = S1[f * FT + base + s];
+        mv<Real, OFF, MR, M>(in, o);
 #pragma unroll
-      for (int s = 0; s < MR; ++s) S2[f * FT + base + s] = o[s];
+        for (int s = 0; s < MR; ++s) S2[f * FT + base + s] = o[s];
+      }
     }
   }
   __syncthreads();
-  if (x.act && x.t < MR * MR) {  // y-lines (x, z), x, z < MR; written in the MR-point layout
-    const int xx = x.t % MR, zz = x.t / MR;
+  {  // y-lines (x, z), x, z < MR; written in the MR-point layout
+    const TckcSlot<MR * MR> w(x);
+    if (w.on) {
+      Real* S1 = x.sm + w.le * SH::SE;
+      Real* S2 = S1 + 4 * FT;
+      const int xx = w.t % MR, zz = w.t / MR;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      Real in[M], o[MR];
+      for (int f = 0; f < 4; ++f) {
+        Real in[M], o[MR];
 #pragma unroll
-      for (int s = 0; s < M; ++s) in[s] = S2[f * FT + xx + P * s + Q * zz];
-      mv<Real, OFF, MR, M>(in, o);
+        for (int s = 0; s < M; ++s) in[s] = S2[f * FT + xx + P * s + Q * zz];
+        mv<Real, OFF, MR, M>(in, o);
 #pragma unroll
-      for (int s = 0; s < MR; ++s) S1[f * FT + xx + PR * s + QR * zz] = o[s];
+        for (int s = 0; s < MR; ++s) S1[f * FT + xx + PR * s + QR * zz] = o[s];
+      }
     }
   }
   __syncthreads();
-  if (x.act && x.t < MR * MR) {  // the new column owners read their columns
-    const int cb = x.t % MR + PR * (x.t / MR);
+  {  // the new column owners read their columns
+    const TckcSlot<MR * MR> w(x);
+    if (w.on) {
+      const Real* S1 = x.sm + w.le * SH::SE;
+      const int cb = w.t % MR + PR * (w.t / MR);
 #pragma unroll
-    for (int f = 0; f < 4; ++f)
+      for (int f = 0; f < 4; ++f)
 #pragma unroll
-      for (int z = 0; z < MR; ++z) c[f][z] = S1[f * FT + cb + QR * z];
+        for (int z = 0; z < MR; ++z) c[f][z] = S1[f * FT + cb + QR * z];
+    }
   }
 }
 
@@ -267,7 +311,8 @@ __device__ __forceinline__ void tckc_project(Real (&c)[4][N], const TckcCtx<Real
 template <int N, typename Real, int RED, bool AFF, int L, int M, bool FIRST>
 __device__ __forceinline__ void tckc_accumulate(const Real (&c)[4][N], Real (&acc)[4][N],
                                                 const TckcCtx<Real>& x, Real cj) {
-  if (!(x.act && x.t < M * M)) return;
+  const TckcSlot<M * M> w(x);
+  if (!w.on) return;
   if constexpr (L == 0) {
 #pragma unroll
     for (int f = 0; f < 4; ++f)
@@ -275,12 +320,12 @@ __device__ __forceinline__ void tckc_accumulate(const Real (&c)[4][N], Real (&ac
       for (int z = 0; z < M; ++z) acc[f][z] = fma(cj, c[f][z], acc[f][z]);
   } else {
     constexpr int M3 = M * M * M;
-    Real* a = x.s + TckcShape<N, RED, AFF>::acc_off(L);
+    Real* a = x.sm + w.le * TckcShape<N, RED, AFF>::SE + TckcShape<N, RED, AFF>::acc_off(L);
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
       for (int z = 0; z < M; ++z) {
-        Real* q = a + f * M3 + x.t + M * M * z;
+        Real* q = a + f * M3 + w.t + M * M * z;
         *q = FIRST ? cj * c[f][z] : fma(cj, c[f][z], *q);
       }
   }
@@ -293,11 +338,12 @@ __device__ __forceinline__ void tckc_steps(Real (&c)[4][N], Real (&acc)[4][N], c
   if constexpr (J <= N && M >= 2) {  // at M = 1 the derivative of a constant vanishes: so does every later term
     if (J == 1 && W) {  // HDG-ADER (Eq. hdg-ader): the DG derivative in place of -S U
       constexpr int N2 = N * N, N3 = N2 * N;
-      if (x.act)
+      const TckcSlot<N2> w(x);
+      if (w.on)
 #pragma unroll
         for (int f = 0; f < 4; ++f)
 #pragma unroll
-          for (int z = 0; z < N; ++z) c[f][z] = __ldg(W + f * N3 + x.t + N2 * z);
+          for (int z = 0; z < N; ++z) c[f][z] = __ldg(W + f * N3 + w.t + N2 * z);
     } else {
       tckc_derivative<N, Real, RED, AFF, M>(c, x);
     }
@@ -325,50 +371,62 @@ __device__ __forceinline__ void tckc_fold(Real (&acc)[4][N], const TckcCtx<Real>
   constexpr int M2 = M * M, M3 = M2 * M;
   constexpr int PB = tckc_P(B), QB = tckc_Q(B), FT = SH::FT;
   constexpr int OFF = OFF_IR(B, RED);  // B x M
-  const Real* src = x.s + SH::acc_off(L);
-  Real* S1 = x.s;
-  Real* S2 = x.s + 4 * FT;
-  if (x.act && x.t < M2) {  // x-lines (y, z) of the compact M^3 sums
-    const int y = x.t % M, z = x.t / M;
+  {  // x-lines (y, z) of the compact M^3 sums
+    const TckcSlot<M2> w(x);
+    if (w.on) {
+      Real* sE = x.sm + w.le * SH::SE;
+      const Real* src = sE + SH::acc_off(L);
+      const int y = w.t % M, z = w.t / M;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      Real in[M], o[B];
+      for (int f = 0; f < 4; ++f) {
+        Real in[M], o[B];
 #pragma unroll
-      for (int s = 0; s < M; ++s) in[s] = src[f * M3 + s + M * y + M2 * z];
-      mv<Real, OFF, B, M>(in, o);
+        for (int s = 0; s < M; ++s) in[s] = src[f * M3 + s + M * y + M2 * z];
+        mv<Real, OFF, B, M>(in, o);
 #pragma unroll
-      for (int s = 0; s < B; ++s) S1[f * FT + s + PB * y + QB * z] = o[s];
+        for (int s = 0; s < B; ++s) sE[f * FT + s + PB * y + QB * z] = o[s];
+      }
     }
   }
   __syncthreads();
-  if (x.act && x.t < B * M) {  // y-lines (x, z), x < B, z < M
-    const int xx = x.t % B, z = x.t / B;
+  {  // y-lines (x, z), x < B, z < M
+    const TckcSlot<B * M> w(x);
+    if (w.on) {
+      Real* S1 = x.sm + w.le * SH::SE;
+      Real* S2 = S1 + 4 * FT;
+      const int xx = w.t % B, z = w.t / B;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      Real in[M], o[B];
+      for (int f = 0; f < 4; ++f) {
+        Real in[M], o[B];
 #pragma unroll
-      for (int s = 0; s < M; ++s) in[s] = S1[f * FT + xx + PB * s + QB * z];
-      mv<Real, OFF, B, M>(in, o);
+        for (int s = 0; s < M; ++s) in[s] = S1[f * FT + xx + PB * s + QB * z];
+        mv<Real, OFF, B, M>(in, o);
 #pragma unroll
-      for (int s = 0; s < B; ++s) S2[f * FT + xx + PB * s + QB * z] = o[s];
+        for (int s = 0; s < B; ++s) S2[f * FT + xx + PB * s + QB * z] = o[s];
+      }
     }
   }
   __syncthreads();
-  if (x.act && x.t < B * B) {  // z, by the B-point column owners
-    const int cb = x.t % B + PB * (x.t / B);
+  {  // z, by the B-point column owners
+    const TckcSlot<B * B> w(x);
+    if (w.on) {
+      Real* sE = x.sm + w.le * SH::SE;
+      const Real* S2 = sE + 4 * FT;
+      const int cb = w.t % B + PB * (w.t / B);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      Real in[M], o[B];
+      for (int f = 0; f < 4; ++f) {
+        Real in[M], o[B];
 #pragma unroll
-      for (int s = 0; s < M; ++s) in[s] = S2[f * FT + cb + QB * s];
-      mv<Real, OFF, B, M>(in, o);
-      if constexpr (L == 1) {
+        for (int s = 0; s < M; ++s) in[s] = S2[f * FT + cb + QB * s];
+        mv<Real, OFF, B, M>(in, o);
+        if constexpr (L == 1) {
 #pragma unroll
-        for (int z = 0; z < B; ++z) acc[f][z] += o[z];
-      } else {
-        Real* dst = x.s + SH::acc_off(L - 1) + f * B * B * B + x.t;
+          for (int z = 0; z < B; ++z) acc[f][z] += o[z];
+        } else {
+          Real* dst = sE + SH::acc_off(L - 1) + f * B * B * B + w.t;
 #pragma unroll
-        for (int z = 0; z < B; ++z) dst[B * B * z] += o[z];
+          for (int z = 0; z < B; ++z) dst[B * B * z] += o[z];
+        }
       }
     }
   }
@@ -382,28 +440,24 @@ __device__ __forceinline__ void tckc_block(const TckParams& p, const int e0, con
   using SH = TckcShape<N, RED, AFF>;
   constexpr int N2 = N * N, N3 = N2 * N;
   TckcCtx<Real> x;
-  const int le = threadIdx.x / N2;
-  x.t = threadIdx.x - le * N2;
-  x.act = le < ne;
-  x.s = sm + le * SH::SE;
+  x.sm = sm;
+  x.ne = ne;
   x.geo_step = p.geo_step;
-  const size_t e = (size_t)e0 + (x.act ? le : 0);
-  x.g = AFF ? nullptr : static_cast<const Real*>(p.geoT) + e * (size_t)p.geoT_stride;
-  if constexpr (AFF) {
-    const Real* gk = static_cast<const Real*>(p.geoKT) + e * DG_AFF_TCK;
-#pragma unroll
-    for (int i = 0; i < 11; ++i) x.gk[i] = __ldg(gk + i);
-  }
+  x.geoT_stride = p.geoT_stride;
+  x.geoT = AFF ? nullptr : static_cast<const Real*>(p.geoT) + (size_t)e0 * (size_t)p.geoT_stride;
+  x.geoKT = AFF ? static_cast<const Real*>(p.geoKT) + (size_t)e0 * DG_AFF_TCK : nullptr;
+  const TckcSlot<N2> w(x);  // the n-point column owners: thread le n^2 + t
+  const size_t e = (size_t)e0 + (w.on ? w.le : 0);
   const Real* __restrict__ U = static_cast<const Real*>(p.U) + e * 4 * N3;
   const Real* __restrict__ W = p.W ? static_cast<const Real*>(p.W) + e * 4 * N3 : nullptr;
   Real c[4][N], acc[4][N];
   const Real c0 = (Real)p.coef[0];
-  if (x.act) {
+  if (w.on) {
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
       for (int z = 0; z < N; ++z) {
-        c[f][z] = __ldg(U + f * N3 + x.t + N2 * z);
+        c[f][z] = __ldg(U + f * N3 + w.t + N2 * z);
         acc[f][z] = c0 * c[f][z];
       }
   }
@@ -412,12 +466,12 @@ __device__ __forceinline__ void tckc_block(const TckParams& p, const int e0, con
     __syncthreads();
     tckc_fold<N, Real, RED, AFF, SH::NL - 1>(acc, x);
   }
-  if (x.act) {
+  if (w.on) {
     Real* __restrict__ out = static_cast<Real*>(p.Ubar) + e * 4 * N3;
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
-      for (int z = 0; z < N; ++z) out[f * N3 + x.t + N2 * z] = acc[f][z];
+      for (int z = 0; z < N; ++z) out[f * N3 + w.t + N2 * z] = acc[f][z];
   }
 }
 

@@ -16,6 +16,27 @@ def contraction(outputs, m):
     return 2 * m * outputs
 
 
+def eo_line(m):
+    """Flops of one m-point line of a square centrosymmetric or
+    skew-centrosymmetric contraction (V, V^-1, D) in the even-odd form the
+    kernels use for m >= 5 (h = m // 2): h sums and h differences, two h x h
+    products, h more multiply-adds with the middle value and the middle row
+    for odd m, and h sums and h differences to combine; 2 m^2 below m = 5."""
+    if m < 5:
+        return 2 * m * m
+    h = m // 2
+    f = 2 * h + 4 * h * h + 2 * h
+    if m % 2:
+        f += 2 * h + 2 * h + 2
+    return f
+
+
+def sq_contraction(outputs, m):
+    """A square V, V^-1 or D contraction producing `outputs` values along
+    m-point lines (the even-odd count where the kernels use it)."""
+    return outputs // m * eo_line(m)
+
+
 def operator_flops(n, curved=True, nonwall_frac=1.0, basis="gl", affine=False):
     """R = -M^-1 K U on one element: basis changes, cell terms, faces, M^-1.
     basis "g": the state is held at the Gauss points (no basis changes; a
@@ -36,15 +57,15 @@ def operator_flops(n, curved=True, nonwall_frac=1.0, basis="gl", affine=False):
         f += 4 * N3
         return f
     f = 0
-    f += 12 * contraction(N3, n)            # GL -> G, 4 fields x 3 directions
+    f += 12 * sq_contraction(N3, n)         # GL -> G, 4 fields x 3 directions
     f += 3 * N3 * (5 + 3)                   # contravariant fluxes per direction
     f += 12 * contraction(N3, n)            # test-gradient (transposed derivative)
     f += 2 * 4 * N3                         # accumulation over the 3 directions
     face_pt = 4 * 2 * n + 5 + 5 + 2 + 4 + 4 + 3 + 4 * 2 * n
     f += 6 * N2 * face_pt                   # traces, flux, lifting
-    f += nonwall_frac * 6 * 4 * 2 * contraction(N2, n)   # neighbour GL face nodes -> Gauss
+    f += nonwall_frac * 6 * 4 * 2 * sq_contraction(N2, n)   # neighbour GL face nodes -> Gauss
     f += 4 * N3                             # diagonal inverse mass
-    f += 12 * contraction(N3, n)            # G -> GL
+    f += 12 * sq_contraction(N3, n)         # G -> GL
     return f
 
 
@@ -67,7 +88,7 @@ def tck_levels(n, red):
 
 def tck_flops(n, red=2, basis="gl", affine=False):
     N3 = n ** 3
-    f = 0 if basis == "g" else 12 * contraction(N3, n) + 12 * contraction(N3, n)   # GL -> G, G -> GL
+    f = 0 if basis == "g" else 12 * sq_contraction(N3, n) + 12 * sq_contraction(N3, n)   # GL -> G, G -> GL
     deriv_contr, deriv_pt = (6, 36) if affine else (12, 36)
     f += 2 * 4 * N3                                          # first Taylor term
     m = n
@@ -77,7 +98,7 @@ def tck_flops(n, red=2, basis="gl", affine=False):
             break
         if m > 1:
             m3 = m ** 3
-            f += deriv_contr * contraction(m3, m) + deriv_pt * m3   # derivatives + chain rule
+            f += deriv_contr * sq_contraction(m3, m) + deriv_pt * m3   # derivatives + chain rule
         if red and j % red == 0:
             if m - red < 1:
                 break
@@ -142,7 +163,7 @@ def flops_per_element(kind, n, red=2, nonwall_frac=1.0, basis="gl", affine=False
     if kind == "tck":
         return tck_flops(n, red, basis, affine)
     if kind == "other":                       # change of basis of a whole state
-        return 12 * contraction(n ** 3, n)
+        return 12 * sq_contraction(n ** 3, n)
     return (operator_flops(n, nonwall_frac=nonwall_frac, basis=basis, affine=affine and basis == "g")
             + EPILOGUE_FLOPS[kind] * 4 * n ** 3)
 

@@ -16,7 +16,12 @@ dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 
     python -m paper_1805_03981_gb300.traffic --csv launches.csv \\
         --workload curved_pulse --prec fp64 --size 32 --k 5 --basis g \\
-        --tiling 5,5 --command "<the ncu command line>"
+        --tiling 5,5 --measured-size 24 --command "<the ncu command line>"
+
+``--measured-size`` records a capture taken on a smaller mesh of the same
+recipe (so that ncu holds a few GB at most) for the full size: every kernel
+here moves a fixed number of bytes per element, so the bytes (and times)
+scale by the ratio of element counts, (size / measured size)^3.
 """
 import argparse
 import csv
@@ -32,7 +37,7 @@ COLUMNS = ("workload", "prec", "size", "k", "basis", "kernel", "elements_per_blo
 NKEY = 7
 
 # epilogue template argument of the operator kernels -> kernel kind
-_EPI_KIND = {0: "operator", 1: "lsrk_stage", 2: "ader_update"}
+_EPI_KIND = {0: "operator", 1: "lsrk_stage", 2: "ader_update", 3: "lsrk_stage"}
 
 
 # The sources that determine the code of the recorded kernels (the 3D operator
@@ -43,8 +48,8 @@ _EPI_KIND = {0: "operator", 1: "lsrk_stage", 2: "ader_update"}
 DIGEST_FILES = ("dg_kernels.cuh", "kern_inst.cuh", "kern_f64_lo.cu", "kern_f64_hi.cu", "kern_f32_lo.cu",
                 "kern_f32_hi.cu", "kern_tck_odd_f64.cu", "kern_tck_odd_f32.cu", "tckc.cuh",
                 "kern_tckc_f64_lo.cu", "kern_tckc_f64_hi.cu", "kern_tckc_f32_lo.cu", "kern_tckc_f32_hi.cu",
-                "tckn.cuh", "kern_tckn.cu",
-                "tables.h", "tables.cpp", "setup.cu")
+                "tckn.cuh", "kern_tckn.cu", "tcki.cuh", "kern_tcki_f32.cu", "kern_lsrk2r_f64.cu",
+                "kern_lsrk2r_f32.cu", "tables.h", "tables.cpp", "setup.cu")
 
 
 def sources_digest():
@@ -65,7 +70,7 @@ def kernel_kind(name):
     m = re.search(r"\b(op|opg|opga)_kernel<\s*\d+\s*,\s*\w+\s*,\s*(\d+)\s*>", name)
     if m:
         return _EPI_KIND.get(int(m.group(2)))
-    if re.search(r"\btck[cn]?_kernel<", name):
+    if re.search(r"\btck[cni]?_kernel<", name):
         return "tck"
     return None
 
@@ -138,9 +143,11 @@ def lookup(workload, prec, size, k, basis, tiling, kernel, path=TABLE):
     return None
 
 
-def record(csv_path, workload, prec, size, k, basis, tiling, command, path=TABLE):
+def record(csv_path, workload, prec, size, k, basis, tiling, command, path=TABLE, measured_size=None):
     """Merge the kinds measured in one ncu CSV into the table.  Rows recorded
-    with other sources are dropped, as they no longer describe the kernels."""
+    with other sources are dropped, as they no longer describe the kernels.
+    measured_size: the capture's mesh size when smaller than size (the
+    figures are scaled by the ratio of element counts)."""
     digest = sources_digest()
     old_digest, comments, rows = read_table(path)
     if old_digest != digest:
@@ -148,6 +155,12 @@ def record(csv_path, workload, prec, size, k, basis, tiling, command, path=TABLE
     measured = parse_ncu_csv(csv_path)
     if not measured:
         raise ValueError("no launches of the path's kernels in %s" % csv_path)
+    if measured_size and measured_size != size:
+        f = (float(size) / measured_size) ** 3
+        for m in measured.values():
+            for key in ("read_bytes", "write_bytes", "traffic_bytes", "avg_us"):
+                m[key] *= f
+        command = "%s   [taken at size %d, scaled by (%d/%d)^3]" % (command, measured_size, size, measured_size)
     for kind, m in sorted(measured.items()):
         row = {"workload": workload, "prec": prec, "size": size, "k": k, "basis": basis,
                "kernel": kind, "elements_per_block": _epb(kind, tiling),
@@ -182,11 +195,12 @@ def main():
     ap.add_argument("--basis", required=True, choices=["g", "gl"])
     ap.add_argument("--tiling", required=True, help="op,tck elements per block")
     ap.add_argument("--command", required=True)
+    ap.add_argument("--measured-size", type=int, default=0)
     ap.add_argument("--out", default=TABLE)
     a = ap.parse_args()
     tiling = tuple(int(x) for x in a.tiling.split(","))
     for kind, m in sorted(record(a.csv, a.workload, a.prec, a.size, a.k, a.basis, tiling,
-                                 a.command, a.out).items()):
+                                 a.command, a.out, a.measured_size or None).items()):
         print("%-12s launches %3d  traffic %.4g B/launch  avg %.1f us"
               % (kind, m["launches"], m["traffic_bytes"], m["avg_us"]))
 

@@ -128,9 +128,36 @@ def test_predictor_kernel_argument():
     cfg = _curved(2, 2, seed=450)
     s, _ = pair(cfg)
     assert s.predictor_kernel() == dgw.PRED_AUTO
-    for kind in (dgw.PRED_LINES, dgw.PRED_COLUMNS, dgw.PRED_AUTO):
+    for kind in (dgw.PRED_LINES, dgw.PRED_COLUMNS, dgw.PRED_INTERLEAVED, dgw.PRED_AUTO):
         s.set_predictor_kernel(kind)
         assert s.predictor_kernel() == kind
-    for bad in (-1, 4):
+    for bad in (-1, 5):
         with pytest.raises(dgw.DGError):
             s.set_predictor_kernel(bad)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("red", [0, 2])
+@pytest.mark.parametrize("N", [2, 3])
+def test_interleaved_equals_columns_bitwise(k, red, N):
+    """FP32 affine elements with constant coefficients: the interleaved
+    column form (tcki.cuh, DG_PRED_INTERLEAVED, the FP32 default there)
+    gives the column form's results bit for bit, on full blocks and on a
+    ragged last block (N^3 = 8 or 27 elements, 8 or 4 per block), and is at
+    oracle parity."""
+    torch = _cuda()
+    cfg = _affine(N, k, seed=300 + 10 * k + red + N)
+    s = dgw.Solver(cfg["mesh"], k, dgw.DG_FP32, 1.0, cfg["rho"], cfg["c"])
+    assert s.is_affine()
+    dt = 0.004
+    Ui = _ader(s, cfg["U0"], dgw.PRED_INTERLEAVED, dt, 2, red)
+    Ua = _ader(s, cfg["U0"], dgw.PRED_AUTO, dt, 2, red)
+    Uc = _ader(s, cfg["U0"], dgw.PRED_COLUMNS, dt, 2, red)
+    torch.cuda.synchronize()
+    s.check_device()
+    assert torch.equal(Ui, Uc)
+    assert torch.equal(Ua, Uc)
+    import oracle
+    o = oracle.Oracle(cfg["mesh"], k, cfg["rho"], cfg["c"], 1.0)
+    assert rel_l2(Ui.cpu().numpy(), o.ader(cfg["U0"], dt, 2, red)) < 2e-5
+    s.close()
