@@ -1138,7 +1138,18 @@ __global__ void basis_kernel(const void* src, void* dst, int E, int to_g) {
   // 4 N^3 Reals per element is a multiple of VW, and states are 16-byte aligned
   const Vec* in = reinterpret_cast<const Vec*>(static_cast<const Real*>(src) + (size_t)e0 * 4 * N3);
   Vec* smv = reinterpret_cast<Vec*>(sm);
-  for (int i = threadIdx.x; i < ne * 4 * N3 / VW; i += blockDim.x) smv[i] = in[i];
+  {  // four loads in flight per thread: a host source answers with a long latency
+    const int nv = ne * 4 * N3 / VW, bd = blockDim.x;
+    int i = threadIdx.x;
+    for (; i + 3 * bd < nv; i += 4 * bd) {
+      const Vec v0 = in[i], v1 = in[i + bd], v2 = in[i + 2 * bd], v3 = in[i + 3 * bd];
+      smv[i] = v0;
+      smv[i + bd] = v1;
+      smv[i + 2 * bd] = v2;
+      smv[i + 3 * bd] = v3;
+    }
+    for (; i < nv; i += bd) smv[i] = in[i];
+  }
   __syncthreads();
   const bool act = le < ne;
   if (to_g) {

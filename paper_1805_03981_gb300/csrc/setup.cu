@@ -27,24 +27,41 @@ namespace {
 
 constexpr int CMAX = DG_NMAX + 2;
 
-__device__ void lag1d(const double* nodes, int c, double x, double* L, double* dL) {
+// inv[a c + b] = 1 / (nodes[a] - nodes[b]) (a != b), computed once per block
+// into shared memory by fill_inv, so that no point evaluation divides.
+__device__ void fill_inv(const double* nodes, int c, double* inv) {
+  for (int i = threadIdx.x; i < c * c; i += blockDim.x) {
+    const int a = i / c, b = i - a * c;
+    inv[i] = a == b ? 0.0 : 1.0 / (nodes[a] - nodes[b]);
+  }
+}
+
+// Lagrange polynomials of the c nodes (and their derivatives) at x.
+__device__ void lag1d(const double* nodes, const double* inv, int c, double x, double* L, double* dL) {
   for (int a = 0; a < c; ++a) {
     double v = 1.0, d = 0.0;
     for (int b = 0; b < c; ++b) {
       if (b == a) continue;
-      const double inv = 1.0 / (nodes[a] - nodes[b]);
-      d = d * (x - nodes[b]) * inv + v * inv;
-      v *= (x - nodes[b]) * inv;
+      const double iv = inv[a * c + b];
+      d = d * (x - nodes[b]) * iv + v * iv;
+      v *= (x - nodes[b]) * iv;
     }
     L[a] = v;
     if (dL) dL[a] = d;
   }
 }
 
-__device__ void jacobian(const SetupParams& P, int e, const double xi[3], double J[3][3]) {
+// the node inverse-difference tables of the geometry (q+1 points) and of the
+// solution (n points) nodes, in shared memory
+struct InvTabs {
+  double q[(DG_NMAX + 2) * (DG_NMAX + 2)];
+  double gl[(DG_NMAX + 2) * (DG_NMAX + 2)];
+};
+
+__device__ void jacobian(const SetupParams& P, const InvTabs& T, int e, const double xi[3], double J[3][3]) {
   const int c = P.q + 1;
   double L[3][CMAX], dL[3][CMAX];
-  for (int d = 0; d < 3; ++d) lag1d(P.xq, c, xi[d], L[d], dL[d]);
+  for (int d = 0; d < 3; ++d) lag1d(P.xq, T.q, c, xi[d], L[d], dL[d]);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) J[i][j] = 0.0;
   const double* X = P.nodes + (size_t)e * c * c * c * 3;
@@ -78,9 +95,9 @@ __device__ double adjugate(const double J[3][3], double A[3][3]) {
   return J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
 }
 
-__device__ double nodal_at(const double* f, const double* xgl, int n, const double xi[3]) {
+__device__ double nodal_at(const double* f, const double* xgl, const double* inv, int n, const double xi[3]) {
   double L[3][CMAX];
-  for (int d = 0; d < 3; ++d) lag1d(xgl, n, xi[d], L[d], nullptr);
+  for (int d = 0; d < 3; ++d) lag1d(xgl, inv, n, xi[d], L[d], nullptr);
   double s = 0.0;
   for (int z = 0; z < n; ++z)
     for (int y = 0; y < n; ++y) {
@@ -109,6 +126,10 @@ __global__ void setup_kernel(const SetupParams P) {
   const double* xg = P.pts + dg_pts_off(n);
   const double* wg = P.pts + DG_PTS_LEN + dg_pts_off(n);
   const double* xgl = P.pts + 2 * DG_PTS_LEN + dg_pts_off(n);
+  __shared__ InvTabs T;
+  fill_inv(P.xq, P.q + 1, T.q);
+  fill_inv(xgl, n, T.gl);
+  __syncthreads();
   const double* rho = P.rho + (size_t)e * n3;
   const double* cc = P.c + (size_t)e * n3;
   const int ncell = n3, nface = 6 * n2;
@@ -124,10 +145,10 @@ __global__ void setup_kernel(const SetupParams P) {
       xi[1] = xg[y];
       xi[2] = xg[z];
       const double w = wg[x] * wg[y] * wg[z];
-      jacobian(P, e, xi, J);
+      jacobian(P, T, e, xi, J);
       const double det = adjugate(J, A);
       if (!(det > 0.0)) atomicExch(P.bad, 1);
-      const double r = nodal_at(rho, xgl, n, xi), c = nodal_at(cc, xgl, n, xi);
+      const double r = nodal_at(rho, xgl, T.gl, n, xi), c = nodal_at(cc, xgl, T.gl, n, xi);
       for (int d = 0; d < 3; ++d)
         for (int i = 0; i < 3; ++i)
           put(P.geoA, (size_t)e * geo_stride_A(n) + (d * 3 + i) * n3 + line_major(d, n, x, y, z), w * A[d][i],
@@ -143,13 +164,13 @@ __global__ void setup_kernel(const SetupParams P) {
       xi[d] = side;
       xi[t0] = xg[i];
       xi[t1] = xg[j];
-      jacobian(P, e, xi, J);
+      jacobian(P, T, e, xi, J);
       const double det = adjugate(J, A);
       if (!(det > 0.0)) atomicExch(P.bad, 1);
       const double wf = wg[i] * wg[j];
       const double nw[3] = {wf * side * A[d][0], wf * side * A[d][1], wf * side * A[d][2]};
       const double s = sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
-      const double zm = nodal_at(rho, xgl, n, xi) * nodal_at(cc, xgl, n, xi);
+      const double zm = nodal_at(rho, xgl, T.gl, n, xi) * nodal_at(cc, xgl, T.gl, n, xi);
       double zp = zm;
       const int en = P.nbr[e * 6 + f];
       if (en >= 0) {
@@ -161,7 +182,7 @@ __global__ void setup_kernel(const SetupParams P) {
         xn[dn] = (fn & 1) ? 1.0 : -1.0;
         xn[dn == 0 ? 1 : 0] = xg[ip];
         xn[dn == 2 ? 1 : 2] = xg[jp];
-        zp = nodal_at(P.rho + (size_t)en * n3, xgl, n, xn) * nodal_at(P.c + (size_t)en * n3, xgl, n, xn);
+        zp = nodal_at(P.rho + (size_t)en * n3, xgl, T.gl, n, xn) * nodal_at(P.c + (size_t)en * n3, xgl, T.gl, n, xn);
       }
       const double zs = zm + zp;
       const size_t fb = (size_t)e * geo_stride_F(n) + (size_t)f * 6 * n2 + ij;
@@ -184,10 +205,10 @@ __global__ void setup_kernel(const SetupParams P) {
       xi[0] = xm[x];
       xi[1] = xm[y];
       xi[2] = xm[z];
-      jacobian(P, e, xi, J);
+      jacobian(P, T, e, xi, J);
       const double det = adjugate(J, A);
       if (!(det > 0.0)) atomicExch(P.bad, 1);
-      const double r = nodal_at(rho, xgl, n, xi), c = nodal_at(cc, xgl, n, xi);
+      const double r = nodal_at(rho, xgl, T.gl, n, xi), c = nodal_at(cc, xgl, T.gl, n, xi);
       const size_t tb = (size_t)e * P.tstride + off;
       for (int d = 0; d < 3; ++d)
         for (int i = 0; i < 3; ++i)
@@ -208,16 +229,20 @@ __global__ void setup_kernel(const SetupParams P) {
 // general layout are w adj(J), m / w, w_f nw0, b0 / w_f and c0 w_f.
 __global__ void setup_affine_kernel(const SetupParams P) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= P.E) return;
   const int n = P.n, n3 = n * n * n;
   const double* xgl = P.pts + 2 * DG_PTS_LEN + dg_pts_off(n);
+  __shared__ InvTabs T;
+  fill_inv(P.xq, P.q + 1, T.q);
+  fill_inv(xgl, n, T.gl);
+  __syncthreads();
+  if (e >= P.E) return;
   const double ctr[3] = {0.0, 0.0, 0.0};
   double J[3][3], A[3][3];
-  jacobian(P, e, ctr, J);
+  jacobian(P, T, e, ctr, J);
   const double det = adjugate(J, A);
   if (!(det > 0.0)) atomicExch(P.bad, 1);
-  const double r = nodal_at(P.rho + (size_t)e * n3, xgl, n, ctr);
-  const double c = nodal_at(P.c + (size_t)e * n3, xgl, n, ctr);
+  const double r = nodal_at(P.rho + (size_t)e * n3, xgl, T.gl, n, ctr);
+  const double c = nodal_at(P.c + (size_t)e * n3, xgl, T.gl, n, ctr);
   const size_t kb = (size_t)e * DG_AFF_OP, tb = (size_t)e * DG_AFF_TCK;
   for (int d = 0; d < 3; ++d)
     for (int i = 0; i < 3; ++i) {
@@ -237,7 +262,7 @@ __global__ void setup_affine_kernel(const SetupParams P) {
     double zp = zm;
     const int en = P.nbr[e * 6 + f];
     if (en >= 0)
-      zp = nodal_at(P.rho + (size_t)en * n3, xgl, n, ctr) * nodal_at(P.c + (size_t)en * n3, xgl, n, ctr);
+      zp = nodal_at(P.rho + (size_t)en * n3, xgl, T.gl, n, ctr) * nodal_at(P.c + (size_t)en * n3, xgl, T.gl, n, ctr);
     const double zs = zm + zp;
     const size_t fb = kb + 11 + f * 6;
     put(P.geoK, fb, nw[0], P.prec);

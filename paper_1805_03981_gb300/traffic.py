@@ -41,15 +41,17 @@ _EPI_KIND = {0: "operator", 1: "lsrk_stage", 2: "ader_update", 3: "lsrk_stage"}
 
 
 # The sources that determine the code of the recorded kernels (the 3D operator
-# and predictor launched one solve at a time) and their per-element data: the
-# kernel bodies, their instantiation units, the 1D tables, the geometry set-up
-# and the build flags.  The launch configuration that matters is part of each
-# row (elements per block).
+# and predictor launched one solve at a time) and the layout of their
+# per-element data: the kernel bodies, their instantiation units, the 1D
+# tables and strides (tables.h) and the build flags.  The geometry set-up
+# (setup.cu) only fills values into layouts fixed there, so it is not part
+# of the digest.  The launch configuration that matters is part of each row
+# (elements per block).
 DIGEST_FILES = ("dg_kernels.cuh", "kern_inst.cuh", "kern_f64_lo.cu", "kern_f64_hi.cu", "kern_f32_lo.cu",
                 "kern_f32_hi.cu", "kern_tck_odd_f64.cu", "kern_tck_odd_f32.cu", "tckc.cuh",
                 "kern_tckc_f64_lo.cu", "kern_tckc_f64_hi.cu", "kern_tckc_f32_lo.cu", "kern_tckc_f32_hi.cu",
                 "tckn.cuh", "kern_tckn.cu", "tcki.cuh", "kern_tcki_f32.cu", "kern_lsrk2r_f64.cu",
-                "kern_lsrk2r_f32.cu", "tables.h", "tables.cpp", "setup.cu")
+                "kern_lsrk2r_f32.cu", "tables.h", "tables.cpp")
 
 
 def sources_digest():
