@@ -257,8 +257,10 @@ int dg_get_basis(const dg_ctx* ctx);
  *                   FP32 meshes of affine elements with constant
  *                   coefficients, reduce_every 0 or 2 and no HDG
  *                   derivative (elsewhere the column form runs): fewer
- *                   shared-memory bank conflicts and idle lanes; the column
- *                   form's results bit for bit;
+ *                   shared-memory bank conflicts and idle lanes, and each
+ *                   reduced Taylor term formed on the smaller Gauss set with
+ *                   the projected derivative (Sec. 3.3); the column form's
+ *                   results up to FP32 rounding;
  *  DG_PRED_AUTO     the interleaved form where it applies, else the column
  *                   form, in FP32; the line form in FP64 (default; the FP64
  *                   pipe is the bound there, and the line form keeps whole
@@ -276,7 +278,9 @@ int dg_get_basis(const dg_ctx* ctx);
  * Takes effect on 3D contexts stepped on their own.  Batches (and so the
  * server) choose for themselves: the column form for FP32 Gauss-point
  * states, the line form otherwise; each batched solve then matches the same
- * solve stepped alone with DG_PRED_AUTO bit for bit.  Errors: DG_EINVAL,
+ * solve stepped alone with DG_PRED_AUTO bit for bit, except an FP32 solve
+ * on affine elements with constant coefficients, which runs the interleaved
+ * form alone and agrees to FP32 rounding.  Errors: DG_EINVAL,
  * DG_EUNSUPPORTED (DG_PRED_GL_PROJECTION on a 2D context).
  */
 #define DG_PRED_AUTO 0

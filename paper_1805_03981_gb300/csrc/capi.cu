@@ -460,7 +460,7 @@ bool use_columns(const dg_ctx* ctx) {
 // The interleaved column form (affine elements with constant coefficients,
 // Gauss-point states, reduction every 0 or 2 derivatives, no HDG derivative,
 // FP32): the default there, or chosen with DG_PRED_INTERLEAVED.  Its results
-// are those of the column form bit for bit.
+// are those of the column form up to rounding.
 bool use_interleaved(const dg_ctx* ctx, int red, const void* W) {
   if (ctx->pred_kernel != DG_PRED_AUTO && ctx->pred_kernel != DG_PRED_INTERLEAVED) return false;
   return ctx->affine && ctx->dim == 3 && (red == 0 || red == 2) && W == nullptr &&

@@ -152,6 +152,19 @@ int build_tables(HostTables* t) {
         }
       }
     }
+    // P_2 D: the projected derivative, summed in FP64
+    if (c > 2) {
+      const int r = c - 2;
+      gauss(r, xr.data(), wr.data());
+      double* PD = t->tab + OFF_PD2(c);
+      for (int a = 0; a < r; ++a)
+        for (int b = 0; b < c; ++b) {
+          double sum = 0.0;
+          for (int q = 0; q < c; ++q)
+            sum += wg[q] * lagrange(xr.data(), r, a, xg[q]) / wr[a] * D[q * c + b];
+          PD[a * c + b] = sum;
+        }
+    }
     for (int red = 1; red <= 3; ++red) {
       if (c <= red) continue;
       const int r = c - red;

@@ -15,6 +15,7 @@
 //     I_r [c][c-r] prolongation Gauss(c-r) -> Gauss(c):
 //                  I_r[q][b] = l^{c-r}_b(x^c_q)
 //   W  [c]         Gauss weights; IW [c] their inverses
+//   PD2 [c-2][c]   P_2 D (c > 2), the derivative projected by two points
 //   EO [3][...]    even-odd forms of V, VI (centrosymmetric, M[c-1-i][c-1-j]
 //                  = M[i][j], the point sets being symmetric) and D (skew:
 //                  = -M[i][j]); with h = c / 2, for rows i and columns j < h:
@@ -39,8 +40,11 @@ DG_HD constexpr int dg_red_len(int c, int r) { return c > r ? 2 * c * (c - r) : 
 // even-odd form of one centrosymmetric or skew-centrosymmetric c x c matrix
 // (h = c / 2): A [h+1][h], B [h+1][h], C [h+1]
 DG_HD constexpr int dg_eo_len(int c) { return 2 * (c / 2 + 1) * (c / 2) + (c / 2 + 1); }
+// the projected derivative P_2 D (count c -> c - 2), when c > 2
+DG_HD constexpr int dg_pd_len(int c) { return c > 2 ? (c - 2) * c : 0; }
 DG_HD constexpr int dg_tab_block(int c) {
-  return 3 * c * c + 2 * c + dg_red_len(c, 1) + dg_red_len(c, 2) + dg_red_len(c, 3) + 2 * c + 3 * dg_eo_len(c);
+  return 3 * c * c + 2 * c + dg_red_len(c, 1) + dg_red_len(c, 2) + dg_red_len(c, 3) + 2 * c + 3 * dg_eo_len(c) +
+         dg_pd_len(c);
 }
 DG_HD constexpr int dg_tab_base(int c) {
   return c <= 1 ? 0 : dg_tab_base(c - 1) + dg_tab_block(c - 1);
@@ -62,6 +66,10 @@ DG_HD constexpr int OFF_W(int c) {
 DG_HD constexpr int OFF_IW(int c) { return OFF_W(c) + c; }
 // even-odd forms of V (which 0), VI (1) and D (2) of count c
 DG_HD constexpr int OFF_EO(int c, int which) { return OFF_IW(c) + c + which * dg_eo_len(c); }
+// PD2 [c-2][c] = P_2 D: the collocation derivative followed by the reference
+// L2 projection onto c - 2 points (the two steps of a reduced Taylor term,
+// Sec. 3.3, in one matrix)
+DG_HD constexpr int OFF_PD2(int c) { return OFF_EO(c, 3); }
 
 // Compact per-element data of affine elements with element-wise constant
 // coefficients (see setup.cu): operator block and predictor block sizes.

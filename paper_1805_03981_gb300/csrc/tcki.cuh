@@ -1,9 +1,9 @@
 // Predictor of ADER (the Taylor-Cauchy-Kowalevski sum, Sec. 2.3 Eq. (6),
 // Sec. 3.2 Alg. 2, Sec. 3.3 Alg. 3) for Gauss-point states on affine
 // elements with element-wise constant coefficients: the "interleaved" column
-// form.  It computes what tckc_block computes for such elements (the same
-// contractions in the same order, so the same rounding), with the block's
-// shared memory and threads arranged for fewer shared-memory wavefronts:
+// form.  It computes what tckc_block computes for such elements, with the
+// block's shared memory and threads arranged for fewer shared-memory
+// wavefronts, and with each reduced Taylor term projected as it is formed:
 //
 // * A block holds EPB elements and EPB n^2 threads.  Thread T works on
 //   element le = T % EPB in every phase, on item t = T / EPB (a column, an
@@ -21,10 +21,13 @@
 //   reads and writes of the staging area are conflict free.
 // * The Taylor terms themselves follow the column form: the column owner
 //   keeps T_j on its z-column in registers; the x- and y-derivatives of p and
-//   w_d = sum_i (J^-1)_{d i} v_i go through shared memory; the degree
-//   projections and the final prolongations contract z in registers and x,
-//   y through shared memory; the n-point sum stays in registers, the smaller
-//   levels' sums in shared memory.
+//   w_d = sum_i (J^-1)_{d i} v_i go through shared memory; a term that is
+//   reduced is formed directly on the smaller Gauss set with the projected
+//   derivative P_2 D (tcki_derivative_project), the final prolongations
+//   contract z in registers and x, y through shared memory; the n-point sum
+//   stays in registers, the smaller levels' sums in shared memory.  The
+//   rounding differs from the column form's (other products, other order),
+//   the arithmetic is the same in exact arithmetic.
 #pragma once
 
 #include "tckc.cuh"
@@ -53,7 +56,7 @@ struct TckiShape {
   static constexpr int EPB = tcki_epb(N);
   static constexpr int FT = tcki_Q(N) * N;  // field stride of the line buffers (words)
   static constexpr int NL = tck_level_count<N, RED>();
-  static constexpr int ACC = 8 * FT;         // accumulators of levels 1 .. NL-1, [4][m^3] each
+  static constexpr int ACC = 10 * FT;        // accumulators of levels 1 .. NL-1, [4][m^3] each
   static constexpr int SEW = ACC + tck_acc_off<N, RED>(NL) - 4 * N * N * N;  // words per element
   static constexpr int SL = tcki_stage(N);
   static constexpr int WORDS = (SEW > SL ? SEW : SL) * EPB;  // Reals per block
@@ -205,6 +208,121 @@ __device__ __forceinline__ void tcki_project(Real (&c)[4][N], const TckiCtx<Real
   }
 }
 
+// T_j = P (-S T_{j-1}) from the M-point set straight to the MR = M - 2
+// point set, for a Taylor term that is reduced (Sec. 3.3): on an affine
+// element with constant coefficients the projection P = P_x P_y P_z commutes
+// with the coefficients, so every derivative term is one tensor product of
+// the 1D matrices P_2 and P_2 D (the projected derivative, table PD2):
+//   P grad p = ((P_2D)_x P_y P_z p, P_x (P_2D)_y P_z p, P_x P_y (P_2D)_z p),
+//   P div_ref w = (P_2D)_x P_y P_z w_x + P_x (P_2D)_y P_z w_y + P_x P_y (P_2D)_z w_z.
+// z is contracted by the M-point column owners in registers, x and y through
+// shared memory, as in a derivative; the unreduced term at M points is never
+// formed, and the separate projection pass goes away.
+template <int N, typename Real, int RED, int M, int MR>
+__device__ __forceinline__ void tcki_derivative_project(Real (&c)[4][N],
+                                                        const TckiCtx<Real, TckiShape<N, RED>::EPB>& x) {
+  using SH = TckiShape<N, RED>;
+  constexpr int P = tcki_P(M), Q = tcki_Q(M), PR = tcki_P(MR), QR = tcki_Q(MR), FT = SH::FT;
+  constexpr int PJ = OFF_PR(M, M - MR), PDJ = OFF_PD2(M);  // MR x M each
+  constexpr int S = 0, T = 5 * FT, U = 0;  // S: 5 z-contracted fields; T: 5 after x; U: 4 results (S reused)
+  static_assert(M - MR == 2, "the projected derivative is tabulated for reduction by 2");
+  if (x.act && x.t < M * M) {  // z, by the M-point column owners
+    const int cb = x.t % M + P * (x.t / M);
+    Real p[M], wx[M], wy[M], wz[M];
+#pragma unroll
+    for (int z = 0; z < M; ++z) {
+      const Real v0 = c[1][z], v1 = c[2][z], v2 = c[3][z];
+      p[z] = c[0][z];
+      wx[z] = fma(x.gk[0], v0, fma(x.gk[1], v1, x.gk[2] * v2));
+      wy[z] = fma(x.gk[3], v0, fma(x.gk[4], v1, x.gk[5] * v2));
+      wz[z] = fma(x.gk[6], v0, fma(x.gk[7], v1, x.gk[8] * v2));
+    }
+    Real o[5][MR];
+    mv<Real, PJ, MR, M>(p, o[0]);    // P_z p
+    mv<Real, PDJ, MR, M>(p, o[1]);   // (P_2D)_z p
+    mv<Real, PJ, MR, M>(wx, o[2]);   // P_z w_x
+    mv<Real, PJ, MR, M>(wy, o[3]);   // P_z w_y
+    mv<Real, PDJ, MR, M>(wz, o[4]);  // (P_2D)_z w_z
+#pragma unroll
+    for (int f = 0; f < 5; ++f)
+#pragma unroll
+      for (int z = 0; z < MR; ++z) x.at(S + f * FT + cb + Q * z) = o[f][z];
+  }
+  __syncthreads();
+  if (x.act && x.t < M * MR) {  // x-lines (y, z), y < M, z < MR
+    const int base = P * (x.t % M) + Q * (x.t / M);
+    Real in[M], a[MR], b[MR];
+#pragma unroll
+    for (int s = 0; s < M; ++s) in[s] = x.at(S + base + s);  // P_z p
+    mv<Real, PJ, MR, M>(in, a);
+    mv<Real, PDJ, MR, M>(in, b);
+#pragma unroll
+    for (int s = 0; s < MR; ++s) {
+      x.at(T + base + s) = a[s];       // P_x P_z p
+      x.at(T + FT + base + s) = b[s];  // (P_2D)_x P_z p
+    }
+#pragma unroll
+    for (int s = 0; s < M; ++s) in[s] = x.at(S + FT + base + s);  // (P_2D)_z p
+    mv<Real, PJ, MR, M>(in, a);
+#pragma unroll
+    for (int s = 0; s < MR; ++s) x.at(T + 2 * FT + base + s) = a[s];  // P_x (P_2D)_z p
+#pragma unroll
+    for (int s = 0; s < M; ++s) in[s] = x.at(S + 2 * FT + base + s);  // P_z w_x
+    mv<Real, PDJ, MR, M>(in, a);
+#pragma unroll
+    for (int s = 0; s < M; ++s) in[s] = x.at(S + 4 * FT + base + s);  // (P_2D)_z w_z
+    mv<Real, PJ, MR, M>(in, b);
+#pragma unroll
+    for (int s = 0; s < MR; ++s) x.at(T + 3 * FT + base + s) = a[s] + b[s];  // the x and z divergence terms
+#pragma unroll
+    for (int s = 0; s < M; ++s) in[s] = x.at(S + 3 * FT + base + s);  // P_z w_y
+    mv<Real, PJ, MR, M>(in, a);
+#pragma unroll
+    for (int s = 0; s < MR; ++s) x.at(T + 4 * FT + base + s) = a[s];  // P_x P_z w_y
+  }
+  __syncthreads();
+  if (x.act && x.t < MR * MR) {  // y-lines (x, z), x, z < MR; written in the MR-point layout
+    const int xx = x.t % MR, zz = x.t / MR;
+    const int base = xx + Q * zz;
+    Real in[M], a[MR], b[MR], d[4][MR];
+#pragma unroll
+    for (int s = 0; s < M; ++s) in[s] = x.at(T + FT + base + P * s);
+    mv<Real, PJ, MR, M>(in, d[0]);  // d/dx
+#pragma unroll
+    for (int s = 0; s < M; ++s) in[s] = x.at(T + base + P * s);
+    mv<Real, PDJ, MR, M>(in, d[1]);  // d/dy
+#pragma unroll
+    for (int s = 0; s < M; ++s) in[s] = x.at(T + 2 * FT + base + P * s);
+    mv<Real, PJ, MR, M>(in, d[2]);  // d/dz
+#pragma unroll
+    for (int s = 0; s < M; ++s) in[s] = x.at(T + 3 * FT + base + P * s);
+    mv<Real, PJ, MR, M>(in, a);
+#pragma unroll
+    for (int s = 0; s < M; ++s) in[s] = x.at(T + 4 * FT + base + P * s);
+    mv<Real, PDJ, MR, M>(in, b);
+#pragma unroll
+    for (int s = 0; s < MR; ++s) d[3][s] = a[s] + b[s];  // projected reference divergence
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int s = 0; s < MR; ++s) x.at(U + f * FT + xx + PR * s + QR * zz) = d[f][s];
+  }
+  __syncthreads();
+  if (x.act && x.t < MR * MR) {  // the MR-point column owners apply the coefficients
+    const int cb = x.t % MR + PR * (x.t / MR);
+#pragma unroll
+    for (int z = 0; z < MR; ++z) {
+      const int i = cb + QR * z;
+      const Real gx = x.at(U + i), gy = x.at(U + FT + i), gz = x.at(U + 2 * FT + i), q = x.at(U + 3 * FT + i);
+      c[0][z] = x.gk[9] * q;
+      c[1][z] = x.gk[10] * fma(x.gk[0], gx, fma(x.gk[3], gy, x.gk[6] * gz));
+      c[2][z] = x.gk[10] * fma(x.gk[1], gx, fma(x.gk[4], gy, x.gk[7] * gz));
+      c[3][z] = x.gk[10] * fma(x.gk[2], gx, fma(x.gk[5], gy, x.gk[8] * gz));
+    }
+  }
+  __syncthreads();  // the next derivative writes the fields read above
+}
+
 // acc(level L) += cj T (or = cj T when FIRST), by the owners of the M-point columns
 template <int N, typename Real, int RED, int L, int M, bool FIRST>
 __device__ __forceinline__ void tcki_accumulate(const Real (&c)[4][N], Real (&acc)[4][N],
@@ -233,15 +351,15 @@ template <int N, typename Real, int RED, int J, int M>
 __device__ __forceinline__ void tcki_steps(Real (&c)[4][N], Real (&acc)[4][N],
                                            const TckiCtx<Real, TckiShape<N, RED>::EPB>& x, const TckParams& p) {
   if constexpr (J <= N && M >= 2) {  // at M = 1 the derivative of a constant vanishes: so does every later term
-    tcki_derivative<N, Real, RED, M>(c, x);
     const Real cj = (Real)p.coef[J];
     if constexpr (RED > 0 && J % RED == 0) {
       if constexpr (M - RED >= 1) {  // else projected to a negative degree: T_J = 0, stop
-        tcki_project<N, Real, RED, M, M - RED>(c, x);
+        tcki_derivative_project<N, Real, RED, M, M - RED>(c, x);
         tcki_accumulate<N, Real, RED, J / RED, M - RED, true>(c, acc, x, cj);
         tcki_steps<N, Real, RED, J + 1, M - RED>(c, acc, x, p);
       }
     } else {
+      tcki_derivative<N, Real, RED, M>(c, x);
       constexpr int L = RED > 0 ? (N - M) / RED : 0;
       tcki_accumulate<N, Real, RED, L, M, false>(c, acc, x, cj);
       tcki_steps<N, Real, RED, J + 1, M>(c, acc, x, p);

@@ -139,10 +139,11 @@ def test_predictor_kernel_argument():
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("red", [0, 2])
 @pytest.mark.parametrize("N", [2, 3])
-def test_interleaved_equals_columns_bitwise(k, red, N):
+def test_interleaved_matches_columns(k, red, N):
     """FP32 affine elements with constant coefficients: the interleaved
-    column form (tcki.cuh, DG_PRED_INTERLEAVED, the FP32 default there)
-    gives the column form's results bit for bit, on full blocks and on a
+    column form (tcki.cuh, DG_PRED_INTERLEAVED, the FP32 default there),
+    which forms each reduced Taylor term directly on the smaller Gauss set,
+    agrees with the column form to FP32 rounding, on full blocks and on a
     ragged last block (N^3 = 8 or 27 elements, 8 or 4 per block), and is at
     oracle parity."""
     torch = _cuda()
@@ -155,8 +156,8 @@ def test_interleaved_equals_columns_bitwise(k, red, N):
     Uc = _ader(s, cfg["U0"], dgw.PRED_COLUMNS, dt, 2, red)
     torch.cuda.synchronize()
     s.check_device()
-    assert torch.equal(Ui, Uc)
-    assert torch.equal(Ua, Uc)
+    assert torch.equal(Ua, Ui)                 # the default is the interleaved form
+    assert rel_l2(Ui.cpu().numpy(), Uc.cpu().numpy()) < 2e-6
     import oracle
     o = oracle.Oracle(cfg["mesh"], k, cfg["rho"], cfg["c"], 1.0)
     assert rel_l2(Ui.cpu().numpy(), o.ader(cfg["U0"], dt, 2, red)) < 2e-5
