@@ -513,7 +513,11 @@ void dg_part_destroy(dg_part* t);
  * advances all admitted solves together (dg_batch) in rounds of at most
  * chunk_steps steps, ending a round when a solve finishes. Finished states are copied to the caller's
  * buffer and their memory released; requests that arrived meanwhile join at
- * the next round. Each result is bitwise identical to solving it alone.
+ * the next round. Each result is bitwise identical to solving it alone
+ * with the predictor form batches run (dg_set_predictor_kernel: for an
+ * FP32 solve on affine elements with constant coefficients that is the
+ * column form, where DG_PRED_AUTO alone runs the interleaved form and
+ * agrees to FP32 rounding).
  */
 typedef struct dg_server dg_server;
 typedef struct {

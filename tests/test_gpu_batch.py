@@ -87,7 +87,12 @@ def test_tune_sets_a_valid_tiling():
 @pytest.mark.parametrize("method", ["ader", "ader_red0", "lsrk"])
 def test_batch_gauss_basis_bitwise_equals_alone(prec, method):
     """Gauss-basis batches (general and affine solves mixed) give each solve
-    exactly the state of its own Gauss-basis stepping."""
+    exactly the state of its own Gauss-basis stepping.  Batches run the
+    column-form predictor for FP32 Gauss-point states; stepped alone, an FP32
+    solve on affine elements with constant coefficients runs the interleaved
+    form (the same arithmetic, other rounding), so for those the batch is
+    compared bitwise with the column form alone and to FP32 rounding with
+    the interleaved form."""
     torch = _cuda()
     cfgs, solvers = _mix(7, 6, prec)
     for k in (3, 5):                                    # affine, constant coefficients
@@ -96,15 +101,25 @@ def test_batch_gauss_basis_bitwise_equals_alone(prec, method):
         solvers.append(dgw.Solver(c["mesh"], k, prec, 1.0, c["rho"], c["c"]))
     assert solvers[-1].is_affine() and not solvers[0].is_affine()
     steps = 11
-    alone = []
-    for c, s in zip(cfgs, solvers):
-        s.set_basis(dgw.BASIS_G)
-        U = s.to_device(c["U0"])
+
+    def step(s, U, dt):
         if method.startswith("ader"):
-            s.step_ader(U, c["dt"], steps, 0 if method == "ader_red0" else 2)
+            s.step_ader(U, dt, steps, 0 if method == "ader_red0" else 2)
         else:
-            s.step_lsrk(U, c["dt"], steps)
+            s.step_lsrk(U, dt, steps)
+
+    alone, interleaved = [], {}
+    for i, (c, s) in enumerate(zip(cfgs, solvers)):
+        s.set_basis(dgw.BASIS_G)
+        if prec == dgw.DG_FP32 and s.is_affine() and method.startswith("ader"):
+            U = s.to_device(c["U0"])
+            step(s, U, c["dt"])                         # DG_PRED_AUTO: the interleaved form
+            interleaved[i] = U
+            s.set_predictor_kernel(dgw.PRED_COLUMNS)
+        U = s.to_device(c["U0"])
+        step(s, U, c["dt"])
         alone.append(U)
+    assert len(interleaved) == (2 if prec == dgw.DG_FP32 and method.startswith("ader") else 0)
     states = [s.to_device(c["U0"]) for c, s in zip(cfgs, solvers)]
     b = dgw.Batch(solvers, states, [c["dt"] for c in cfgs])
     b.set_basis(dgw.BASIS_G, convert_each_call=True)
@@ -115,4 +130,6 @@ def test_batch_gauss_basis_bitwise_equals_alone(prec, method):
     torch.cuda.synchronize()
     for i, (u, v) in enumerate(zip(states, alone)):
         assert torch.equal(u, v), (i, (u - v).abs().max().item())
+    for i, v in interleaved.items():
+        assert rel_l2(states[i].cpu().numpy(), v.cpu().numpy()) < 1e-5, i
     b.close()
