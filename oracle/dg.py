@@ -37,10 +37,12 @@ for the two-register schemes, all Butcher order conditions up to their order
 and the paper's critical Courant numbers; TCK terms against symbolic
 (-S)^j u; convergence of both schemes to the analytic standing wave at the
 expected rates; the energy 1/2 U^T M U and the L2 errors against closed
-forms on graded meshes.  Curved meshes with variable
-coefficients are covered by the same code path; beyond the energy identity
-(which is not exact there) and convergence, their parity is unpinned by the
-paper.
+forms on graded meshes; on curved meshes, free-stream preservation (a
+constant state is steady) wherever the Gauss rule integrates the metric
+terms exactly (geometry degree q <= (k + 2) / 2), and the same operator for
+an affine map described by nodes of any degree.  Curved meshes with
+variable coefficients are covered by the same code path; beyond these
+identities and convergence, no value printed in the paper fixes them.
 """
 import math
 import numpy as np

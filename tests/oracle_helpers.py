@@ -15,6 +15,21 @@ def linear_map(A, shift=(0.0, 0.0, 0.0)):
 
 SHEAR = np.array([[1.0, 0.2, 0.1], [0.05, 0.9, 0.15], [-0.1, 0.07, 1.1]])
 
+# phases of the generic curving below (one row per displaced coordinate)
+CURVE_PHASES = np.array([[0.3, 1.1, 2.0], [0.7, 0.2, 1.4], [1.9, 0.5, 0.9]])
+
+
+def generic_curving(a):
+    """x_i <- x_i + a prod_j sin(2 pi x_j + phi_ij): a periodic curving whose
+    three displacements differ, so that the Jacobian has no special
+    structure (the bench's curving adds the same scalar to every
+    coordinate)."""
+    def f(x):
+        s = [np.prod([np.sin(2 * np.pi * x[..., j] + CURVE_PHASES[i, j]) for j in range(3)], axis=0)
+             for i in range(3)]
+        return x + a * np.stack(s, axis=-1)
+    return f
+
 
 def single_element_mesh(A, x0=(0.3, -0.2, 0.5)):
     """One affine element x = x0 + A xi (xi in [-1,1]^3), all faces walls."""

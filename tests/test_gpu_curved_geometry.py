@@ -1,0 +1,92 @@
+"""The GPU's curved geometry against exact properties and the oracle.
+
+* Free-stream preservation: for a map of degree q <= (k + 2) / 2 the
+  (k+1)-point Gauss rule integrates the metric terms exactly, so a constant
+  state has R = 0 to rounding and stays constant under LSRK and ADER steps
+  (the oracle pin in test_oracle_curved_geometry.py).  This checks the GPU's
+  own geometry set-up (Jacobians, inverse-mass diagonals, Nanson normals,
+  orientation of the face data) without reference to the oracle, in both
+  storage bases and both precisions.
+* A generic curving (different displacement per coordinate) at q = k:
+  operator and one step of each method at oracle parity.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1805_03981_gb300 as dgw
+from gpu_helpers import rel_l2
+from oracle_helpers import generic_curving
+
+pytestmark = pytest.mark.gpu
+
+
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _problem(k, q, N, seed=3):
+    mesh = synth.cube_mesh(N, q=q, periodic=True, deform=generic_curving(0.04))
+    n3 = (k + 1) ** 3
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.6, 1.8, (N ** 3, n3))
+    c = rng.uniform(0.6, 1.8, (N ** 3, n3))
+    return mesh, rho, c
+
+
+@pytest.mark.parametrize("prec", [dgw.DG_FP64, dgw.DG_FP32])
+@pytest.mark.parametrize("basis", [dgw.BASIS_GL, dgw.BASIS_G])
+@pytest.mark.parametrize("k,q,N", [(2, 2, 3), (3, 2, 3), (4, 3, 2), (5, 3, 2)])
+def test_constant_state_is_steady(k, q, N, basis, prec):
+    torch = _cuda()
+    assert 2 * q + k - 1 <= 2 * k + 1
+    mesh, rho, c = _problem(k, q, N)
+    s = dgw.Solver(mesh, k, prec, 1.0, rho, c)
+    s.set_basis(basis)
+    n3 = (k + 1) ** 3
+    U0 = np.empty((N ** 3, 4, n3))
+    U0[:, 0] = 0.7
+    U0[:, 1:] = np.array([0.3, -0.5, 0.2])[:, None]
+    tol = 5e-11 if prec == dgw.DG_FP64 else 2e-4   # |R| of a random state is O(10^2)
+    R = s.apply(s.to_device(U0))
+    torch.cuda.synchronize()
+    assert R.abs().max().item() < tol
+    dt = 0.2 / (N * k ** 1.5) / 1.8
+    step_tol = 1e-13 if prec == dgw.DG_FP64 else 2e-6
+    for method in ("lsrk", "ader"):
+        U = s.to_device(U0)
+        if method == "lsrk":
+            s.step_lsrk(U, dt, 3)
+        else:
+            s.step_ader(U, dt, 3, 2)
+        torch.cuda.synchronize()
+        assert np.abs(U.double().cpu().numpy() - U0).max() < step_tol, method
+    s.close()
+
+
+@pytest.mark.parametrize("basis", [dgw.BASIS_GL, dgw.BASIS_G])
+def test_generic_curving_at_oracle_parity(basis):
+    torch = _cuda()
+    k, q, N = 3, 3, 3
+    mesh, rho, c = _problem(k, q, N, seed=8)
+    o = oracle.Oracle(mesh, k, rho, c, 1.0)
+    s = dgw.Solver(mesh, k, dgw.DG_FP64, 1.0, rho, c)
+    s.set_basis(basis)
+    U0 = np.random.default_rng(4).standard_normal((N ** 3, 4, (k + 1) ** 3))
+    R = s.apply(s.to_device(U0))
+    torch.cuda.synchronize()
+    assert rel_l2(R.cpu().numpy(), o.apply(U0)) < 1e-12
+    dt = 0.1 / (N * k ** 1.5) / 1.8
+    U = s.to_device(U0)
+    s.step_lsrk(U, dt, 2)
+    torch.cuda.synchronize()
+    assert rel_l2(U.cpu().numpy(), o.lsrk(U0, dt, 2)) < 1e-12
+    U = s.to_device(U0)
+    s.step_ader(U, dt, 2, 2)
+    torch.cuda.synchronize()
+    assert rel_l2(U.cpu().numpy(), o.ader(U0, dt, 2, 2)) < 1e-12
+    s.close()

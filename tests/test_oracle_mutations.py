@@ -493,3 +493,39 @@ def test_2r_step_pin_catches_a_loop_that_restarts_from_u():
         return S
     assert np.abs(o.lsrk2r(U0, dt, 1) - acc).max() / np.abs(U0).max() < 1e-14
     assert np.abs(wrong(U0) - acc).max() / np.abs(U0).max() > 1e-8
+
+
+# --- curved geometry: free-stream preservation where the quadrature is exact ---
+def _refaces(o, nanson):
+    """Recompute the oracle's face measures and normals with the given
+    version of Nanson's formula (as the oracle's face loop would)."""
+    wf = np.outer(o.wg, o.wg).T.reshape(-1)
+    for f in range(6):
+        Jf = o.jacobian(odg.face_points(f, o.xg))
+        detJf, Jinvf = np.linalg.det(Jf), np.linalg.inv(Jf)
+        d, side = f // 2, (1.0 if f % 2 else -1.0)
+        nw = nanson(wf[None, :, None], detJf[:, :, None], Jinvf, d, side)
+        s = np.linalg.norm(nw, axis=2)
+        o.s[:, f] = s
+        o.nrm[:, f] = nw / s[:, :, None]
+
+
+def test_free_stream_pin_catches_curved_geometry_mistakes():
+    """On a curved mesh with q <= (k+2)/2 a constant state is steady; a
+    transposed Jacobian, a face measure without detJ, or the Nanson normal
+    taken from a column of J^-1 instead of a row each break that."""
+    from test_oracle_curved_geometry import free_stream_residual
+    k, q, N = 3, 2, 3
+
+    class Transposed(oracle.Oracle):
+        def jacobian(self, pts):
+            return np.swapaxes(super().jacobian(pts), -1, -2)
+
+    right = lambda w, det, Ji, d, side: w * det * side * Ji[:, :, d, :]
+    no_det = lambda w, det, Ji, d, side: w * side * Ji[:, :, d, :]
+    column = lambda w, det, Ji, d, side: w * det * side * Ji[:, :, :, d]
+    assert free_stream_residual(k, q, N, 1.0) < 5e-11
+    assert free_stream_residual(k, q, N, 1.0, mutate=lambda o: _refaces(o, right)) < 5e-11
+    assert free_stream_residual(k, q, N, 1.0, oracle_cls=Transposed) > 1e-3
+    assert free_stream_residual(k, q, N, 1.0, mutate=lambda o: _refaces(o, no_det)) > 1e-3
+    assert free_stream_residual(k, q, N, 1.0, mutate=lambda o: _refaces(o, column)) > 1e-3
