@@ -51,3 +51,12 @@ def poly1d_lagrange(nodes, a):
 def exact_int(p):
     P = p.integ()
     return P(1.0) - P(-1.0)
+
+
+def generic_curving_2d(a):
+    """2D counterpart of generic_curving: x_i <- x_i + a prod_j sin(2 pi x_j + phi_ij)."""
+    def f(x):
+        s = [np.prod([np.sin(2 * np.pi * x[..., j] + CURVE_PHASES[i, j]) for j in range(2)], axis=0)
+             for i in range(2)]
+        return x + a * np.stack(s, axis=-1)
+    return f

@@ -9,6 +9,7 @@
   storage bases and both precisions.
 * A generic curving (different displacement per coordinate) at q = k:
   operator and one step of each method at oracle parity.
+* The 2D path: a constant state is steady for q <= k + 2.
 """
 import numpy as np
 import pytest
@@ -16,8 +17,9 @@ import pytest
 import oracle
 import synth
 import paper_1805_03981_gb300 as dgw
+from synth import mesh2d
 from gpu_helpers import rel_l2
-from oracle_helpers import generic_curving
+from oracle_helpers import generic_curving, generic_curving_2d
 
 pytestmark = pytest.mark.gpu
 
@@ -89,4 +91,34 @@ def test_generic_curving_at_oracle_parity(basis):
     s.step_ader(U, dt, 2, 2)
     torch.cuda.synchronize()
     assert rel_l2(U.cpu().numpy(), o.ader(U0, dt, 2, 2)) < 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [dgw.DG_FP64, dgw.DG_FP32])
+@pytest.mark.parametrize("k,q", [(1, 3), (3, 5), (5, 7)])
+def test_2d_constant_state_is_steady(k, q, prec):
+    torch = _cuda()
+    N = 4
+    mesh = mesh2d.square_mesh(N, q=q, periodic=True, deform=generic_curving_2d(0.04))
+    n2 = (k + 1) ** 2
+    rng = np.random.default_rng(5)
+    rho = rng.uniform(0.6, 1.8, (N * N, n2))
+    c = rng.uniform(0.6, 1.8, (N * N, n2))
+    s = dgw.Solver2D(mesh, k, prec, 1.0, rho, c)
+    U0 = np.empty((N * N, 3, n2))
+    U0[:, 0] = 0.7
+    U0[:, 1] = 0.3
+    U0[:, 2] = -0.5
+    R = s.apply(s.to_device(U0))
+    torch.cuda.synchronize()
+    assert R.abs().max().item() < (5e-11 if prec == dgw.DG_FP64 else 2e-4)
+    dt = 0.2 / (N * k ** 1.5) / 1.8
+    for method in ("lsrk", "ader"):
+        U = s.to_device(U0)
+        if method == "lsrk":
+            s.step_lsrk(U, dt, 3)
+        else:
+            s.step_ader(U, dt, 3, 2)
+        torch.cuda.synchronize()
+        assert np.abs(U.double().cpu().numpy() - U0).max() < (1e-13 if prec == dgw.DG_FP64 else 2e-6), method
     s.close()

@@ -17,13 +17,18 @@ inverse Jacobians at the quadrature points, Nanson's formula on the faces).
   crime Sec. 3 accepts), which makes the pin sharp.
 * An affine map described by geometry nodes of degree q > 1 gives the same
   operator as its degree-1 description.
+* In 2D the cofactor entries are single derivatives of the map (degree q
+  along one direction, q - 1 along the other), so the cell integrands have
+  degree <= q + k - 1 and the face terms <= q - 1 + k: exact, and a
+  constant state steady, for q <= k + 2, and not beyond.
 """
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from oracle_helpers import SHEAR, generic_curving, linear_map
+from synth import mesh2d
+from oracle_helpers import SHEAR, generic_curving, generic_curving_2d, linear_map
 
 
 def constant_state(E, n3, p0=0.7, v0=(0.3, -0.5, 0.2)):
@@ -75,3 +80,24 @@ def test_high_degree_description_of_an_affine_map(k):
     scale = np.abs(R[0]).max()
     assert np.abs(R[1] - R[0]).max() < 1e-12 * scale
     assert np.abs(R[2] - R[0]).max() < 1e-12 * scale
+
+
+def free_stream_residual_2d(k, q, N=4, alpha=1.0, seed=3):
+    mesh = mesh2d.square_mesh(N, q=q, periodic=True, deform=generic_curving_2d(0.04))
+    n2 = (k + 1) ** 2
+    rng = np.random.default_rng(seed)
+    rho = rng.uniform(0.6, 1.8, (N * N, n2))
+    c = rng.uniform(0.6, 1.8, (N * N, n2))
+    o = oracle.Oracle2D(mesh, k, rho, c, alpha)
+    U = np.empty((N * N, 3, n2))
+    U[:, 0] = 0.7
+    U[:, 1] = 0.3
+    U[:, 2] = -0.5
+    return np.abs(o.apply(U)).max()
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_2d_constant_state_steady_up_to_q_k_plus_2(k):
+    for q in range(1, k + 3):
+        assert free_stream_residual_2d(k, q) < 5e-11, q
+    assert free_stream_residual_2d(k, k + 3) > 1e-4
