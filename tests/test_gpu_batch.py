@@ -73,6 +73,32 @@ def test_batch_matches_oracle_and_tiling_invariance():
     b.close()
 
 
+def test_autotune_table_records_tiling_and_predictor_form():
+    """autotune.tune times the Gauss-basis kernels and both predictor forms;
+    the recorded form is the faster one, and apply sets it on a curved
+    solver but not on an affine one."""
+    _cuda()
+    from paper_1805_03981_gb300 import autotune
+    table = autotune.tune(("fp32",), [3], reps=1)
+    for cls in autotune.SIZE_CLASSES:
+        r = table["fp32"]["3"][cls]
+        assert r["pred"] in ("lines", "columns")
+        other = "lines" if r["pred"] == "columns" else "columns"
+        assert r["tck"]["ms"] == r["tck_" + r["pred"]]["ms"] <= r["tck_" + other]["ms"]
+        assert r["epb_tck"] == r["tck_" + r["pred"]]["epb"]
+    cfg = synth.configs.curved_pulse(N=4, k=3)
+    s = dgw.Solver(cfg["mesh"], 3, dgw.DG_FP32, 1.0, cfg["rho"], cfg["c"])
+    autotune.apply(s, table)
+    want = dgw.PRED_COLUMNS if table["fp32"]["3"]["small"]["pred"] == "columns" else dgw.PRED_LINES
+    assert s.predictor_kernel() == want
+    s.close()
+    c = synth.configs.standing_wave(N=4, k=3)
+    s = dgw.Solver(c["mesh"], 3, dgw.DG_FP32, 1.0, c["rho"], c["c"])
+    autotune.apply(s, table)
+    assert s.predictor_kernel() == dgw.PRED_AUTO
+    s.close()
+
+
 def test_tune_sets_a_valid_tiling():
     torch = _cuda()
     cfg = synth.configs.curved_pulse(N=4, k=4)
