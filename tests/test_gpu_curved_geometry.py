@@ -122,3 +122,35 @@ def test_2d_constant_state_is_steady(k, q, prec):
         torch.cuda.synchronize()
         assert np.abs(U.double().cpu().numpy() - U0).max() < (1e-13 if prec == dgw.DG_FP64 else 2e-6), method
     s.close()
+
+
+@pytest.mark.parametrize("prec", [dgw.DG_FP64, dgw.DG_FP32])
+@pytest.mark.parametrize("k", [2, 3, 5])
+@pytest.mark.parametrize("red", [0, 2])
+def test_tck_of_linear_fields_closed_form(k, red, prec):
+    """The predictor of a linear field of the discrete map on a curved mesh
+    (geometry degree k, constant coefficients) is dt u + dt^2/2 T_1 with the
+    constant T_1 = (-rho c^2 tr B, -a / rho) (the oracle pin in
+    test_oracle_curved_geometry.py): dg_tck (GL states) directly, and the
+    Gauss-point predictors in both forms through one ADER step, whose
+    increment must then be R(dt u + dt^2/2 T_1)."""
+    torch = _cuda()
+    from test_oracle_curved_geometry import curved_linear_case
+    mesh, rho, c, U, T1 = curved_linear_case(k)
+    s = dgw.Solver(mesh, k, prec, 1.0, rho, c)
+    dt = 0.01
+    ref = dt * U + 0.5 * dt ** 2 * T1
+    tol = 1e-13 if prec == dgw.DG_FP64 else 2e-6
+    Ub = s.tck(s.to_device(U), dt, red)
+    torch.cuda.synchronize()
+    assert np.abs(Ub.double().cpu().numpy() - ref).max() < tol * np.abs(ref).max()
+    incr = s.apply(s.to_device(ref)).double().cpu().numpy()
+    s.set_basis(dgw.BASIS_G)
+    for pred in (dgw.PRED_LINES, dgw.PRED_COLUMNS):
+        s.set_predictor_kernel(pred)
+        V = s.to_device(U)
+        s.step_ader(V, dt, 1, red)
+        torch.cuda.synchronize()
+        got = V.double().cpu().numpy() - U
+        assert np.abs(got - incr).max() < (1e-11 if prec == dgw.DG_FP64 else 2e-4) * np.abs(incr).max(), pred
+    s.close()

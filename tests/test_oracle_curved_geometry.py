@@ -101,3 +101,47 @@ def test_2d_constant_state_steady_up_to_q_k_plus_2(k):
     for q in range(1, k + 3):
         assert free_stream_residual_2d(k, q) < 5e-11, q
     assert free_stream_residual_2d(k, k + 3) > 1e-4
+
+
+def linear_fields(x, rng):
+    """p = a.x + b and v = B x + v0 at the points x [E, P, 3], packed as a
+    state [E, 4, P], with the exact T_1 = -S u for constant rho, c:
+    (-rho c^2 tr B, -a / rho), and T_j = 0 beyond (T_1 is constant)."""
+    a, b = rng.standard_normal(3), rng.standard_normal()
+    B, v0 = rng.standard_normal((3, 3)), rng.standard_normal(3)
+    U = np.empty((x.shape[0], 4, x.shape[1]))
+    U[:, 0] = x @ a + b
+    U[:, 1:] = np.transpose(x @ B.T + v0, (0, 2, 1))
+    return U, a, np.trace(B)
+
+
+def curved_linear_case(k, seed=31):
+    """A generically curved periodic mesh with geometry degree q = k, whose
+    geometry nodes are the solution nodes, so a linear function of the
+    discrete map is exactly a degree-k field; constant rho and c."""
+    mesh = synth.cube_mesh(3, q=k, periodic=True, deform=generic_curving(0.04))
+    n3 = (k + 1) ** 3
+    rho0, c0 = 1.3, 0.8
+    U, a, trB = linear_fields(np.asarray(mesh["nodes"]), np.random.default_rng(seed))
+    T1 = np.empty_like(U)
+    T1[:, 0] = -rho0 * c0 ** 2 * trB
+    T1[:, 1:] = (-a / rho0)[None, :, None]
+    return mesh, np.full((27, n3), rho0), np.full((27, n3), c0), U, T1
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("red", [0, 2])
+def test_tck_of_linear_fields_on_a_curved_mesh(k, red):
+    """On a curved mesh the collocated gradient and divergence of a linear
+    field of the discrete map are exact (grad_ref p = J^T a), so the first
+    Taylor term is the constant -S u and the predictor is dt u + dt^2/2 T_1."""
+    mesh, rho, c, U, T1 = curved_linear_case(k)
+    o = oracle.Oracle(mesh, k, rho, c, 1.0)
+    dt = 0.01
+    Ubar, terms = o.tck(U, dt, red, return_terms=True)
+    ref = dt * U + 0.5 * dt ** 2 * T1
+    assert np.abs(Ubar - ref).max() < 1e-13 * np.abs(ref).max()
+    m1, t1 = terms[1]
+    assert m1 == k + 1 and np.abs(t1 - T1[:, :, :1]).max() < 1e-11 * np.abs(T1).max()
+    m2, t2 = terms[2]  # the derivative of a constant: rounding only (later terms differentiate that again)
+    assert t2 is None or np.abs(t2).max() < 1e-9 * np.abs(T1).max()

@@ -529,3 +529,22 @@ def test_free_stream_pin_catches_curved_geometry_mistakes():
     assert free_stream_residual(k, q, N, 1.0, oracle_cls=Transposed) > 1e-3
     assert free_stream_residual(k, q, N, 1.0, mutate=lambda o: _refaces(o, no_det)) > 1e-3
     assert free_stream_residual(k, q, N, 1.0, mutate=lambda o: _refaces(o, column)) > 1e-3
+
+
+def test_curved_tck_pin_catches_a_transposed_jacobian():
+    """The predictor of a linear field on a curved mesh is dt u + dt^2/2 T_1
+    in closed form; an oracle that evaluates the Jacobian transposed (which
+    the affine symbolic pins on a diagonal map cannot see) misses it."""
+    from test_oracle_curved_geometry import curved_linear_case
+    k = 3
+    mesh, rho, c, U, T1 = curved_linear_case(k)
+    ref = 0.01 * U + 0.5 * 0.01 ** 2 * T1
+
+    class Transposed(oracle.Oracle):
+        def jacobian(self, pts):
+            return np.swapaxes(super().jacobian(pts), -1, -2)
+
+    good = oracle.Oracle(mesh, k, rho, c, 1.0).tck(U, 0.01, 2)
+    bad = Transposed(mesh, k, rho, c, 1.0).tck(U, 0.01, 2)
+    assert np.abs(good - ref).max() < 1e-13 * np.abs(ref).max()
+    assert np.abs(bad - ref).max() > 1e-8 * np.abs(ref).max()
