@@ -39,8 +39,9 @@ and the paper's critical Courant numbers; TCK terms against symbolic
 expected rates; the energy 1/2 U^T M U and the L2 errors against closed
 forms on graded meshes; on curved meshes, free-stream preservation (a
 constant state is steady) wherever the Gauss rule integrates the metric
-terms exactly (geometry degree q <= (k + 2) / 2), and the same operator for
-an affine map described by nodes of any degree.  Curved meshes with
+terms exactly (geometry degree q <= (k + 2) / 2), the same operator for
+an affine map described by nodes of any degree, and the predictor of a
+linear field of the discrete map in closed form.  Curved meshes with
 variable coefficients are covered by the same code path; beyond these
 identities and convergence, no value printed in the paper fixes them.
 """
